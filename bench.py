@@ -1,0 +1,405 @@
+#!/usr/bin/env python3
+"""Benchmark of the Log(Graph) hot path on GB300.
+
+One step = one pass of the whole hot path over one synthetic graph resident in
+HBM: lg_encode (DM relabel, widths, prefix sums, bit packing, Elias-Fano
+offsets), lg_bfs from 16 sources (bit-parallel multi-source sweeps with the
+decoder fused into frontier expansion) and lg_pagerank (20 pull iterations with
+the decoder fused in), then lg_free.  The same kernels on the uncompressed
+32-bit CSR (LG_ID_CSR32) run beside it as the baseline arm.
+
+Metric: GTEPS = traversed edges per second, where a BFS from one source counts
+(sum of the degrees of the reached vertices) / 2 (Graph500 convention) and a
+PageRank iteration counts every stored arc once.  ``value`` is over the full
+step (encode included); the JSON also carries kernel-only BFS / PageRank GTEPS,
+the CSR-32 arm, bytes per arc, the roofline of the PageRank kernel and the CPU
+oracle baseline.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lg|reference]
+                       [--workload community|rmat16|rmat27]
+Under torchrun (N > 1) every rank runs an independent replica ("replicas only":
+one GPU holds the whole graph, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import gen  # noqa: E402  (seeded inputs)
+
+WORKLOADS = {
+    # name: (description, generator, encode options, BFS sources, PageRank iterations)
+    "community": ("community graph: 2^24 vertices in 2^14 blocks of 1024, Zipf(2) out-degrees mean 16, "
+                  "90% intra-block, random global permutation; DM relabel + local-gap IDs + Elias-Fano "
+                  "offsets (select sample 512)",
+                  lambda: gen.community_2p24(seed=2),
+                  dict(id_mode=2, off_mode=1, relabel=True, select_sample=512), 16, 20),
+    "rmat16": ("R-MAT scale 16, edge factor 16, (a,b,c)=(.57,.19,.19); global 16-bit IDs + packed offsets",
+               lambda: gen.rmat_s16_ef16(seed=1),
+               dict(id_mode=0, off_mode=0, relabel=False), 64, 20),
+    "rmat27": ("R-MAT scale 27, edge factor 16, weights in [1,255] at 8 bits; global 27-bit IDs + "
+               "Elias-Fano offsets",
+               lambda: gen.rmat_s27_ef16_weighted(seed=5),
+               dict(id_mode=0, off_mode=1, relabel=False, weight_bits=8), 16, 20),
+}
+HBM_FALLBACK_GBS = 6800.0
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return HBM_FALLBACK_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("lg_traverse.cuh", "lg_device.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2010_15879_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload):
+    """DRAM bytes per launch of the PageRank kernel from the committed ncu
+    summary, only if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(workload)
+    if not e or e.get("source_sha") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.proc = None
+        self.f = None
+
+    def __enter__(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.f is None:
+            return None
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        mhz = [r[0] for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower().startswith("active")})
+        return {"sm_mhz": float(np.median(mhz)), "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": reasons}
+
+
+def teps_bfs(depths_u32: np.ndarray, deg: np.ndarray) -> int:
+    """Graph500 traversed edges: sum of degrees of reached vertices / 2, per source."""
+    total = 0
+    for row in depths_u32:
+        total += int(deg[row != 0xFFFFFFFF].sum()) // 2
+    return total
+
+
+# --------------------------------------------------------------------- GPU arm
+def run_lg(args, rank, world):
+    import torch
+
+    import paper_2010_15879_gb300 as lg
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    lg.load(auto_build=True)
+    desc, make, opts, S, T = WORKLOADS[args.workload]
+    t0 = time.time()
+    g0 = make()
+    log(f"[rank {rank}] generated {g0.name}: n={g0.n} arcs={g0.arcs} in {time.time() - t0:.1f}s")
+    deg = g0.degrees()
+    src_h = gen.sources(g0, S, seed=7)
+    rp_h = torch.from_numpy(g0.row_ptr.view(np.int64))
+    col_h = torch.from_numpy(g0.col.view(np.int32))
+    w_h = None if g0.weights is None or "weight_bits" not in opts else torch.from_numpy(g0.weights.view(np.int32))
+    rp_d, col_d = rp_h.to(dev), col_h.to(dev)
+    w_d = None if w_h is None else w_h.to(dev)
+    src_d = torch.from_numpy(src_h.view(np.int32)).to(dev)
+    depths = torch.empty((S, g0.n), dtype=torch.int32, device=dev)
+    ranks = torch.empty(g0.n, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def step(id_mode_opts, ev=None):
+        """one pass of the hot path; optional events (enc, bfs, pr, end)."""
+        if ev: ev[0].record(stream)
+        g = lg.lg_encode(rp_d, col_d, w_d, **id_mode_opts)
+        if ev: ev[1].record(stream)
+        lg.lg_bfs(g, src_d, out=depths)
+        if ev: ev[2].record(stream)
+        lg.lg_pagerank(g, 0.85, T, out=ranks)
+        if ev: ev[3].record(stream)
+        st = g.stats()
+        g.free()
+        return st
+
+    def timed(id_mode_opts, label):
+        for _ in range(args.warmup):
+            step(id_mode_opts)
+        torch.cuda.synchronize(dev)
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize(dev)
+        l0 = lg.lg_kernel_launches()
+        start.record(stream)
+        for k in range(args.steps):
+            st = step(id_mode_opts, evs[k])
+        stop.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        launches = lg.lg_kernel_launches() - l0
+        ms = start.elapsed_time(stop)
+        enc = [e[0].elapsed_time(e[1]) for e in evs]
+        bfs = [e[1].elapsed_time(e[2]) for e in evs]
+        pr = [e[2].elapsed_time(e[3]) for e in evs]
+        log(f"[rank {rank}] {label}: step {ms / args.steps:.2f} ms (encode {np.median(enc):.2f}, "
+            f"bfs {np.median(bfs):.2f}, pr {np.median(pr):.2f})")
+        return dict(ms=ms, enc=enc, bfs=bfs, pr=pr, stats=st, launches=launches)
+
+    # correctness-independent TEPS accounting from one BFS run
+    step(opts)
+    torch.cuda.synchronize(dev)
+    te_bfs = teps_bfs(depths.cpu().numpy().view(np.uint32), deg)
+    te_pr = g0.arcs * T
+    te_step = te_bfs + te_pr
+
+    with ClockSampler(dev.index) as clk:
+        res = timed(opts, "log(graph)")
+    clocks = clk.summary()
+    csr = timed(dict(id_mode=3, relabel=False), "csr32")
+
+    # e2e: host CSR in pinned memory -> device -> hot path -> results to pinned host
+    rp_p, col_p = rp_h.pin_memory(), col_h.pin_memory()
+    w_p = None if w_h is None else w_h.pin_memory()
+    src_p = torch.from_numpy(src_h.view(np.int32)).pin_memory()
+    dep_p = torch.empty((S, g0.n), dtype=torch.int32).pin_memory()
+    rk_p = torch.empty(g0.n, dtype=torch.float32).pin_memory()
+
+    def e2e_step():
+        g = lg.lg_encode(rp_p, col_p, w_p, **opts)
+        d = lg.lg_bfs(g, src_p.to(dev, non_blocking=True), out=depths)
+        r = lg.lg_pagerank(g, 0.85, T, out=ranks)
+        dep_p.copy_(d, non_blocking=True)
+        rk_p.copy_(r, non_blocking=True)
+        g.free()
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    h2d = rp_h.numel() * 8 + col_h.numel() * 4 + (0 if w_h is None else w_h.numel() * 4) + S * 4
+    d2h = S * g0.n * 4 + g0.n * 4
+
+    step_ms = res["ms"] / args.steps
+    st = res["stats"]
+    pr_ms_iter = float(np.median(res["pr"])) / T
+    bfs_ms = float(np.median(res["bfs"]))
+    csr_pr_ms_iter = float(np.median(csr["pr"])) / T
+    csr_bfs_ms = float(np.median(csr["bfs"]))
+    # algorithmic bytes of one PageRank pull launch: the compressed A and O
+    # payload, a 4 B contribution gather per arc and a 4 B contribution write
+    # per vertex
+    alg_bytes = (st["bits_A"] + st["bits_O"]) // 8 + 4 * g0.arcs + 4 * g0.n
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / (pr_ms_iter * 1e-3) / 1e9
+
+    out = {
+        "metric": "GTEPS (BFS 16 sources + PageRank 20 iterations, Log(Graph) compressed, full step incl. encode)",
+        "value": None, "unit": "GTEPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32 ids / fp32 ranks", "data": "synthetic (seeded generator; no dataset)",
+        "config": {"workload": desc, "n": g0.n, "arcs": g0.arcs, "bfs_sources": S, "pr_iters": T,
+                   "damping": 0.85, "l2": "inputs larger than L2 (CSR %.2f GB)" %
+                   ((g0.n + 1) * 8 / 1e9 + g0.arcs * 4 / 1e9), "parallelism": f"replicas x{world}"},
+    }
+    local = {"te_step": te_step, "step_ms": step_ms, "e2e_ms": e2e_ms}
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([step_ms, e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms, e2e_ms = float(t[0]), float(t[1])
+    out["ms_per_step"] = step_ms
+    out["value"] = world * te_step / (step_ms * 1e-3) / 1e9
+    out["e2e"] = {"value": world * te_step / (e2e_ms * 1e-3) / 1e9, "unit": "GTEPS", "ms_per_step": e2e_ms,
+                  "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    out["gpu_launches"] = int(res["launches"])
+    out["detail"] = {
+        "encode_ms": float(np.median(res["enc"])), "bfs_ms": bfs_ms, "pr_ms_per_iter": pr_ms_iter,
+        "bfs_gteps": te_bfs / (bfs_ms * 1e-3) / 1e9, "pr_gteps": te_pr / (pr_ms_iter * T * 1e-3) / 1e9,
+        "bits_per_arc": st["bits_per_arc"], "bits_A": st["bits_A"], "bits_O": st["bits_O"],
+        "bytes_total": st["bytes_total"],
+        "csr32": {"step_ms": csr["ms"] / args.steps, "encode_ms": float(np.median(csr["enc"])),
+                  "bfs_ms": csr_bfs_ms, "pr_ms_per_iter": csr_pr_ms_iter,
+                  "bfs_gteps": te_bfs / (csr_bfs_ms * 1e-3) / 1e9,
+                  "pr_gteps": te_pr / (csr_pr_ms_iter * T * 1e-3) / 1e9,
+                  "bytes_payload": 4 * g0.arcs + 8 * (g0.n + 1),
+                  "value": te_step / (csr["ms"] / args.steps * 1e-3) / 1e9},
+        "bytes_vs_csr32": ((st["bits_A"] + st["bits_O"]) / 8) / (4 * g0.arcs + 8 * (g0.n + 1)),
+        "bfs_gteps_vs_csr32": csr_bfs_ms / bfs_ms, "pr_gteps_vs_csr32": csr_pr_ms_iter / pr_ms_iter,
+    }
+    out["roofline"] = {"kernel": "k_pr_pull (PageRank pull iteration, decode fused)", "bound": "hbm",
+                       "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                       "peak_kind": f"{peak_kind} (copy bandwidth)",
+                       "algorithmic_bytes_per_launch": alg_bytes,
+                       "traffic": ncu_traffic(args.workload)}
+    out["clocks"] = clocks
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(g0, src_h, T, min_seconds=10.0)
+    return out, rank
+
+
+# ------------------------------------------------------------------ CPU oracle
+def cpu_baseline(g0, src_h, T, min_seconds=10.0, max_units=None):
+    """The oracle as it stands (single-threaded C) on a bounded sample: BFS from
+    the first sources and whole PageRank iterations, until about min_seconds."""
+    import oracle
+
+    deg = g0.degrees()
+    te = 0
+    t0 = time.time()
+    nb = npr = 0
+    while True:
+        s = int(src_h[nb % len(src_h)])
+        d = oracle.bfs(g0.n, g0.row_ptr, g0.col, s)
+        te += int(deg[d != 0xFFFFFFFF].sum()) // 2
+        nb += 1
+        oracle.pagerank(g0.n, g0.row_ptr, g0.col, 0.85, 1)
+        te += g0.arcs
+        npr += 1
+        el = time.time() - t0
+        if el >= min_seconds or (max_units and nb >= max_units):
+            break
+    return {"value": te / el / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+            "sample": f"{nb} BFS source(s) + {npr} PageRank iteration(s) of the same graph, {el:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    desc, make, opts, S, T = WORKLOADS[args.workload]
+    g0 = make()
+    src_h = gen.sources(g0, S, seed=7)
+    for _ in range(args.warmup):
+        cpu_baseline(g0, src_h, T, min_seconds=0.0, max_units=1)
+    t0 = time.time()
+    vals = []
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(g0, src_h, T, min_seconds=0.0, max_units=1))
+    el = time.time() - t0
+    v = float(np.mean([x["value"] for x in vals]))
+    out = {"impl": "reference", "metric": "GTEPS (BFS 16 sources + PageRank 20 iterations, Log(Graph) "
+                                          "compressed, full step incl. encode)",
+           "value": v, "unit": "GTEPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64 ranks / u32 depths", "data": "synthetic (seeded generator)",
+           "config": {"workload": desc, "n": g0.n, "arcs": g0.arcs, "bfs_sources": S, "pr_iters": T,
+                      "parallelism": "host cores"},
+           "cpu_baseline": {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                            "sample": "per step: 1 BFS source + 1 PageRank iteration of the same graph"},
+           "e2e": {"value": v, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    return out, rank
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["lg", "reference"], default="lg")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="community")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        log("warmup raised to 3 (timing rule)")
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        out, _ = run_reference(args, rank, world)
+        print(json.dumps(out), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    out, rank = run_lg(args, rank, world)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * lg.h -- C ABI of the GB300 Log(Graph) hot path (liblg.so).
+ *
+ * Log(Graph) (Besta et al., PACT'18; full version arXiv:2010.15879) stores a
+ * graph's adjacency array AA = (O, A) in "logarithmized" form: vertex IDs in
+ * ceil(log n) bits or in per-neighborhood local / fixed-size-gap widths, edge
+ * weights in ceil(log maxW) bits, and the offsets O either bit-packed at
+ * ceil(log 2m) bits or as an Elias-Fano (sparse succinct, "bvSD") bit vector.
+ * This library builds that structure on the GPU from a CSR and runs the graph
+ * kernels directly on it, decoding neighborhoods inside the kernels.
+ *
+ * Conventions shared by every entry point
+ *   - Pointers marked "device" must be CUDA device (or managed) memory on the
+ *     current device; "host" means ordinary host memory.  No entry point frees
+ *     a caller buffer.  All sizes are element counts unless said otherwise.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued on it.  Entry points that must read a device
+ *     result on the host (sizes, error flags, BFS frontier counts) synchronize
+ *     that stream before returning; each says so.
+ *   - Vertex IDs at the API are the caller's original 0-based IDs (n < 2^32).
+ *     A relabeling chosen at encode time stays internal.
+ *   - Errors: every entry point returns an lg_status; a human-readable message
+ *     for the calling thread is available from lg_last_error().  No kernel
+ *     traps; device-detected errors are reported through a device flag.
+ *   - Thread safety: calls on distinct lg_graph objects may run concurrently;
+ *     calls on the same graph may run concurrently only if they use the same
+ *     stream or are otherwise ordered by the caller.
+ */
+#ifndef LG_H
+#define LG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lg_graph lg_graph; /* opaque; owns all of its device memory */
+
+typedef enum {
+    LG_OK = 0,
+    LG_EINVAL = 1,        /* bad argument or invalid input CSR              */
+    LG_ENOMEM = 2,        /* device or host allocation failed                */
+    LG_ECUDA = 3,         /* a CUDA runtime call failed                      */
+    LG_ERANGE = 4,        /* output capacity too small (sizes were written)  */
+    LG_ETIMEOUT = 5,      /* a bounded device wait ran out                   */
+    LG_EUNSUPPORTED = 6   /* valid but unsupported combination of options    */
+} lg_status;
+
+/* How vertex IDs are stored in A (Sections 3.2.1, 3.2.2 and 3.6). */
+typedef enum {
+    LG_ID_GLOBAL = 0,     /* every ID in s = ceil(log2 n) bits ("LG-g")                     */
+    LG_ID_LOCAL = 1,      /* per neighborhood: [w_v : H][d_v IDs of w_v bits] ("LG-l")      */
+    LG_ID_LOCAL_GAP = 2,  /* [g_v : H][first ID : s][d_v - 1 differences of g_v bits]
+                             ("LG-l-gap", fixed-size gap encoding)                          */
+    LG_ID_CSR32 = 3       /* not compressed: 32-bit IDs and 64-bit row offsets, the
+                             traditional adjacency array run by the same kernels            */
+} lg_id_mode;
+
+/* How the offsets O are stored (Sections 3.4 and 4.3). */
+typedef enum {
+    LG_OFF_PACKED = 0,    /* O[0..n] each in w_O = bits(x_n) bits ("ptrLogn")             */
+    LG_OFF_EF = 1         /* Elias-Fano over x_0..x_n with select samples ("bvSD")         */
+} lg_off_mode;
+
+#define LG_FLAG_CHECK_SYMMETRIC 1u /* lg_encode also verifies that every arc has its reverse */
+
+typedef struct {
+    uint32_t id_mode;       /* lg_id_mode                                                   */
+    uint32_t off_mode;      /* lg_off_mode (ignored for LG_ID_CSR32)                        */
+    uint32_t relabel;       /* 0 = keep IDs, 1 = DM permuter (Section 5.6): higher degree
+                               gets a smaller label, ties by original ID                    */
+    uint32_t select_sample; /* EF select sample rate, a power of two in [64, 65536];
+                               0 means 512                                                  */
+    uint32_t weight_bits;   /* 0 = bits(max weight); else the fixed weight width (<= 32)    */
+    uint32_t flags;         /* LG_FLAG_* bits                                               */
+} lg_encode_opts;
+
+typedef struct {
+    uint64_t n, arcs;          /* vertices, stored arcs (2m for an undirected graph)        */
+    uint64_t bits_A;           /* exact payload bits of A                                   */
+    uint64_t bits_O;           /* exact payload bits of O (packed, or EF low + high +
+                                  64 per select sample)                                     */
+    uint64_t bytes_A, bytes_O; /* device bytes held, with padding and guard words           */
+    uint64_t bytes_perm;       /* device bytes of the permutation (0 without relabel)       */
+    uint64_t bytes_total;      /* bytes_A + bytes_O + bytes_perm                            */
+    uint64_t max_degree;
+    uint32_t id_mode, off_mode, relabel, weighted;
+    uint32_t s;                /* global ID width, max(1, bits(n - 1))                      */
+    uint32_t H;                /* width of the per-neighborhood width field, bits(s)        */
+    uint32_t omega;            /* weight width (0 if unweighted)                            */
+    uint32_t w_O;              /* packed offset width (0 for EF)                            */
+    uint32_t ef_l;             /* Elias-Fano low-bit count (0 for packed)                   */
+    uint32_t select_sample;
+    double bits_per_arc;       /* (bits_A + bits_O) / arcs                                  */
+} lg_stats;
+
+/* Read-only device views of the encoded arrays, for inspection and parity
+   checks.  Each stream is u64 words, zero padded to an even count, followed by
+   two zero guard words; `words_*` counts all of them. */
+typedef struct {
+    const uint64_t *A;         uint64_t words_A;
+    const uint64_t *O;         uint64_t words_O;         /* packed offsets or CSR row_ptr */
+    const uint64_t *ef_low;    uint64_t words_ef_low;
+    const uint64_t *ef_high;   uint64_t words_ef_high;
+    const uint64_t *ef_samples; uint64_t words_ef_samples;
+    const uint32_t *perm;      /* original -> stored label, NULL without relabel */
+    const uint32_t *inv_perm;  /* stored -> original label, NULL without relabel */
+} lg_arrays;
+
+/*
+ * lg_encode -- build the logarithmized graph from a CSR adjacency array.
+ * Paper: the construction of Listing 3 (Section 6): permute (DM, Section 5.6),
+ * transform A (Sections 3.2-3.6), build and logarithmize O (Sections 3.4, 4.3).
+ *   row_ptr  device, n+1 u64, row_ptr[0] = 0, nondecreasing, row_ptr[n] = arcs
+ *   col      device, arcs u32, each row strictly increasing, every value < n
+ *   weights  device, arcs u32 or NULL; a weight must fit weight_bits when given.
+ *            Weights need LG_ID_GLOBAL or LG_ID_CSR32 (else LG_EUNSUPPORTED).
+ *   n        1 <= n <= 2^32 - 1
+ *   opts     host; NULL means {LG_ID_GLOBAL, LG_OFF_PACKED, 0, 512, 0, 0}
+ *   out      host; receives the new graph (NULL on error)
+ * The inputs are read on `stream` and may be freed once the call returns.  The
+ * call synchronizes `stream` (validation result, sizes).  An invalid CSR gives
+ * LG_EINVAL.  The graph models an undirected graph (Section 2.1): BFS and
+ * PageRank assume every arc has its reverse; set LG_FLAG_CHECK_SYMMETRIC to
+ * have that verified.
+ */
+lg_status lg_encode(const uint64_t *row_ptr, const uint32_t *col, const uint32_t *weights,
+                    uint64_t n, uint64_t arcs, const lg_encode_opts *opts, void *stream,
+                    lg_graph **out);
+
+/* lg_stats_get -- sizes and widths of an encoded graph.  `out` host.  No GPU work. */
+lg_status lg_stats_get(const lg_graph *g, lg_stats *out);
+
+/* lg_arrays_get -- device pointers to the encoded arrays (owned by g; valid
+   until lg_free).  `out` host.  No GPU work. */
+lg_status lg_arrays_get(const lg_graph *g, lg_arrays *out);
+
+/*
+ * lg_neighbors -- decode N_v for a list of vertices (getNeighbors of Listing 3,
+ * the edge and neighborhood access of Section 3.7.2, the degree of 3.7.3).
+ *   vertices     device, k u32 original IDs (< n; repeats allowed)
+ *   out_offsets  device, k+1 u64: out_offsets[i] .. out_offsets[i+1] is the
+ *                slice of out_ids holding N_{vertices[i]}; always written
+ *   out_ids      device, out_capacity u32: neighbors as original IDs, each
+ *                slice ascending (equal to the input CSR row)
+ *   out_weights  device, out_capacity u32, or NULL (weighted graphs only)
+ * If the total degree exceeds out_capacity the call writes out_offsets, leaves
+ * out_ids untouched and returns LG_ERANGE (call again with a larger buffer).
+ * A vertex >= n gives LG_EINVAL.  Synchronizes `stream` once (to read the
+ * total size) and again at the end.
+ */
+lg_status lg_neighbors(const lg_graph *g, const uint32_t *vertices, uint64_t k,
+                       uint64_t *out_offsets, uint32_t *out_ids, uint32_t *out_weights,
+                       uint64_t out_capacity, void *stream);
+
+/*
+ * lg_bfs -- breadth-first search from S sources (Section 7.1.2, a
+ * direction-optimizing, level-synchronous BFS), decoding the compressed
+ * neighborhoods inside the traversal kernels.  Sources are processed as
+ * bit-parallel multi-source sweeps of up to 64 sources each.
+ *   sources  device, S u32 original IDs (< n)
+ *   depths   device, S*n u32, row-major by source: depths[i*n + v] = number of
+ *            edges on a shortest path from sources[i] to v, UINT32_MAX if v is
+ *            unreachable (ties do not matter: depths are unique)
+ * Synchronizes `stream` once per BFS level (frontier sizes steer the
+ * direction).  A source >= n gives LG_EINVAL.
+ */
+lg_status lg_bfs(const lg_graph *g, const uint32_t *sources, uint32_t S, uint32_t *depths,
+                 void *stream);
+
+/*
+ * lg_pagerank -- pull PageRank without atomics (Section 7.1.2), FP32, exactly
+ * `iters` iterations, neighborhoods decoded inside the kernel:
+ *   global:        r_0 = 1/n,    r_t[v] = (1-d)/n      + d * sum_{u in N_v} r_{t-1}[u] / d_u
+ *   personalized:  r_0 = e_s,    r_t[v] = (1-d)*[v==s] + d * sum_{u in N_v} r_{t-1}[u] / d_u
+ * Vertices of degree 0 keep the teleport term only (no dangling mass).
+ *   damping             d in [0, 1]
+ *   personalize_source  host pointer to one u32 original ID s, or NULL for global
+ *   ranks               device, n floats indexed by original ID
+ * Asynchronous: returns once the work is enqueued (argument errors return
+ * before any GPU work).
+ */
+lg_status lg_pagerank(const lg_graph *g, float damping, uint32_t iters,
+                      const uint32_t *personalize_source, float *ranks, void *stream);
+
+/* lg_free -- release a graph and all of its device memory.  NULL-safe.  The
+   caller must make sure no enqueued work still uses g. */
+void lg_free(lg_graph *g);
+
+/* lg_kernel_launches -- number of CUDA kernels this library has launched in
+   this process so far (all threads, all devices).  For instrumentation: the
+   difference across a region counts the library's launches in it.  No GPU work. */
+uint64_t lg_kernel_launches(void);
+
+/* lg_last_error -- message describing the last failure on this thread ("" if
+   none).  The pointer stays valid until the next lg_* call on this thread. */
+const char *lg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LG_H */

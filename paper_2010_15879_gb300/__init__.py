@@ -1,0 +1,266 @@
+"""GB300 Log(Graph): Python binding of liblg.so.
+
+The functions here carry the names of the C ABI in ``include/lg.h`` and do
+argument marshalling only: every step of the encoder and of the graph kernels
+runs in the CUDA library.  PyTorch provides device memory and streams.  There is
+no CPU fallback: if liblg.so is missing or no GPU is present, the calls raise.
+
+Quick use::
+
+    import torch, paper_2010_15879_gb300 as lg
+    g = lg.lg_encode(row_ptr_cuda_u64, col_cuda_u32, id_mode=lg.LG_ID_LOCAL_GAP,
+                     off_mode=lg.LG_OFF_EF, relabel=True)
+    depths = lg.lg_bfs(g, sources_cuda_u32)          # (S, n) uint32 as int32
+    ranks = lg.lg_pagerank(g, 0.85, 20)              # (n,) float32
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+import torch
+
+from ._build import LIB, build, is_stale
+
+__all__ = [
+    "LG_ID_GLOBAL", "LG_ID_LOCAL", "LG_ID_LOCAL_GAP", "LG_ID_CSR32", "LG_OFF_PACKED", "LG_OFF_EF",
+    "LgError", "LogGraph", "build", "load", "lg_encode", "lg_stats_get", "lg_arrays_get", "lg_neighbors",
+    "lg_bfs", "lg_pagerank", "lg_free", "lg_last_error", "lg_kernel_launches",
+]
+
+LG_ID_GLOBAL, LG_ID_LOCAL, LG_ID_LOCAL_GAP, LG_ID_CSR32 = 0, 1, 2, 3
+LG_OFF_PACKED, LG_OFF_EF = 0, 1
+LG_FLAG_CHECK_SYMMETRIC = 1
+STATUS = {0: "LG_OK", 1: "LG_EINVAL", 2: "LG_ENOMEM", 3: "LG_ECUDA", 4: "LG_ERANGE", 5: "LG_ETIMEOUT",
+          6: "LG_EUNSUPPORTED"}
+
+_u64, _u32, _i32, _f32, _dbl, _vp = (ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_float,
+                                     ctypes.c_double, ctypes.c_void_p)
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("id_mode", _u32), ("off_mode", _u32), ("relabel", _u32), ("select_sample", _u32),
+                ("weight_bits", _u32), ("flags", _u32)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("n", _u64), ("arcs", _u64), ("bits_A", _u64), ("bits_O", _u64), ("bytes_A", _u64),
+                ("bytes_O", _u64), ("bytes_perm", _u64), ("bytes_total", _u64), ("max_degree", _u64),
+                ("id_mode", _u32), ("off_mode", _u32), ("relabel", _u32), ("weighted", _u32), ("s", _u32),
+                ("H", _u32), ("omega", _u32), ("w_O", _u32), ("ef_l", _u32), ("select_sample", _u32),
+                ("bits_per_arc", _dbl)]
+
+
+class _Arrays(ctypes.Structure):
+    _fields_ = [("A", _vp), ("words_A", _u64), ("O", _vp), ("words_O", _u64), ("ef_low", _vp),
+                ("words_ef_low", _u64), ("ef_high", _vp), ("words_ef_high", _u64), ("ef_samples", _vp),
+                ("words_ef_samples", _u64), ("perm", _vp), ("inv_perm", _vp)]
+
+
+class LgError(RuntimeError):
+    def __init__(self, status: int, what: str, msg: str):
+        super().__init__(f"{what} -> {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(auto_build: bool = False):
+    """Load liblg.so (building it first only when ``auto_build``)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if auto_build and is_stale():
+            build()
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"{LIB} is not built: run paper_2010_15879_gb300.build() (nvcc, sm_103a)")
+        h = ctypes.CDLL(LIB)
+        h.lg_encode.argtypes = [_vp, _vp, _vp, _u64, _u64, ctypes.POINTER(_Opts), _vp, ctypes.POINTER(_vp)]
+        h.lg_stats_get.argtypes = [_vp, ctypes.POINTER(_Stats)]
+        h.lg_arrays_get.argtypes = [_vp, ctypes.POINTER(_Arrays)]
+        h.lg_neighbors.argtypes = [_vp, _vp, _u64, _vp, _vp, _vp, _u64, _vp]
+        h.lg_bfs.argtypes = [_vp, _vp, _u32, _vp, _vp]
+        h.lg_pagerank.argtypes = [_vp, _f32, _u32, ctypes.POINTER(_u32), _vp, _vp]
+        h.lg_free.argtypes = [_vp]
+        h.lg_free.restype = None
+        h.lg_last_error.restype = ctypes.c_char_p
+        h.lg_kernel_launches.argtypes = []
+        h.lg_kernel_launches.restype = _u64
+        for f in ("lg_encode", "lg_stats_get", "lg_arrays_get", "lg_neighbors", "lg_bfs", "lg_pagerank"):
+            getattr(h, f).restype = _i32
+        _lib = h
+    return _lib
+
+
+def lg_last_error() -> str:
+    return load().lg_last_error().decode()
+
+
+def lg_kernel_launches() -> int:
+    """Kernels launched by liblg.so in this process so far."""
+    return int(load().lg_kernel_launches())
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        raise LgError(status, what, lg_last_error())
+
+
+def _stream(stream) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _dev(t: torch.Tensor, dtype: torch.dtype, name: str) -> torch.Tensor:
+    """Device-resident contiguous tensor of the given dtype (host tensors are copied)."""
+    if not isinstance(t, torch.Tensor):
+        t = torch.as_tensor(np.ascontiguousarray(t))
+    if t.dtype != dtype:
+        if t.element_size() != torch.empty(0, dtype=dtype).element_size():
+            raise TypeError(f"{name}: expected {dtype}, got {t.dtype}")
+        t = t.view(dtype)
+    if not t.is_cuda:
+        t = t.to("cuda", non_blocking=True)
+    return t.contiguous()
+
+
+class LogGraph:
+    """Owner of an lg_graph handle (freed with lg_free)."""
+
+    def __init__(self, handle: int, keepalive=()):
+        self._h = _vp(handle)
+        self._keep = keepalive
+
+    @property
+    def handle(self):
+        return self._h
+
+    def stats(self) -> dict:
+        return lg_stats_get(self)
+
+    def free(self):
+        if self._h is not None and self._h.value:
+            lg_free(self)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def lg_encode(row_ptr, col, weights=None, *, id_mode: int = LG_ID_GLOBAL, off_mode: int = LG_OFF_PACKED,
+              relabel: bool = False, select_sample: int = 512, weight_bits: int = 0,
+              check_symmetric: bool = False, stream=None) -> LogGraph:
+    """lg_encode: build the logarithmized graph from a CSR (row_ptr uint64[n+1],
+    col uint32[arcs], optional weights uint32[arcs]; int64/int32 tensors are
+    reinterpreted).  Host tensors are copied to the current device first."""
+    lib = load()
+    rp = _dev(row_ptr, torch.int64, "row_ptr")
+    cl = _dev(col, torch.int32, "col")
+    wt = None if weights is None else _dev(weights, torch.int32, "weights")
+    n = rp.numel() - 1
+    opts = _Opts(id_mode, off_mode, int(bool(relabel)), select_sample, weight_bits,
+                 LG_FLAG_CHECK_SYMMETRIC if check_symmetric else 0)
+    h = _vp()
+    st = _stream(stream)
+    _check(lib.lg_encode(rp.data_ptr(), cl.data_ptr() if cl.numel() else None,
+                         None if wt is None else wt.data_ptr(), n, cl.numel(), ctypes.byref(opts), st,
+                         ctypes.byref(h)), "lg_encode")
+    return LogGraph(h.value)
+
+
+def lg_free(g: LogGraph) -> None:
+    load().lg_free(g.handle)
+
+
+def lg_stats_get(g: LogGraph) -> dict:
+    s = _Stats()
+    _check(load().lg_stats_get(g.handle, ctypes.byref(s)), "lg_stats_get")
+    return {k: getattr(s, k) for k, _ in _Stats._fields_}
+
+
+class _DevView:
+    """__cuda_array_interface__ over library-owned device memory (read-only use)."""
+
+    def __init__(self, ptr: int, count: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (count,), "typestr": typestr, "data": (ptr, False),
+                                         "version": 3, "strides": None}
+
+
+def lg_arrays_get(g: LogGraph) -> dict:
+    """Host (numpy) copies of the encoded arrays: uint64 word streams (with
+    padding and guard words) and the uint32 permutation if relabeled."""
+    a = _Arrays()
+    _check(load().lg_arrays_get(g.handle, ctypes.byref(a)), "lg_arrays_get")
+    n = lg_stats_get(g)["n"]
+    out = {}
+    torch.cuda.synchronize()
+    for name in ("A", "O", "ef_low", "ef_high", "ef_samples"):
+        ptr, cnt = getattr(a, name), getattr(a, "words_" + name)
+        if ptr and cnt:
+            t = torch.as_tensor(_DevView(ptr, cnt, "<i8"), device="cuda")
+            out[name] = t.cpu().numpy().view(np.uint64).copy()
+        else:
+            out[name] = np.zeros(0, dtype=np.uint64)
+    for name in ("perm", "inv_perm"):
+        ptr = getattr(a, name)
+        if ptr:
+            t = torch.as_tensor(_DevView(ptr, n, "<i4"), device="cuda")
+            out[name] = t.cpu().numpy().view(np.uint32).copy()
+        else:
+            out[name] = np.zeros(0, dtype=np.uint32)
+    return out
+
+
+def lg_neighbors(g: LogGraph, vertices, with_weights: bool = False, stream=None):
+    """lg_neighbors: (offsets int64[k+1], ids uint32-as-int32[total][, weights])
+    for the given original vertex IDs; each slice ascending."""
+    lib = load()
+    vs = _dev(vertices, torch.int32, "vertices")
+    k = vs.numel()
+    st = _stream(stream)
+    off = torch.empty(k + 1, dtype=torch.int64, device="cuda")
+    vptr = vs.data_ptr() if k else None
+    rc = lib.lg_neighbors(g.handle, vptr, k, off.data_ptr(), None, None, 0, st)
+    if rc not in (0, 4):
+        _check(rc, "lg_neighbors")
+    total = int(off[-1].item())
+    ids = torch.empty(max(total, 1), dtype=torch.int32, device="cuda")
+    wts = torch.empty(max(total, 1), dtype=torch.int32, device="cuda") if with_weights else None
+    _check(lib.lg_neighbors(g.handle, vptr, k, off.data_ptr(), ids.data_ptr(),
+                            None if wts is None else wts.data_ptr(), total, st), "lg_neighbors")
+    ids = ids[:total]
+    return (off, ids, wts[:total]) if with_weights else (off, ids)
+
+
+def lg_bfs(g: LogGraph, sources, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """lg_bfs: depths (S, n) as int32 holding uint32 values (UINT32_MAX = -1:
+    unreachable)."""
+    lib = load()
+    src = _dev(sources, torch.int32, "sources")
+    S = src.numel()
+    n = lg_stats_get(g)["n"]
+    if out is None:
+        out = torch.empty((S, n), dtype=torch.int32, device="cuda")
+    _check(lib.lg_bfs(g.handle, src.data_ptr() if S else None, S, out.data_ptr(), _stream(stream)), "lg_bfs")
+    return out
+
+
+def lg_pagerank(g: LogGraph, damping: float = 0.85, iters: int = 20, personalize: Optional[int] = None,
+                out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """lg_pagerank: FP32 ranks (n,) indexed by original vertex ID."""
+    lib = load()
+    n = lg_stats_get(g)["n"]
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, device="cuda")
+    ps = None if personalize is None else ctypes.byref(_u32(personalize))
+    _check(lib.lg_pagerank(g.handle, damping, iters, ps, out.data_ptr(), _stream(stream)), "lg_pagerank")
+    return out

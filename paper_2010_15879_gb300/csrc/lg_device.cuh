@@ -1,0 +1,191 @@
+// Device-side building blocks shared by the encoder and the traversal kernels.
+//
+// Bit order (Listing 2, Section 3.7.2 of the Log(Graph) paper): a stream is an
+// array of little-endian words; a w-bit field at bit position p holds value
+// bit k at stream bit p + k.  On a little-endian GPU the same memory read as
+// 32-bit or 64-bit words gives the same bit positions, so the decoders read
+// 32-bit words and use one funnel shift per field.
+//
+// Every stream allocation is padded to an even number of u64 words and
+// followed by two zero guard words, so any read of word i+1 (or of the 16-byte
+// chunk holding word i) for a data word i stays inside the allocation.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define LG_FULL_MASK 0xffffffffu
+
+namespace lg {
+
+enum IdMode : int { ID_GLOBAL = 0, ID_LOCAL = 1, ID_LOCAL_GAP = 2, ID_CSR32 = 3 };
+enum OffMode : int { OFF_PACKED = 0, OFF_EF = 1, OFF_ROWPTR = 2 };
+
+// Device error flag bits (combined with atomicOr; read back by the host).
+enum DevErr : int {
+  DERR_ROWPTR = 1,      // row_ptr not monotone / out of range
+  DERR_COL_RANGE = 2,   // neighbor id >= n
+  DERR_UNSORTED = 4,    // row not strictly increasing
+  DERR_WEIGHT = 8,      // weight does not fit the requested width
+  DERR_ASYM = 16,       // an arc without its reverse
+  DERR_QUERY = 32,      // query vertex >= n
+  DERR_INTERNAL = 64,   // a structural invariant did not hold (bounded loop ran out)
+};
+
+// Read-only view of an encoded graph, passed by value to kernels.
+struct GView {
+  const uint32_t* A32;        // A stream as 32-bit words (CSR32: the col array)
+  const uint64_t* A64;        // same memory as 64-bit words
+  const uint64_t* O;          // packed offsets (PACKED) or row_ptr (ROWPTR)
+  const uint64_t* ef_low;
+  const uint32_t* ef_high32;  // EF high bits as 32-bit words
+  const uint64_t* ef_samples;
+  const uint32_t* perm;       // original -> stored (nullptr without relabel)
+  const uint32_t* inv_perm;   // stored -> original
+  const uint32_t* W32;        // CSR32 only: 32-bit weights beside the IDs (nullptr if none)
+  uint64_t n, arcs;
+  uint64_t ef_high_words32;   // number of valid 32-bit words of the high vector
+  uint32_t s, H, omega, r, w_O, ef_l, sample_log2;
+};
+
+__device__ __forceinline__ uint32_t bits_u32(uint32_t x) { return 32u - __clz(x); }
+__device__ __forceinline__ uint32_t bits_u64(uint64_t x) { return 64u - __clzll(x); }
+
+__device__ __forceinline__ uint32_t mask_lo(uint32_t w) { return w >= 32 ? 0xffffffffu : ((1u << w) - 1u); }
+
+// w <= 32 bit field at bit p of a 32-bit word stream.
+__device__ __forceinline__ uint32_t ext32(const uint32_t* __restrict__ A, uint64_t p, uint32_t w) {
+  const uint64_t wi = p >> 5;
+  const uint32_t lo = __ldg(A + wi);
+  const uint32_t hi = __ldg(A + wi + 1);
+  return __funnelshift_r(lo, hi, (uint32_t)p & 31u) & mask_lo(w);
+}
+
+// w <= 64 bit field at bit p of a 64-bit word stream.
+__device__ __forceinline__ uint64_t ext64(const uint64_t* __restrict__ A, uint64_t p, uint32_t w) {
+  const uint64_t wi = p >> 6;
+  const uint32_t sh = (uint32_t)p & 63u;
+  const uint64_t lo = __ldg(A + wi);
+  const uint64_t hi = __ldg(A + wi + 1);
+  const uint64_t v = sh ? ((lo >> sh) | (hi << (64u - sh))) : lo;
+  return w >= 64 ? v : (v & ((1ull << w) - 1ull));
+}
+
+// Position (0..31) of the r-th set bit (0-based) of x; requires r < popc(x).
+__device__ __forceinline__ uint32_t select_in_u32(uint32_t x, uint32_t r) {
+  uint32_t pos = 0, c;
+  c = __popc(x & 0xffffu); if (r >= c) { r -= c; x >>= 16; pos += 16; }
+  c = __popc(x & 0xffu);   if (r >= c) { r -= c; x >>= 8;  pos += 8; }
+  c = __popc(x & 0xfu);    if (r >= c) { r -= c; x >>= 4;  pos += 4; }
+  c = __popc(x & 0x3u);    if (r >= c) { r -= c; x >>= 2;  pos += 2; }
+  c = x & 1u;              if (r >= c) { pos += 1; }
+  return pos;
+}
+
+// 128-bit read-only load (address must be 16-byte aligned).
+__device__ __forceinline__ uint4 ldg128(const uint32_t* p) { return __ldg(reinterpret_cast<const uint4*>(p)); }
+
+// ---------------------------------------------------------------------------
+// Sequential bit reader: one thread walks a run of fields.  Refills 32 bits at
+// a time from a 16-byte register chunk, so a warp whose lanes walk different
+// runs issues one 128-bit load per ~128 bits consumed per lane.
+// ---------------------------------------------------------------------------
+struct BitReader {
+  const uint32_t* A;
+  uint64_t wnext;     // index of the next 32-bit word to append to buf
+  uint64_t buf;       // unread bits, LSB first
+  uint32_t nb;        // number of valid bits in buf
+  uint4 q;            // words wnext.. of the current 16-byte chunk (shifted down)
+  uint32_t nq;        // valid words in q
+
+  __device__ __forceinline__ void load_chunk() {
+    const uint64_t c = wnext & ~3ull;
+    uint4 v = ldg128(A + c);
+    const uint32_t skip = (uint32_t)(wnext - c);
+    // drop words before wnext
+    if (skip >= 1) { v.x = v.y; v.y = v.z; v.z = v.w; }
+    if (skip >= 2) { v.x = v.y; v.y = v.z; }
+    if (skip >= 3) { v.x = v.y; }
+    q = v;
+    nq = 4u - skip;
+  }
+  __device__ __forceinline__ void push_word() {
+    if (nq == 0) load_chunk();
+    buf |= (uint64_t)q.x << nb;
+    nb += 32;
+    q.x = q.y; q.y = q.z; q.z = q.w;
+    nq--;
+    wnext++;
+  }
+  __device__ __forceinline__ void init(const uint32_t* base, uint64_t bit) {
+    A = base;
+    wnext = bit >> 5;
+    buf = 0; nb = 0; nq = 0;
+    push_word();
+    const uint32_t sh = (uint32_t)bit & 31u;
+    buf >>= sh;
+    nb -= sh;
+  }
+  // w <= 32
+  __device__ __forceinline__ uint32_t get(uint32_t w) {
+    if (nb < w) push_word();
+    const uint32_t v = (uint32_t)buf & mask_lo(w);
+    buf = (w >= 64) ? 0 : (buf >> w);
+    nb -= w;
+    return v;
+  }
+  __device__ __forceinline__ void skip(uint32_t w) { (void)get(w); }
+};
+
+// ---------------------------------------------------------------------------
+// warp / block scans
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T x) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T y = __shfl_up_sync(LG_FULL_MASK, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(LG_FULL_MASK, x, o);
+  return x;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_or(T x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x |= __shfl_xor_sync(LG_FULL_MASK, x, o);
+  return x;
+}
+
+// Exclusive scan over a block of NT threads; `tmp` holds NT/32 elements of
+// shared memory.  Returns the exclusive prefix and the block total.
+template <typename T, int NT>
+__device__ __forceinline__ T block_excl_scan(T v, T& total, T* tmp) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  constexpr int NW = NT / 32;
+  T x = warp_incl_scan(v);
+  if (lane == 31) tmp[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    T w = lane < NW ? tmp[lane] : T(0);
+    w = warp_incl_scan(w);
+    if (lane < NW) tmp[lane] = w;
+  }
+  __syncthreads();
+  const T pre = (wid > 0 ? tmp[wid - 1] : T(0)) + x - v;
+  total = tmp[NW - 1];
+  __syncthreads();
+  return pre;
+}
+
+__device__ __forceinline__ void set_err(int* err, int bit) { atomicOr(err, bit); }
+
+}  // namespace lg

@@ -1,0 +1,399 @@
+// Encoder kernels: input validation, per-neighborhood widths (Sections 3.2.2
+// and 3.6), the prefix sum of bit lengths, bit packing of A (Sections 3.2-3.3,
+// bit order of Listing 2) and of the offsets (Section 3.4, packed; Section 4.3,
+// Elias-Fano with select samples).
+//
+// Packing is word-owned: every output word is assembled by exactly one thread
+// (fixed-width streams) or one CTA (variable-width local streams, assembled in
+// shared memory), so no global atomics touch A and the result is deterministic.
+#include "lg_internal.h"
+
+namespace lg {
+
+// =========================================================================
+// exclusive scan (u32 or u64 input, u64 output with the total at out[n])
+// =========================================================================
+constexpr int SCAN_NT = 256;
+constexpr int SCAN_IPT = 8;
+constexpr int SCAN_TILE = SCAN_NT * SCAN_IPT;
+
+uint64_t scan_tmp_words(uint64_t n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 2; }
+
+template <typename T>
+__global__ void __launch_bounds__(SCAN_NT) k_scan_reduce(const T* __restrict__ in, uint64_t n,
+                                                         uint64_t* __restrict__ part) {
+  __shared__ uint64_t tmp[SCAN_NT / 32];
+  const uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE;
+  uint64_t s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_IPT; k++) {
+    const uint64_t i = base + (uint64_t)k * SCAN_NT + threadIdx.x;
+    if (i < n) s += (uint64_t)in[i];
+  }
+  uint64_t total;
+  block_excl_scan<uint64_t, SCAN_NT>(s, total, tmp);
+  if (threadIdx.x == 0) part[blockIdx.x] = total;
+}
+
+// single block: exclusive scan of the tile partials in place, total at part[np]
+__global__ void __launch_bounds__(SCAN_NT) k_scan_partials(uint64_t* part, uint64_t np) {
+  __shared__ uint64_t tmp[SCAN_NT / 32];
+  uint64_t carry = 0;
+  for (uint64_t base = 0; base < np; base += SCAN_TILE) {
+    uint64_t v[SCAN_IPT];
+    uint64_t s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_IPT; k++) {
+      const uint64_t i = base + (uint64_t)threadIdx.x * SCAN_IPT + k;
+      v[k] = i < np ? part[i] : 0;
+      s += v[k];
+    }
+    uint64_t total;
+    uint64_t pre = block_excl_scan<uint64_t, SCAN_NT>(s, total, tmp) + carry;
+#pragma unroll
+    for (int k = 0; k < SCAN_IPT; k++) {
+      const uint64_t i = base + (uint64_t)threadIdx.x * SCAN_IPT + k;
+      if (i < np) part[i] = pre;
+      pre += v[k];
+    }
+    carry += total;
+  }
+  if (threadIdx.x == 0) part[np] = carry;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(SCAN_NT) k_scan_down(const T* __restrict__ in, uint64_t n,
+                                                       const uint64_t* __restrict__ part,
+                                                       uint64_t np, uint64_t* __restrict__ out) {
+  __shared__ uint64_t tmp[SCAN_NT / 32];
+  const uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE;
+  uint64_t v[SCAN_IPT];
+  uint64_t s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_IPT; k++) {
+    const uint64_t i = base + (uint64_t)threadIdx.x * SCAN_IPT + k;
+    v[k] = i < n ? (uint64_t)in[i] : 0;
+    s += v[k];
+  }
+  uint64_t total;
+  uint64_t pre = block_excl_scan<uint64_t, SCAN_NT>(s, total, tmp) + part[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < SCAN_IPT; k++) {
+    const uint64_t i = base + (uint64_t)threadIdx.x * SCAN_IPT + k;
+    if (i < n) out[i] = pre;
+    pre += v[k];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = part[np];
+}
+
+template <typename T>
+static cudaError_t scan_impl(const T* in, uint64_t n, uint64_t* out, uint64_t* tmp, cudaStream_t st) {
+  const uint64_t np = (n + SCAN_TILE - 1) / SCAN_TILE;
+  if (np == 0) return cudaMemsetAsync(out, 0, sizeof(uint64_t), st);
+  k_scan_reduce<T><<<(unsigned)np, SCAN_NT, 0, st>>>(in, n, tmp);
+  count_launch();
+  k_scan_partials<<<1, SCAN_NT, 0, st>>>(tmp, np);
+  count_launch();
+  k_scan_down<T><<<(unsigned)np, SCAN_NT, 0, st>>>(in, n, tmp, np, out);
+  count_launch();
+  return cudaGetLastError();
+}
+cudaError_t scan_excl_u64(const uint64_t* in, uint64_t n, uint64_t* out, uint64_t* tmp, cudaStream_t st) {
+  return scan_impl<uint64_t>(in, n, out, tmp, st);
+}
+cudaError_t scan_excl_u32(const uint32_t* in, uint64_t n, uint64_t* out, uint64_t* tmp, cudaStream_t st) {
+  return scan_impl<uint32_t>(in, n, out, tmp, st);
+}
+
+// =========================================================================
+// validation (one warp per row; never reads outside the given arrays)
+// =========================================================================
+__global__ void __launch_bounds__(256) k_validate(const uint64_t* __restrict__ rp, const uint32_t* __restrict__ col,
+                                                  const uint32_t* __restrict__ w, uint64_t n, uint64_t arcs,
+                                                  uint32_t wbits, int* err, unsigned long long* max_deg,
+                                                  uint32_t* max_w) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  uint32_t wmax = 0;
+  int flags = 0;
+  for (uint64_t v = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); v < n; v += warps) {
+    const uint64_t lo = rp[v], hi = rp[v + 1];
+    const bool bad = hi < lo || hi > arcs || (v == 0 && lo != 0) || (v == n - 1 && hi != arcs);
+    if (bad) { flags |= DERR_ROWPTR; continue; }
+    if (lane == 0) atomicMax(max_deg, (unsigned long long)(hi - lo));
+    for (uint64_t j = lo + lane; j < hi; j += 32) {
+      const uint32_t c = col[j];
+      if (c >= n) flags |= DERR_COL_RANGE;
+      if (j > lo && col[j - 1] >= c) flags |= DERR_UNSORTED;
+      if (w) {
+        const uint32_t x = w[j];
+        wmax = max(wmax, x);
+        if (wbits && wbits < 32 && (x >> wbits)) flags |= DERR_WEIGHT;
+      }
+    }
+  }
+  flags = __reduce_or_sync(LG_FULL_MASK, flags);
+  wmax = __reduce_max_sync(LG_FULL_MASK, wmax);
+  if (lane == 0) {
+    if (flags) atomicOr(err, flags);
+    if (w) atomicMax(max_w, wmax);
+  }
+}
+
+cudaError_t enc_validate(const uint64_t* rp, const uint32_t* col, const uint32_t* w, uint64_t n, uint64_t arcs,
+                         uint32_t wbits, int* err, unsigned long long* max_deg, uint32_t* max_w, cudaStream_t st) {
+  k_validate<<<grid_for(n, 8, 152 * 64), 256, 0, st>>>(rp, col, w, n, arcs, wbits, err, max_deg, max_w);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// every arc (v, u) needs the arc (u, v): binary search of v in row u
+__global__ void __launch_bounds__(256) k_check_sym(const uint64_t* __restrict__ rp, const uint32_t* __restrict__ col,
+                                                   uint64_t n, int* err) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  int flags = 0;
+  for (uint64_t v = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); v < n; v += warps) {
+    for (uint64_t j = rp[v] + lane; j < rp[v + 1]; j += 32) {
+      const uint32_t u = col[j];
+      uint64_t lo = rp[u], hi = rp[u + 1];
+      while (lo < hi) {
+        const uint64_t mid = (lo + hi) >> 1;
+        if (col[mid] < v) lo = mid + 1; else hi = mid;
+      }
+      if (lo == rp[u + 1] || col[lo] != v) flags |= DERR_ASYM;
+    }
+  }
+  flags = __reduce_or_sync(LG_FULL_MASK, flags);
+  if (lane == 0 && flags) atomicOr(err, flags);
+}
+
+cudaError_t enc_check_symmetric(const uint64_t* rp, const uint32_t* col, uint64_t n, int* err, cudaStream_t st) {
+  k_check_sym<<<grid_for(n, 8, 152 * 64), 256, 0, st>>>(rp, col, n, err);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// =========================================================================
+// local widths: w_v = max(1, bits(maxN_v)) (Section 3.2.2) or
+// g_v = max(1, bits(max gap)) (Section 3.6); len_v = bits of the neighborhood
+// =========================================================================
+__global__ void __launch_bounds__(256) k_local_lengths(const uint64_t* __restrict__ rp,
+                                                       const uint32_t* __restrict__ col, uint64_t n, int gap,
+                                                       uint32_t s, uint32_t H, uint8_t* __restrict__ wid,
+                                                       uint64_t* __restrict__ len) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t v = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); v < n; v += warps) {
+    const uint64_t lo = rp[v], hi = rp[v + 1], d = hi - lo;
+    uint32_t w = 0;
+    if (!gap) {
+      if (d > 0) w = max(1u, bits_u32(col[hi - 1]));
+    } else if (d >= 2) {
+      uint32_t mg = 0;
+      for (uint64_t j = lo + 1 + lane; j < hi; j += 32) mg = max(mg, col[j] - col[j - 1]);
+      mg = __reduce_max_sync(LG_FULL_MASK, mg);
+      w = max(1u, bits_u32(mg));
+    }
+    if (lane == 0) {
+      wid[v] = (uint8_t)w;
+      len[v] = gap ? (uint64_t)H + (d >= 1 ? s : 0) + (d >= 2 ? (d - 1) * (uint64_t)w : 0)
+                   : (uint64_t)H + d * (uint64_t)w;
+    }
+  }
+}
+
+cudaError_t enc_local_lengths(const uint64_t* rp, const uint32_t* col, uint64_t n, int gap, uint32_t s, uint32_t H,
+                              uint8_t* wid, uint64_t* len, cudaStream_t st) {
+  k_local_lengths<<<grid_for(n, 8, 152 * 64), 256, 0, st>>>(rp, col, n, gap, s, H, wid, len);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// =========================================================================
+// fixed-width packing: record j = [id : s][weight : omega] at bit j * r
+// (Sections 3.2.1 and 3.3; the weight directly after the ID).  One thread
+// assembles one output word from the (at most 64/r + 2) records touching it.
+// =========================================================================
+__global__ void __launch_bounds__(256) k_pack_global(const uint32_t* __restrict__ col, const uint32_t* __restrict__ w,
+                                                     uint64_t arcs, uint32_t s, uint32_t omega,
+                                                     uint64_t* __restrict__ out, uint64_t data_words) {
+  const uint32_t r = s + omega;
+  for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < data_words;
+       k += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t b0 = k * 64;
+    const uint64_t j0 = b0 / r;
+    uint64_t j1 = (b0 + 63) / r;
+    if (j1 >= arcs) j1 = arcs - 1;
+    uint64_t acc = 0;
+    for (uint64_t j = j0; j <= j1; j++) {
+      uint64_t rec = (uint64_t)col[j];
+      if (w) rec |= (uint64_t)w[j] << s;
+      const int64_t off = (int64_t)(j * r) - (int64_t)b0;
+      acc |= off >= 0 ? (rec << off) : (rec >> (-off));
+    }
+    out[k] = acc;
+  }
+}
+
+cudaError_t enc_pack_global(const uint32_t* col, const uint32_t* w, uint64_t arcs, uint32_t s, uint32_t omega,
+                            uint64_t* out, uint64_t data_words, cudaStream_t st) {
+  if (data_words == 0) return cudaSuccess;
+  k_pack_global<<<grid_for(data_words, 256, 152 * 32), 256, 0, st>>>(col, w, arcs, s, omega, out, data_words);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// value j (u64, w <= 64 bits) at bit j * w
+__global__ void __launch_bounds__(256) k_pack_u64(const uint64_t* __restrict__ vals, uint64_t count, uint32_t wbits,
+                                                  uint64_t* __restrict__ out, uint64_t data_words) {
+  const uint64_t mask = wbits >= 64 ? ~0ull : ((1ull << wbits) - 1ull);
+  for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < data_words;
+       k += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t b0 = k * 64;
+    const uint64_t j0 = b0 / wbits;
+    uint64_t j1 = (b0 + 63) / wbits;
+    if (j1 >= count) j1 = count - 1;
+    uint64_t acc = 0;
+    for (uint64_t j = j0; j <= j1; j++) {
+      const uint64_t rec = vals[j] & mask;
+      const int64_t off = (int64_t)(j * wbits) - (int64_t)b0;
+      acc |= off >= 0 ? (rec << off) : (rec >> (-off));
+    }
+    out[k] = acc;
+  }
+}
+
+cudaError_t enc_pack_u64(const uint64_t* vals, uint64_t count, uint32_t w, uint64_t* out, uint64_t data_words,
+                         cudaStream_t st) {
+  if (data_words == 0 || w == 0) return cudaSuccess;
+  k_pack_u64<<<grid_for(data_words, 256, 152 * 32), 256, 0, st>>>(vals, count, w, out, data_words);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// =========================================================================
+// variable-width local packing (Sections 3.2.2 / 3.6): each CTA owns a window
+// of PW u64 output words, finds the neighborhoods overlapping it by binary
+// search on the bit offsets x, ORs the overlapping fields into shared memory
+// (clipped to the window) and writes the window out.  Differences are
+// independent of each other, so any field can be produced without a prefix.
+// =========================================================================
+constexpr int PW = 1024;
+
+__device__ __forceinline__ void put_clip(unsigned long long* win, uint64_t w0, uint64_t wcnt, uint64_t p,
+                                         uint32_t wbits, uint64_t val) {
+  if (wbits == 0) return;
+  const uint64_t q0 = p >> 6;
+  const uint32_t sh = (uint32_t)p & 63u;
+  if (q0 >= w0 && q0 < w0 + wcnt) atomicOr(&win[q0 - w0], (unsigned long long)(val << sh));
+  if (sh + wbits > 64) {
+    const uint64_t q1 = q0 + 1;
+    if (q1 >= w0 && q1 < w0 + wcnt) atomicOr(&win[q1 - w0], (unsigned long long)(val >> (64 - sh)));
+  }
+}
+
+__global__ void __launch_bounds__(256) k_pack_local(const uint64_t* __restrict__ rp, const uint32_t* __restrict__ col,
+                                                    const uint64_t* __restrict__ x, const uint8_t* __restrict__ wid,
+                                                    uint64_t n, int gap, uint32_t s, uint32_t H,
+                                                    uint64_t* __restrict__ out, uint64_t data_words) {
+  __shared__ unsigned long long win[PW];
+  __shared__ uint64_t vrange[2];
+  const uint64_t w0 = (uint64_t)blockIdx.x * PW;
+  const uint64_t wcnt = min((uint64_t)PW, data_words - w0);
+  const uint64_t b0 = w0 * 64, b1 = (w0 + wcnt) * 64;
+  for (int i = threadIdx.x; i < PW; i += blockDim.x) win[i] = 0;
+  if (threadIdx.x == 0) {
+    // last v with x[v] <= b0, and first v with x[v] >= b1 (x strictly increasing)
+    uint64_t lo = 0, hi = n;
+    while (lo < hi) { uint64_t m = (lo + hi + 1) >> 1; if (x[m] <= b0) lo = m; else hi = m - 1; }
+    vrange[0] = lo;
+    uint64_t a = lo, b = n;
+    while (a < b) { uint64_t m = (a + b) >> 1; if (x[m] < b1) a = m + 1; else b = m; }
+    vrange[1] = a;
+  }
+  __syncthreads();
+  const uint64_t vb = vrange[0], ve = vrange[1];
+  const int lane = threadIdx.x & 31, wid_ = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (uint64_t v = vb + wid_; v < ve && v < n; v += nw) {
+    const uint64_t lo = rp[v], d = rp[v + 1] - lo;
+    const uint32_t wv = wid[v];
+    const uint64_t base = x[v];
+    if (lane == 0) {
+      put_clip(win, w0, wcnt, base, H, wv);
+      if (gap && d >= 1) put_clip(win, w0, wcnt, base + H, s, col[lo]);
+    }
+    // fields k = 0.. of width wv starting at fs: IDs (local) or differences (gap)
+    const uint64_t fs = base + H + (gap ? s : 0);
+    const uint64_t nf = gap ? (d >= 1 ? d - 1 : 0) : d;
+    if (nf == 0 || wv == 0) continue;
+    const uint64_t klo = b0 > fs ? (b0 - fs) / wv : 0;
+    const uint64_t khi = min(nf, b1 > fs ? (b1 - fs + wv - 1) / wv : 0);
+    for (uint64_t k = klo + lane; k < khi; k += 32) {
+      const uint64_t val = gap ? (uint64_t)(col[lo + k + 1] - col[lo + k]) : (uint64_t)col[lo + k];
+      put_clip(win, w0, wcnt, fs + k * wv, wv, val);
+    }
+  }
+  __syncthreads();
+  for (uint64_t i = threadIdx.x; i < wcnt; i += blockDim.x) out[w0 + i] = win[i];
+}
+
+cudaError_t enc_pack_local(const uint64_t* rp, const uint32_t* col, const uint64_t* x, const uint8_t* wid, uint64_t n,
+                           int gap, uint32_t s, uint32_t H, uint64_t* out, uint64_t data_words, cudaStream_t st) {
+  if (data_words == 0) return cudaSuccess;
+  k_pack_local<<<grid_for(data_words, PW), 256, 0, st>>>(rp, col, x, wid, n, gap, s, H, out, data_words);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// =========================================================================
+// Elias-Fano (Section 4.3): one set bit per value at (x_i >> l) + i, and the
+// select samples S[k] = (x_{k*sample} >> l) + k*sample.  Each warp combines
+// the bits that fall into the same word before one atomicOr per word.
+// =========================================================================
+__global__ void __launch_bounds__(256) k_ef_high(const uint64_t* __restrict__ x, uint64_t N, uint32_t l,
+                                                 unsigned long long* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  for (uint64_t base = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~31ull; base < N;
+       base += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t i = base + lane;
+    const bool ok = i < N;
+    const uint64_t pos = ok ? (x[i] >> l) + i : 0;
+    const uint64_t word = ok ? pos >> 6 : ~0ull;
+    unsigned long long bit = ok ? (1ull << (pos & 63)) : 0ull;
+    // positions increase with i, so equal words are adjacent lanes: segmented OR
+    const uint64_t prev_word = __shfl_up_sync(LG_FULL_MASK, word, 1);
+    const bool head = lane == 0 || prev_word != word;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long b = __shfl_down_sync(LG_FULL_MASK, bit, o);
+      const uint64_t wd = __shfl_down_sync(LG_FULL_MASK, word, o);
+      if (lane + o < 32 && wd == word) bit |= b;
+    }
+    if (ok && head) atomicOr(&out[word], bit);
+  }
+}
+
+cudaError_t enc_ef_high(const uint64_t* x, uint64_t N, uint32_t l, uint64_t* out, cudaStream_t st) {
+  k_ef_high<<<grid_for(N, 256, 152 * 32), 256, 0, st>>>(x, N, l, reinterpret_cast<unsigned long long*>(out));
+  count_launch();
+  return cudaGetLastError();
+}
+
+__global__ void k_ef_samples(const uint64_t* __restrict__ x, uint64_t N, uint32_t l, uint32_t sample,
+                             uint64_t* __restrict__ out, uint64_t ns) {
+  for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < ns; k += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t i = k * sample;
+    if (i < N) out[k] = (x[i] >> l) + i;
+  }
+}
+
+cudaError_t enc_ef_samples(const uint64_t* x, uint64_t N, uint32_t l, uint32_t sample, uint64_t* out, uint64_t ns,
+                           cudaStream_t st) {
+  if (ns == 0) return cudaSuccess;
+  k_ef_samples<<<grid_for(ns, 256, 4096), 256, 0, st>>>(x, N, l, sample, out, ns);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace lg

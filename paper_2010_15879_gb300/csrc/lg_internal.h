@@ -1,0 +1,158 @@
+// Host-side internals of liblg.so: the graph object, the kernel launchers and
+// the argument blocks of the traversal kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "lg.h"
+#include "lg_device.cuh"
+
+struct lg_graph {
+  int device;
+  uint64_t n, arcs;
+  uint32_t id_mode, off_mode, relabel, weighted;
+  uint32_t s, H, omega, r, w_O, ef_l, sample, sample_log2;
+  uint64_t bits_A, bits_O;
+  uint64_t ef_N, ef_U, ef_low_bits, ef_high_bits, n_samples;
+  uint64_t max_degree;
+  uint64_t *A;          uint64_t words_A;
+  uint64_t *O;          uint64_t words_O;  // packed offsets, or row_ptr for CSR32
+  uint64_t *ef_low;     uint64_t words_ef_low;
+  uint64_t *ef_high;    uint64_t words_ef_high;
+  uint64_t *ef_samples; uint64_t words_ef_samples;
+  uint32_t *perm, *inv_perm;
+  uint32_t *W;          // CSR32 weights (nullptr otherwise)
+};
+
+namespace lg {
+
+// u64 words for `bits` payload bits: padded to an even count plus two guard words.
+inline uint64_t padded_words(uint64_t bits) {
+  uint64_t w = (bits + 63) / 64;
+  w += (w & 1);
+  return w + 2;
+}
+inline uint32_t host_bits(uint64_t x) {
+  uint32_t b = 0;
+  while (x) { b++; x >>= 1; }
+  return b;
+}
+inline unsigned grid_for(uint64_t items, unsigned per_block, unsigned cap = 1u << 30) {
+  uint64_t g = (items + per_block - 1) / per_block;
+  if (g == 0) g = 1;
+  if (g > cap) g = cap;
+  return (unsigned)g;
+}
+
+GView make_view(const lg_graph* g);
+
+// every kernel launch site calls this right after its <<<...>>> (instrumentation)
+void count_launch();
+
+// ------------------------------------------------------------------ scan
+// out[0] = 0, out[i+1] = out[i] + in[i] for i < n (n+1 outputs).  `tmp` needs
+// scan_tmp_words(n) u64 words.
+uint64_t scan_tmp_words(uint64_t n);
+cudaError_t scan_excl_u64(const uint64_t* in, uint64_t n, uint64_t* out, uint64_t* tmp, cudaStream_t st);
+cudaError_t scan_excl_u32(const uint32_t* in, uint64_t n, uint64_t* out, uint64_t* tmp, cudaStream_t st);
+
+// ------------------------------------------------------------------ sort
+// Stable LSD radix sort of (key, value) pairs on the low `key_bits` bits.
+// Buffers *_alt have the same size; the result ends in keys/vals.
+size_t radix_tmp_bytes(uint64_t n);
+cudaError_t radix_sort_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
+                           uint64_t n, uint32_t key_bits, void* tmp, cudaStream_t st);
+cudaError_t radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
+                           uint64_t n, uint32_t key_bits, void* tmp, cudaStream_t st);
+// Sort each row [off[i], off[i+1]) of keys ascending, moving vals (nullable) along.
+cudaError_t segmented_sort(uint32_t* keys, uint32_t* vals, const uint64_t* off, uint64_t rows,
+                           uint64_t total, uint64_t max_row, cudaStream_t st);
+
+// ------------------------------------------------------------------ encoder
+cudaError_t enc_validate(const uint64_t* rp, const uint32_t* col, const uint32_t* w, uint64_t n,
+                         uint64_t arcs, uint32_t wbits, int* err, unsigned long long* max_deg,
+                         uint32_t* max_w, cudaStream_t st);
+cudaError_t enc_check_symmetric(const uint64_t* rp, const uint32_t* col, uint64_t n, int* err,
+                                cudaStream_t st);
+cudaError_t enc_dm_relabel(const uint64_t* rp, const uint32_t* col, const uint32_t* w, uint64_t n,
+                           uint64_t arcs, uint64_t max_deg, uint32_t* perm, uint32_t* inv_perm,
+                           uint64_t* nrp, uint32_t* ncol, uint32_t* nw, cudaStream_t st);
+cudaError_t enc_local_lengths(const uint64_t* rp, const uint32_t* col, uint64_t n, int gap, uint32_t s,
+                              uint32_t H, uint8_t* wid, uint64_t* len, cudaStream_t st);
+cudaError_t enc_pack_global(const uint32_t* col, const uint32_t* w, uint64_t arcs, uint32_t s,
+                            uint32_t omega, uint64_t* out, uint64_t data_words, cudaStream_t st);
+cudaError_t enc_pack_local(const uint64_t* rp, const uint32_t* col, const uint64_t* x, const uint8_t* wid,
+                           uint64_t n, int gap, uint32_t s, uint32_t H, uint64_t* out, uint64_t data_words,
+                           cudaStream_t st);
+cudaError_t enc_pack_u64(const uint64_t* vals, uint64_t count, uint32_t w, uint64_t* out,
+                         uint64_t data_words, cudaStream_t st);
+cudaError_t enc_ef_high(const uint64_t* x, uint64_t N, uint32_t l, uint64_t* out, cudaStream_t st);
+cudaError_t enc_ef_samples(const uint64_t* x, uint64_t N, uint32_t l, uint32_t sample, uint64_t* out,
+                           uint64_t ns, cudaStream_t st);
+
+// ------------------------------------------------------------------ traversal
+struct PrArgs {
+  const float* contrib_in;   // r_{t-1}[u] / d_u, stored labels
+  float* contrib_out;        // r_t[v] / d_v
+  float* ranks_out;          // written on the last iteration (original labels)
+  int last;                  // 1 on the last iteration
+  float base_all;            // (1-d)/n for global PageRank
+  float damp;
+  int64_t personal;          // stored label of the personalization source, -1 = global
+  float r0_all;              // 1/n (initial rank, global)
+  uint32_t heavy_min;        // degree above which a vertex is decoded by a whole warp
+};
+
+struct BfsArgs {
+  void* vis;                 // visited masks [n]
+  const void* front_in;      // frontier masks of this level [n]
+  void* front_out;           // frontier masks of the next level [n] (zero before a push level)
+  uint32_t* depth;           // S x n depths in stored labels
+  uint64_t all_mask;         // bits of the active sources
+  uint32_t S;
+  uint32_t level;            // depth of the current frontier
+  const uint32_t* queue_in;  // frontier vertices (push levels)
+  uint32_t queue_in_len;
+  uint32_t* queue_out;       // vertices of the next frontier
+  uint32_t* counters;        // [0] next queue length, [1] new (vertex, source) pairs
+  uint32_t heavy_min;
+  int* err;
+};
+
+struct NbrArgs {
+  const uint32_t* vertices;  // original IDs
+  uint64_t k;
+  uint64_t* out_offsets;     // k+1 (the degree pass writes degrees into [0..k))
+  uint32_t* out_ids;
+  uint32_t* out_weights;
+  int* err;
+};
+
+struct TravOps {
+  cudaError_t (*pr_init)(const GView&, const PrArgs&, cudaStream_t);
+  cudaError_t (*pr_pull)(const GView&, const PrArgs&, cudaStream_t);
+  cudaError_t (*bfs_pull)(const GView&, const BfsArgs&, int mask_bytes, cudaStream_t);
+  cudaError_t (*bfs_push)(const GView&, const BfsArgs&, int mask_bytes, cudaStream_t);
+  cudaError_t (*nbr_degrees)(const GView&, const NbrArgs&, cudaStream_t);
+  cudaError_t (*nbr_decode)(const GView&, const NbrArgs&, cudaStream_t);
+};
+
+const TravOps* trav_ops(int id_mode, int off_mode);
+const TravOps* trav_ops_global_packed();
+const TravOps* trav_ops_global_ef();
+const TravOps* trav_ops_local_packed();
+const TravOps* trav_ops_local_ef();
+const TravOps* trav_ops_gap_packed();
+const TravOps* trav_ops_gap_ef();
+const TravOps* trav_ops_csr32();
+
+// BFS helpers (lg_bfs_host.cu)
+cudaError_t bfs_seed(void* vis, void* front, uint32_t* depth, uint64_t n, const uint32_t* sources_stored,
+                     uint32_t S, int mask_bytes, uint32_t* queue, uint32_t* counters, cudaStream_t st);
+cudaError_t bfs_permute_depths(const uint32_t* tmp, uint32_t* out, const uint32_t* perm, uint64_t n,
+                               uint32_t S, cudaStream_t st);
+cudaError_t map_ids(const uint32_t* in, uint32_t* out, const uint32_t* perm, uint64_t k, uint64_t n,
+                    int* err, cudaStream_t st);
+
+}  // namespace lg

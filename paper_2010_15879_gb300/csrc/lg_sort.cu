@@ -1,0 +1,393 @@
+// Sorting used by the encoder: a stable LSD radix sort (8-bit digits) of
+// (key, value) pairs, the DM permuter of Section 5.6 (vertices ordered by
+// degree descending, ties by original ID) built on it, and a segmented sort of
+// CSR rows (the relabeled neighborhoods must be sorted again, Section 2.3).
+#include "lg_internal.h"
+
+namespace lg {
+
+// =========================================================================
+// stable LSD radix sort
+// =========================================================================
+constexpr int RS_NT = 256;
+constexpr int RS_ROUNDS = 16;
+constexpr int RS_TILE = RS_NT * RS_ROUNDS;  // keys per CTA
+constexpr int RS_NW = RS_NT / 32;
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+template <typename K>
+__global__ void __launch_bounds__(RS_NT) k_rs_hist(const K* __restrict__ keys, uint64_t n, uint32_t shift,
+                                                   uint32_t* __restrict__ hist, uint64_t ntiles) {
+  __shared__ uint32_t cnt[256];
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const uint64_t base = (uint64_t)blockIdx.x * RS_TILE;
+  for (int r = 0; r < RS_ROUNDS; r++) {
+    const uint64_t i = base + (uint64_t)r * RS_NT + threadIdx.x;
+    if (i < n) atomicAdd(&cnt[(uint32_t)(keys[i] >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  hist[(uint64_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];  // digit-major
+}
+
+template <typename K>
+__global__ void __launch_bounds__(RS_NT) k_rs_scatter(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                                      K* __restrict__ kout, uint32_t* __restrict__ vout, uint64_t n,
+                                                      uint32_t shift, const uint64_t* __restrict__ off,
+                                                      uint64_t ntiles) {
+  __shared__ uint32_t wcnt[RS_NW][256];
+  __shared__ uint64_t run[256];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  run[threadIdx.x] = off[(uint64_t)threadIdx.x * ntiles + blockIdx.x];
+  const uint64_t base = (uint64_t)blockIdx.x * RS_TILE;
+  for (int r = 0; r < RS_ROUNDS; r++) {
+    for (int k = 0; k < RS_NW; k++) wcnt[k][threadIdx.x] = 0;
+    __syncthreads();
+    const uint64_t i = base + (uint64_t)r * RS_NT + threadIdx.x;
+    const bool ok = i < n;
+    K key = ok ? kin[i] : K(0);
+    const uint32_t val = (ok && vin) ? vin[i] : 0u;
+    const uint32_t dig = ok ? ((uint32_t)(key >> shift) & 255u) : 256u;
+    const uint32_t peers = __match_any_sync(LG_FULL_MASK, dig);
+    const uint32_t rank = __popc(peers & lanemask_lt());
+    if (ok && rank == 0) wcnt[w][dig] = __popc(peers);
+    __syncthreads();
+    // thread t owns digit t: exclusive prefix over warps, then advance the run
+    {
+      uint32_t acc = 0;
+      for (int k = 0; k < RS_NW; k++) {
+        const uint32_t c = wcnt[k][threadIdx.x];
+        wcnt[k][threadIdx.x] = acc;
+        acc += c;
+      }
+      // read run before updating: positions use the old value
+      __syncthreads();
+      if (ok) {
+        const uint64_t pos = run[dig] + wcnt[w][dig] + rank;
+        kout[pos] = key;
+        if (vin) vout[pos] = val;
+      }
+      __syncthreads();
+      run[threadIdx.x] += acc;
+    }
+    __syncthreads();
+  }
+  (void)lane;
+}
+
+size_t radix_tmp_bytes(uint64_t n) {
+  const uint64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
+  const uint64_t cells = 256 * ntiles;
+  return cells * sizeof(uint32_t) + (cells + 1) * sizeof(uint64_t) + scan_tmp_words(cells) * sizeof(uint64_t) + 256;
+}
+
+template <typename K>
+static cudaError_t radix_impl(K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals_alt, uint64_t n,
+                              uint32_t key_bits, void* tmp, cudaStream_t st) {
+  if (n <= 1 || key_bits == 0) return cudaSuccess;
+  const uint64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
+  const uint64_t cells = 256 * ntiles;
+  uint32_t* hist = reinterpret_cast<uint32_t*>(tmp);
+  uint64_t* off = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(tmp) + ((cells * 4 + 15) & ~15ull));
+  uint64_t* stmp = off + cells + 2;
+  K* ka = keys; K* kb = keys_alt;
+  uint32_t* va = vals; uint32_t* vb = vals_alt;
+  const uint32_t passes = (key_bits + 7) / 8;
+  for (uint32_t p = 0; p < passes; p++) {
+    const uint32_t shift = 8 * p;
+    k_rs_hist<K><<<(unsigned)ntiles, RS_NT, 0, st>>>(ka, n, shift, hist, ntiles);
+    count_launch();
+    cudaError_t e = scan_excl_u32(hist, cells, off, stmp, st);
+    if (e != cudaSuccess) return e;
+    k_rs_scatter<K><<<(unsigned)ntiles, RS_NT, 0, st>>>(ka, va, kb, vb, n, shift, off, ntiles);
+    count_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    K* t = ka; ka = kb; kb = t;
+    uint32_t* tv = va; va = vb; vb = tv;
+  }
+  if (ka != keys) {
+    cudaError_t e = cudaMemcpyAsync(keys, ka, n * sizeof(K), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+    if (vals) e = cudaMemcpyAsync(vals, va, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t radix_sort_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, uint64_t n,
+                           uint32_t key_bits, void* tmp, cudaStream_t st) {
+  return radix_impl<uint32_t>(keys, vals, keys_alt, vals_alt, n, key_bits, tmp, st);
+}
+cudaError_t radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt, uint64_t n,
+                           uint32_t key_bits, void* tmp, cudaStream_t st) {
+  return radix_impl<uint64_t>(keys, vals, keys_alt, vals_alt, n, key_bits, tmp, st);
+}
+
+// =========================================================================
+// segmented sort of CSR rows
+// =========================================================================
+constexpr uint32_t SEG_SMALL = 32;    // one warp per row, bitonic network in registers
+constexpr uint32_t SEG_MEDIUM = 8192; // one CTA per row, bitonic in shared memory
+
+// warp bitonic sort of one (key, val) per lane, ascending
+__device__ __forceinline__ void warp_bitonic(uint32_t& key, uint32_t& val) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const uint32_t ok = __shfl_xor_sync(LG_FULL_MASK, key, j);
+      const uint32_t ov = __shfl_xor_sync(LG_FULL_MASK, val, j);
+      const bool up = ((lane & k) == 0);
+      const bool lower = ((lane & j) == 0);
+      // lower lane keeps the min when sorting up
+      const bool take_other = lower ? (up ? (ok < key) : (ok > key)) : (up ? (ok > key) : (ok < key));
+      if (take_other) { key = ok; val = ov; }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_seg_small(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                                   const uint64_t* __restrict__ off, uint64_t rows) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t r = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += warps) {
+    const uint64_t lo = off[r], d = off[r + 1] - lo;
+    if (d <= 1 || d > SEG_SMALL) continue;
+    uint32_t key = lane < d ? keys[lo + lane] : 0xffffffffu;
+    uint32_t val = (lane < d && vals) ? vals[lo + lane] : 0u;
+    warp_bitonic(key, val);
+    if (lane < d) {
+      keys[lo + lane] = key;
+      if (vals) vals[lo + lane] = val;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_seg_medium(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                                    const uint64_t* __restrict__ off, const uint32_t* __restrict__ list,
+                                                    uint32_t nlist) {
+  extern __shared__ uint32_t sm[];
+  uint32_t* sk = sm;
+  uint32_t* sv = sm + SEG_MEDIUM;
+  for (uint32_t li = blockIdx.x; li < nlist; li += gridDim.x) {
+    const uint64_t r = list[li];
+    const uint64_t lo = off[r];
+    const uint32_t d = (uint32_t)(off[r + 1] - lo);
+    uint32_t P = 64;
+    while (P < d) P <<= 1;
+    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
+      sk[i] = i < d ? keys[lo + i] : 0xffffffffu;
+      sv[i] = (i < d && vals) ? vals[lo + i] : 0u;
+    }
+    __syncthreads();
+    for (uint32_t k = 2; k <= P; k <<= 1) {
+      for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+        for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
+          const uint32_t ixj = i ^ j;
+          if (ixj > i) {
+            const bool up = (i & k) == 0;
+            const uint32_t a = sk[i], b = sk[ixj];
+            if (up ? (a > b) : (a < b)) {
+              sk[i] = b; sk[ixj] = a;
+              const uint32_t t = sv[i]; sv[i] = sv[ixj]; sv[ixj] = t;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    for (uint32_t i = threadIdx.x; i < d; i += blockDim.x) {
+      keys[lo + i] = sk[i];
+      if (vals) vals[lo + i] = sv[i];
+    }
+    __syncthreads();
+  }
+}
+
+// rows by size class: medium rows listed, large rows listed separately
+__global__ void k_seg_classify(const uint64_t* __restrict__ off, uint64_t rows, uint32_t* med, uint32_t* nmed,
+                               uint32_t* big, uint32_t* nbig) {
+  for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t d = off[r + 1] - off[r];
+    if (d > SEG_SMALL && d <= SEG_MEDIUM) med[atomicAdd(nmed, 1u)] = (uint32_t)r;
+    else if (d > SEG_MEDIUM) big[atomicAdd(nbig, 1u)] = (uint32_t)r;
+  }
+}
+
+// large rows: gather (row rank, key) composite keys, radix sort, scatter back
+__global__ void k_seg_big_gather(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
+                                 const uint64_t* __restrict__ off, const uint32_t* __restrict__ big,
+                                 const uint64_t* __restrict__ boff, uint32_t nbig, uint64_t* __restrict__ ck,
+                                 uint32_t* __restrict__ cv) {
+  for (uint32_t b = blockIdx.x; b < nbig; b += gridDim.x) {
+    const uint64_t lo = off[big[b]], d = off[big[b] + 1] - lo, o = boff[b];
+    for (uint64_t i = threadIdx.x; i < d; i += blockDim.x) {
+      ck[o + i] = ((uint64_t)b << 32) | keys[lo + i];
+      cv[o + i] = vals ? vals[lo + i] : 0u;
+    }
+  }
+}
+__global__ void k_seg_big_scatter(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                  const uint64_t* __restrict__ off, const uint32_t* __restrict__ big,
+                                  const uint64_t* __restrict__ boff, uint32_t nbig, const uint64_t* __restrict__ ck,
+                                  const uint32_t* __restrict__ cv) {
+  for (uint32_t b = blockIdx.x; b < nbig; b += gridDim.x) {
+    const uint64_t lo = off[big[b]], d = off[big[b] + 1] - lo, o = boff[b];
+    for (uint64_t i = threadIdx.x; i < d; i += blockDim.x) {
+      keys[lo + i] = (uint32_t)ck[o + i];
+      if (vals) vals[lo + i] = cv[o + i];
+    }
+  }
+}
+__global__ void k_seg_big_sizes(const uint64_t* __restrict__ off, const uint32_t* __restrict__ big, uint32_t nbig,
+                                uint64_t* __restrict__ sizes) {
+  for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < nbig; b += gridDim.x * blockDim.x)
+    sizes[b] = off[big[b] + 1] - off[big[b]];
+}
+
+cudaError_t segmented_sort(uint32_t* keys, uint32_t* vals, const uint64_t* off, uint64_t rows, uint64_t total,
+                           uint64_t max_row, cudaStream_t st) {
+  if (rows == 0 || total == 0 || max_row <= 1) return cudaSuccess;
+  cudaError_t e;
+  k_seg_small<<<grid_for(rows, 8, 152 * 64), 256, 0, st>>>(keys, vals, off, rows);
+  count_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (max_row <= SEG_SMALL) return cudaSuccess;
+  uint32_t *list = nullptr, *cnt = nullptr;
+  const uint64_t cap = rows;
+  if ((e = cudaMallocAsync((void**)&list, 2 * cap * sizeof(uint32_t) + 16, st)) != cudaSuccess) return e;
+  if ((e = cudaMallocAsync((void**)&cnt, 2 * sizeof(uint32_t), st)) != cudaSuccess) { cudaFreeAsync(list, st); return e; }
+  uint32_t* big = list + cap;
+  cudaMemsetAsync(cnt, 0, 2 * sizeof(uint32_t), st);
+  k_seg_classify<<<grid_for(rows, 256, 152 * 16), 256, 0, st>>>(off, rows, list, cnt, big, cnt + 1);
+  count_launch();
+  uint32_t h[2] = {0, 0};
+  cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) { cudaFreeAsync(list, st); cudaFreeAsync(cnt, st); return e; }
+  if (h[0]) {
+    const size_t smem = 2 * SEG_MEDIUM * sizeof(uint32_t);
+    cudaFuncSetAttribute(k_seg_medium, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_seg_medium<<<grid_for(h[0], 1, 152 * 8), 256, smem, st>>>(keys, vals, off, list, h[0]);
+    count_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) { cudaFreeAsync(list, st); cudaFreeAsync(cnt, st); return e; }
+  }
+  if (h[1]) {
+    const uint32_t nbig = h[1];
+    uint64_t *sizes = nullptr, *boff = nullptr, *ck = nullptr, *ck2 = nullptr, *stmp = nullptr;
+    uint32_t *cv = nullptr, *cv2 = nullptr;
+    void* rtmp = nullptr;
+    // total elements of big rows is at most `total`
+    e = cudaMallocAsync((void**)&sizes, nbig * sizeof(uint64_t), st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&boff, (nbig + 1) * sizeof(uint64_t), st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&stmp, scan_tmp_words(nbig) * sizeof(uint64_t), st);
+    uint64_t nb_total = 0;
+    if (e == cudaSuccess) {
+      k_seg_big_sizes<<<grid_for(nbig, 256, 1024), 256, 0, st>>>(off, big, nbig, sizes);
+      count_launch();
+      e = scan_excl_u64(sizes, nbig, boff, stmp, st);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&nb_total, boff + nbig, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&ck, nb_total * sizeof(uint64_t), st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&ck2, nb_total * sizeof(uint64_t), st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&cv, nb_total * sizeof(uint32_t), st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&cv2, nb_total * sizeof(uint32_t), st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&rtmp, radix_tmp_bytes(nb_total), st);
+    if (e == cudaSuccess) {
+      k_seg_big_gather<<<grid_for(nbig, 1, 4096), 256, 0, st>>>(keys, vals, off, big, boff, nbig, ck, cv);
+      count_launch();
+      e = radix_sort_u64(ck, cv, ck2, cv2, nb_total, 32 + host_bits(nbig), rtmp, st);
+    }
+    if (e == cudaSuccess) {
+      k_seg_big_scatter<<<grid_for(nbig, 1, 4096), 256, 0, st>>>(keys, vals, off, big, boff, nbig, ck, cv);
+      count_launch();
+      e = cudaGetLastError();
+    }
+    cudaFreeAsync(sizes, st); cudaFreeAsync(boff, st); cudaFreeAsync(stmp, st);
+    cudaFreeAsync(ck, st); cudaFreeAsync(ck2, st); cudaFreeAsync(cv, st); cudaFreeAsync(cv2, st);
+    cudaFreeAsync(rtmp, st);
+    if (e != cudaSuccess) { cudaFreeAsync(list, st); cudaFreeAsync(cnt, st); return e; }
+  }
+  cudaFreeAsync(list, st);
+  cudaFreeAsync(cnt, st);
+  return cudaGetLastError();
+}
+
+// =========================================================================
+// DM permuter (Section 5.6): label i goes to the i-th vertex in the order
+// (degree descending, original ID ascending); the relabeled CSR holds row
+// P(v) = sorted { P(u) : u in N_v }.
+// =========================================================================
+__global__ void k_dm_keys(const uint64_t* __restrict__ rp, uint64_t n, uint64_t max_deg, uint32_t* __restrict__ keys,
+                          uint32_t* __restrict__ vals) {
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x) {
+    keys[v] = (uint32_t)(max_deg - (rp[v + 1] - rp[v]));
+    vals[v] = (uint32_t)v;
+  }
+}
+__global__ void k_dm_perm(const uint32_t* __restrict__ inv, uint64_t n, uint32_t* __restrict__ perm,
+                          const uint64_t* __restrict__ rp, uint32_t* __restrict__ newdeg) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t v = inv[i];
+    perm[v] = (uint32_t)i;
+    newdeg[i] = (uint32_t)(rp[v + 1] - rp[v]);
+  }
+}
+__global__ void __launch_bounds__(256) k_dm_scatter(const uint64_t* __restrict__ rp, const uint32_t* __restrict__ col,
+                                                    const uint32_t* __restrict__ w, const uint32_t* __restrict__ inv,
+                                                    const uint32_t* __restrict__ perm, const uint64_t* __restrict__ nrp,
+                                                    uint32_t* __restrict__ ncol, uint32_t* __restrict__ nw, uint64_t n) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t i = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+    const uint32_t v = inv[i];
+    const uint64_t lo = rp[v], d = rp[v + 1] - lo, o = nrp[i];
+    for (uint64_t k = lane; k < d; k += 32) {
+      ncol[o + k] = perm[col[lo + k]];
+      if (w) nw[o + k] = w[lo + k];
+    }
+  }
+}
+
+cudaError_t enc_dm_relabel(const uint64_t* rp, const uint32_t* col, const uint32_t* w, uint64_t n, uint64_t arcs,
+                           uint64_t max_deg, uint32_t* perm, uint32_t* inv_perm, uint64_t* nrp, uint32_t* ncol,
+                           uint32_t* nw, cudaStream_t st) {
+  cudaError_t e;
+  uint32_t *keys = nullptr, *k2 = nullptr, *v2 = nullptr, *newdeg = nullptr;
+  uint64_t* stmp = nullptr;
+  void* rtmp = nullptr;
+  e = cudaMallocAsync((void**)&keys, n * sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&k2, n * sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&v2, n * sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&newdeg, n * sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&stmp, scan_tmp_words(n) * sizeof(uint64_t), st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&rtmp, radix_tmp_bytes(n), st);
+  if (e == cudaSuccess) {
+    k_dm_keys<<<grid_for(n, 256, 152 * 32), 256, 0, st>>>(rp, n, max_deg, keys, inv_perm);
+    count_launch();
+    e = radix_sort_u32(keys, inv_perm, k2, v2, n, host_bits(max_deg), rtmp, st);
+  }
+  if (e == cudaSuccess) {
+    k_dm_perm<<<grid_for(n, 256, 152 * 32), 256, 0, st>>>(inv_perm, n, perm, rp, newdeg);
+    count_launch();
+    e = scan_excl_u32(newdeg, n, nrp, stmp, st);
+  }
+  if (e == cudaSuccess) {
+    k_dm_scatter<<<grid_for(n, 8, 152 * 64), 256, 0, st>>>(rp, col, w, inv_perm, perm, nrp, ncol, nw, n);
+    count_launch();
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = segmented_sort(ncol, w ? nw : nullptr, nrp, n, arcs, max_deg, st);
+  cudaFreeAsync(keys, st); cudaFreeAsync(k2, st); cudaFreeAsync(v2, st); cudaFreeAsync(newdeg, st);
+  cudaFreeAsync(stmp, st); cudaFreeAsync(rtmp, st);
+  return e;
+}
+
+}  // namespace lg

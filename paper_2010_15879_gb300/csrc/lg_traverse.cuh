@@ -1,0 +1,669 @@
+// Graph kernels with the Log(Graph) decoder fused in (Sections 3.7.2-3.7.3 for
+// the access path, Section 7.1.2 for BFS and PageRank).
+//
+// Pull sweeps (PageRank, bottom-up BFS) walk the vertices in tiles of TV = 512
+// consecutive stored labels, one CTA per tile:
+//   1. offsets x_v of the tile (packed fields, CSR row_ptr, or an Elias-Fano
+//      block decode: the tile starts on a select sample, the CTA popcounts the
+//      high-bit words it spans and every thread selects one vertex's one);
+//   2. per vertex: degree and field width from the offsets and the
+//      neighborhood header;
+//   3. vertices of degree <= heavy_min are split over the threads in contiguous
+//      runs of nearly equal field counts, each thread decoding its own run with
+//      a sequential bit reader (one 128-bit load per ~128 bits, a funnel shift
+//      and a mask per field, a running sum for gap-coded IDs);
+//   4. vertices of higher degree are decoded by a whole warp, lane i taking
+//      field i of each 32-field chunk (gap-coded IDs by a warp prefix sum).
+// Push steps and neighbor queries decode one random vertex per warp.
+#pragma once
+
+#include "lg_internal.h"
+
+namespace lg {
+
+constexpr int TV = 512;   // vertices per tile
+constexpr int TNT = 256;  // threads per tile CTA
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t udiv_small(uint64_t a, uint32_t b) {
+  return a < 0x100000000ull ? (uint64_t)((uint32_t)a / b) : a / b;
+}
+__device__ __forceinline__ uint32_t lane_lt_mask() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+template <typename M> __device__ __forceinline__ M atomic_or_mask(M* p, M m);
+template <> __device__ __forceinline__ uint16_t atomic_or_mask<uint16_t>(uint16_t* p, uint16_t m) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+  uint32_t* w = reinterpret_cast<uint32_t*>(a & ~(uintptr_t)3);
+  const uint32_t sh = (uint32_t)(a & 2) * 8u;
+  return (uint16_t)(atomicOr(w, (uint32_t)m << sh) >> sh);
+}
+template <> __device__ __forceinline__ uint32_t atomic_or_mask<uint32_t>(uint32_t* p, uint32_t m) {
+  return atomicOr(p, m);
+}
+template <> __device__ __forceinline__ uint64_t atomic_or_mask<uint64_t>(uint64_t* p, uint64_t m) {
+  return (uint64_t)atomicOr(reinterpret_cast<unsigned long long*>(p), (unsigned long long)m);
+}
+
+template <typename M>
+__device__ __forceinline__ void write_depths(uint32_t* depth, uint64_t n, uint64_t v, M bitsv, uint32_t d) {
+  uint64_t b = (uint64_t)bitsv;
+  while (b) {
+    const int s = __ffsll((long long)b) - 1;
+    b &= b - 1;
+    depth[(uint64_t)s * n + v] = d;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// offsets of a tile: xs[i] = x_{v0+i}, i = 0..cnt (cnt+1 values)
+// ---------------------------------------------------------------------------
+struct TileScratch {
+  uint32_t cum[TNT];
+  uint32_t w[TNT];
+  uint32_t red[TNT / 32];
+};
+
+template <int OFF>
+__device__ __forceinline__ void tile_offsets(const GView& g, uint64_t v0, int cnt, uint64_t* xs, TileScratch& ts);
+
+template <>
+__device__ __forceinline__ void tile_offsets<OFF_PACKED>(const GView& g, uint64_t v0, int cnt, uint64_t* xs,
+                                                         TileScratch&) {
+  for (int i = threadIdx.x; i <= cnt; i += TNT) xs[i] = ext64(g.O, (v0 + i) * g.w_O, g.w_O);
+}
+
+template <>
+__device__ __forceinline__ void tile_offsets<OFF_ROWPTR>(const GView& g, uint64_t v0, int cnt, uint64_t* xs,
+                                                         TileScratch&) {
+  for (int i = threadIdx.x; i <= cnt; i += TNT) xs[i] = __ldg(g.O + v0 + i);
+}
+
+// Elias-Fano block decode (Section 4.3): ones number v0 .. v0+cnt of the high
+// vector, starting from the sample at or below v0.
+template <>
+__device__ __forceinline__ void tile_offsets<OFF_EF>(const GView& g, uint64_t v0, int cnt, uint64_t* xs,
+                                                     TileScratch& ts) {
+  const uint64_t k = v0 >> g.sample_log2;
+  const uint64_t p0 = __ldg(g.ef_samples + k);
+  const uint64_t skip = v0 - (k << g.sample_log2);
+  const uint64_t need_end = skip + (uint64_t)cnt + 1;
+  uint64_t wbase = p0 >> 5;
+  uint64_t carry = 0;
+  bool first = true;
+  while (carry < need_end && wbase < g.ef_high_words32) {
+    const uint64_t wi = wbase + threadIdx.x;
+    uint32_t w = wi < g.ef_high_words32 ? __ldg(g.ef_high32 + wi) : 0u;
+    if (first && threadIdx.x == 0) w &= (0xffffffffu << ((uint32_t)p0 & 31u));
+    uint32_t total;
+    const uint32_t pre = block_excl_scan<uint32_t, TNT>((uint32_t)__popc(w), total, ts.red);
+    ts.cum[threadIdx.x] = pre;
+    ts.w[threadIdx.x] = w;
+    __syncthreads();
+    const uint64_t r_lo = carry > skip ? carry : skip;
+    const uint64_t r_hi = (carry + total) < need_end ? (carry + total) : need_end;
+    for (uint64_t r = r_lo + threadIdx.x; r < r_hi; r += TNT) {
+      const uint32_t local = (uint32_t)(r - carry);
+      int lo = 0, hi = TNT - 1;
+      while (lo < hi) {
+        const int m = (lo + hi + 1) >> 1;
+        if (ts.cum[m] <= local) lo = m; else hi = m - 1;
+      }
+      const uint64_t pos = (wbase + (uint64_t)lo) * 32u + select_in_u32(ts.w[lo], local - ts.cum[lo]);
+      const uint64_t i = r - skip;
+      xs[i] = (pos - (v0 + i)) << g.ef_l;
+    }
+    carry += total;
+    wbase += TNT;
+    first = false;
+    __syncthreads();
+  }
+  if (g.ef_l)
+    for (int i = threadIdx.x; i <= cnt; i += TNT) xs[i] |= ext64(g.ef_low, (v0 + i) * g.ef_l, g.ef_l);
+}
+
+// ---------------------------------------------------------------------------
+// random-access offsets x_v, x_{v+1}; called by all 32 lanes of a warp
+// ---------------------------------------------------------------------------
+template <int OFF>
+__device__ __forceinline__ void offset_pair(const GView& g, uint64_t v, uint64_t& x0, uint64_t& x1);
+
+template <>
+__device__ __forceinline__ void offset_pair<OFF_PACKED>(const GView& g, uint64_t v, uint64_t& x0, uint64_t& x1) {
+  x0 = ext64(g.O, v * g.w_O, g.w_O);
+  x1 = ext64(g.O, (v + 1) * g.w_O, g.w_O);
+}
+template <>
+__device__ __forceinline__ void offset_pair<OFF_ROWPTR>(const GView& g, uint64_t v, uint64_t& x0, uint64_t& x1) {
+  x0 = __ldg(g.O + v);
+  x1 = __ldg(g.O + v + 1);
+}
+// warp select of ones number v and v+1 (Section 4.1: O_v = select_O(v))
+template <>
+__device__ __forceinline__ void offset_pair<OFF_EF>(const GView& g, uint64_t v, uint64_t& x0, uint64_t& x1) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t k = v >> g.sample_log2;
+  const uint64_t p0 = __ldg(g.ef_samples + k);
+  const uint64_t rem = v - (k << g.sample_log2);
+  uint64_t wbase = p0 >> 5;
+  uint64_t carry = 0;
+  uint64_t pos[2] = {0, 0};
+  uint32_t found = 0;
+  bool first = true;
+  while (found != 3u && wbase < g.ef_high_words32) {
+    const uint64_t wi = wbase + lane;
+    uint32_t w = wi < g.ef_high_words32 ? __ldg(g.ef_high32 + wi) : 0u;
+    if (first && lane == 0) w &= (0xffffffffu << ((uint32_t)p0 & 31u));
+    const uint32_t c = __popc(w);
+    const uint32_t incl = warp_incl_scan<uint32_t>(c);
+    const uint32_t excl = incl - c;
+    const uint32_t total = __shfl_sync(LG_FULL_MASK, incl, 31);
+#pragma unroll
+    for (int t = 0; t < 2; t++) {
+      const uint64_t target = rem + t;
+      const bool here = !(found >> t & 1u) && carry + excl <= target && target < carry + incl;
+      const uint32_t b = __ballot_sync(LG_FULL_MASK, here);
+      uint64_t p = here ? wi * 32u + select_in_u32(w, (uint32_t)(target - carry - excl)) : 0;
+      if (b) {
+        p = __shfl_sync(LG_FULL_MASK, p, __ffs(b) - 1);
+        pos[t] = p;
+        found |= 1u << t;
+      }
+    }
+    carry += total;
+    wbase += 32;
+    first = false;
+  }
+  const uint64_t lo0 = g.ef_l ? ext64(g.ef_low, v * g.ef_l, g.ef_l) : 0;
+  const uint64_t lo1 = g.ef_l ? ext64(g.ef_low, (v + 1) * g.ef_l, g.ef_l) : 0;
+  x0 = ((pos[0] - v) << g.ef_l) | lo0;
+  x1 = ((pos[1] - (v + 1)) << g.ef_l) | lo1;
+}
+
+// ---------------------------------------------------------------------------
+// neighborhood geometry from consecutive offsets (Section 3.7.3: d_v from
+// O[v+1] - O[v]; in the local modes from the bit length and the header)
+//   start: bit of the first field; w: field width (IDs, or gaps for LOCAL_GAP)
+// ---------------------------------------------------------------------------
+template <int IDM>
+__device__ __forceinline__ void vgeo(const GView& g, uint64_t x0, uint64_t x1, uint64_t& start, uint32_t& deg,
+                                     uint32_t& w) {
+  if (IDM == ID_GLOBAL) {
+    start = x0 * g.r; deg = (uint32_t)(x1 - x0); w = g.s;
+  } else if (IDM == ID_CSR32) {
+    start = x0 * 32u; deg = (uint32_t)(x1 - x0); w = 32;
+  } else if (IDM == ID_LOCAL) {
+    w = ext32(g.A32, x0, g.H);
+    deg = w ? (uint32_t)udiv_small(x1 - x0 - g.H, w) : 0u;
+    start = x0 + g.H;
+  } else {
+    w = ext32(g.A32, x0, g.H);
+    const uint64_t len = x1 - x0;
+    deg = len == g.H ? 0u : (w == 0 ? 1u : 1u + (uint32_t)udiv_small(len - g.H - g.s, w));
+    start = x0 + g.H;
+  }
+}
+
+// sequential decoder for one neighborhood (light path)
+template <int IDM>
+struct SeqDec {
+  BitReader br;
+  uint32_t w, s, omega, id;
+  bool first;
+  __device__ __forceinline__ void init(const GView& g, uint64_t start, uint32_t width) {
+    br.init(g.A32, start);
+    w = width; s = g.s; omega = g.omega; id = 0; first = true;
+  }
+  __device__ __forceinline__ uint32_t next() {
+    if (IDM == ID_GLOBAL) {
+      const uint32_t v = br.get(s);
+      if (omega) br.skip(omega);
+      return v;
+    } else if (IDM == ID_CSR32) {
+      return br.get(32);
+    } else if (IDM == ID_LOCAL) {
+      return br.get(w);
+    } else {
+      id = first ? br.get(s) : id + br.get(w);
+      first = false;
+      return id;
+    }
+  }
+};
+
+// value of field i for the warp path (not yet prefix-summed for gaps)
+template <int IDM>
+__device__ __forceinline__ uint32_t field_at(const GView& g, uint64_t start, uint32_t w, uint64_t i) {
+  if (IDM == ID_GLOBAL) return ext32(g.A32, start + i * g.r, g.s);
+  if (IDM == ID_CSR32) return __ldg(g.A32 + (start >> 5) + i);
+  if (IDM == ID_LOCAL) return ext32(g.A32, start + i * w, w);
+  return i == 0 ? ext32(g.A32, start, g.s) : ext32(g.A32, start + g.s + (i - 1) * (uint64_t)w, w);
+}
+__device__ __forceinline__ uint32_t weight_at(const GView& g, uint64_t start, uint64_t i) {
+  return ext32(g.A32, start + i * g.r + g.s, g.omega);
+}
+
+// ---------------------------------------------------------------------------
+// tile phases shared by the pull kernels
+// ---------------------------------------------------------------------------
+struct TileSmem {
+  uint64_t xs[TV + 1];     // offsets
+  uint64_t st[TV];         // first-field bit of each vertex
+  uint32_t deg[TV];
+  uint32_t fpre[TV + 1];   // field prefix over the compacted light list
+  uint16_t clist[TV];      // compacted light vertices (local index)
+  uint16_t hlist[TV];      // heavy vertices
+  uint8_t wid[TV];
+  uint32_t nlight, nheavy, nfields;
+  uint64_t red64[TNT / 32];
+  TileScratch ts;
+};
+
+// Phase 2: geometry of each vertex; `keep(i, d)` says whether vertex i has work
+// (else the caller handles it as trivial); light/heavy split and the compacted,
+// prefix-summed light list.
+template <int IDM, typename Keep>
+__device__ __forceinline__ void tile_classify(const GView& g, TileSmem& sm, int cnt, uint32_t heavy_min, Keep keep) {
+  if (threadIdx.x == 0) sm.nheavy = 0;
+  __syncthreads();
+  uint32_t lc = 0, lf = 0;
+  bool light[TV / TNT];
+#pragma unroll
+  for (int q = 0; q < TV / TNT; q++) {
+    const int i = threadIdx.x * (TV / TNT) + q;
+    light[q] = false;
+    if (i < cnt) {
+      uint64_t start; uint32_t d, w;
+      vgeo<IDM>(g, sm.xs[i], sm.xs[i + 1], start, d, w);
+      sm.st[i] = start; sm.deg[i] = d; sm.wid[i] = (uint8_t)w;
+      if (d > 0 && keep(i, d)) {
+        if (d <= heavy_min) { light[q] = true; lc++; lf += d; }
+        else sm.hlist[atomicAdd(&sm.nheavy, 1u)] = (uint16_t)i;
+      }
+    }
+  }
+  uint64_t total;
+  const uint64_t pre = block_excl_scan<uint64_t, TNT>(((uint64_t)lc << 32) | lf, total, sm.red64);
+  uint32_t ci = (uint32_t)(pre >> 32), cf = (uint32_t)pre;
+#pragma unroll
+  for (int q = 0; q < TV / TNT; q++) {
+    const int i = threadIdx.x * (TV / TNT) + q;
+    if (light[q]) {
+      sm.clist[ci] = (uint16_t)i;
+      sm.fpre[ci] = cf;
+      ci++;
+      cf += sm.deg[i];
+    }
+  }
+  if (threadIdx.x == 0) {
+    sm.nlight = (uint32_t)(total >> 32);
+    sm.nfields = (uint32_t)total;
+    sm.fpre[sm.nlight] = (uint32_t)total;
+  }
+  __syncthreads();
+}
+
+// range of compacted light vertices owned by this thread (balanced by fields)
+__device__ __forceinline__ void light_range(const TileSmem& sm, uint32_t& jb, uint32_t& je) {
+  const uint64_t F = sm.nfields;
+  const uint32_t flo = (uint32_t)((F * threadIdx.x) / TNT);
+  const uint32_t fhi = (uint32_t)((F * (threadIdx.x + 1)) / TNT);
+  const uint32_t nl = sm.nlight;
+  uint32_t a = 0, b = nl;
+  while (a < b) { const uint32_t m = (a + b) >> 1; if (sm.fpre[m] < flo) a = m + 1; else b = m; }
+  jb = a;
+  b = nl;
+  while (a < b) { const uint32_t m = (a + b) >> 1; if (sm.fpre[m] < fhi) a = m + 1; else b = m; }
+  je = a;
+}
+
+// ===========================================================================
+// PageRank
+// ===========================================================================
+template <int IDM, int OFF>
+__global__ void __launch_bounds__(TNT) k_pr_init(GView g, PrArgs a) {
+  __shared__ TileSmem sm;
+  const uint64_t v0 = (uint64_t)blockIdx.x * TV;
+  const int cnt = (int)min((uint64_t)TV, g.n - v0);
+  tile_offsets<OFF>(g, v0, cnt, sm.xs, sm.ts);
+  __syncthreads();
+  for (int i = threadIdx.x; i < cnt; i += TNT) {
+    uint64_t start; uint32_t d, w;
+    vgeo<IDM>(g, sm.xs[i], sm.xs[i + 1], start, d, w);
+    const uint64_t v = v0 + i;
+    const float r0 = a.personal < 0 ? a.r0_all : ((int64_t)v == a.personal ? 1.0f : 0.0f);
+    a.contrib_out[v] = d ? r0 / (float)d : 0.0f;
+  }
+}
+
+template <int IDM, int OFF>
+__global__ void __launch_bounds__(TNT) k_pr_pull(GView g, PrArgs a) {
+  __shared__ TileSmem sm;
+  const uint64_t v0 = (uint64_t)blockIdx.x * TV;
+  const int cnt = (int)min((uint64_t)TV, g.n - v0);
+  tile_offsets<OFF>(g, v0, cnt, sm.xs, sm.ts);
+  __syncthreads();
+  tile_classify<IDM>(g, sm, cnt, a.heavy_min, [](int, uint32_t) { return true; });
+  const float* __restrict__ c = a.contrib_in;
+
+  auto finish = [&](uint64_t v, uint32_t d, float sum) {
+    const float base = a.personal < 0 ? a.base_all : ((int64_t)v == a.personal ? a.base_all : 0.0f);
+    const float r = base + a.damp * sum;
+    a.contrib_out[v] = d ? r / (float)d : 0.0f;
+    if (a.last) a.ranks_out[g.inv_perm ? (uint64_t)g.inv_perm[v] : v] = r;
+  };
+
+  // zero-degree vertices keep the teleport term only
+  for (int i = threadIdx.x; i < cnt; i += TNT)
+    if (sm.deg[i] == 0) finish(v0 + i, 0, 0.0f);
+
+  // light vertices: sequential decode of contiguous runs
+  uint32_t jb, je;
+  light_range(sm, jb, je);
+  for (uint32_t j = jb; j < je; j++) {
+    const int i = sm.clist[j];
+    const uint32_t d = sm.deg[i];
+    SeqDec<IDM> dec;
+    dec.init(g, sm.st[i], sm.wid[i]);
+    float s0 = 0.f, s1 = 0.f;
+    uint32_t k = 0;
+    for (; k + 4 <= d; k += 4) {
+      const uint32_t u0 = dec.next(), u1 = dec.next(), u2 = dec.next(), u3 = dec.next();
+      const float f0 = __ldg(c + u0), f1 = __ldg(c + u1), f2 = __ldg(c + u2), f3 = __ldg(c + u3);
+      s0 += f0 + f1;
+      s1 += f2 + f3;
+    }
+    for (; k < d; k++) s0 += __ldg(c + dec.next());
+    finish(v0 + i, d, s0 + s1);
+  }
+
+  // heavy vertices: one warp each, compensated (Kahan) lane sums
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  for (uint32_t h = wp; h < sm.nheavy; h += TNT / 32) {
+    const int i = sm.hlist[h];
+    const uint32_t d = sm.deg[i], w = sm.wid[i];
+    const uint64_t start = sm.st[i];
+    float acc = 0.f, comp = 0.f;
+    uint32_t carry = 0;
+    for (uint32_t base = 0; base < d; base += 32) {
+      const uint32_t idx = base + lane;
+      const bool ok = idx < d;
+      uint32_t val = ok ? field_at<IDM>(g, start, w, idx) : 0u;
+      if (IDM == ID_LOCAL_GAP) {
+        val = warp_incl_scan<uint32_t>(val) + carry;
+        carry = __shfl_sync(LG_FULL_MASK, val, 31);
+      }
+      if (ok) {
+        const float y = __ldg(c + val) - comp;
+        const float t = acc + y;
+        comp = (t - acc) - y;
+        acc = t;
+      }
+    }
+    acc = warp_sum<float>(acc);
+    if (lane == 0) finish(v0 + i, d, acc);
+  }
+}
+
+// ===========================================================================
+// BFS (multi-source, bit-parallel): bit s of a mask is source s
+// ===========================================================================
+template <int IDM, int OFF, typename M>
+__global__ void __launch_bounds__(TNT) k_bfs_pull(GView g, BfsArgs a) {
+  __shared__ TileSmem sm;
+  __shared__ M need_sm[TV];
+  __shared__ uint32_t qbuf[TV];
+  __shared__ uint32_t qn, newpairs, qbase;
+  const uint64_t v0 = (uint64_t)blockIdx.x * TV;
+  const int cnt = (int)min((uint64_t)TV, g.n - v0);
+  M* vis = reinterpret_cast<M*>(a.vis);
+  const M* __restrict__ fin = reinterpret_cast<const M*>(a.front_in);
+  M* fout = reinterpret_cast<M*>(a.front_out);
+  const M all = (M)a.all_mask;
+  if (threadIdx.x == 0) { qn = 0; newpairs = 0; }
+  for (int i = threadIdx.x; i < cnt; i += TNT) need_sm[i] = (M)(all & (M)~vis[v0 + i]);
+  tile_offsets<OFF>(g, v0, cnt, sm.xs, sm.ts);
+  __syncthreads();
+  tile_classify<IDM>(g, sm, cnt, a.heavy_min, [&](int i, uint32_t) { return need_sm[i] != 0; });
+  const uint32_t nd = a.level + 1;
+
+  auto finish = [&](int i, M found) {
+    const uint64_t v = v0 + i;
+    const M nb = found & need_sm[i];
+    fout[v] = nb;
+    if (nb) {
+      vis[v] = (M)(vis[v] | nb);
+      write_depths<M>(a.depth, g.n, v, nb, nd);
+      qbuf[atomicAdd(&qn, 1u)] = (uint32_t)v;
+      atomicAdd(&newpairs, (uint32_t)__popcll((unsigned long long)nb));
+    }
+  };
+
+  for (int i = threadIdx.x; i < cnt; i += TNT)
+    if (sm.deg[i] == 0 || need_sm[i] == 0) fout[v0 + i] = 0;
+
+  uint32_t jb, je;
+  light_range(sm, jb, je);
+  for (uint32_t j = jb; j < je; j++) {
+    const int i = sm.clist[j];
+    const uint32_t d = sm.deg[i];
+    const M need = need_sm[i];
+    SeqDec<IDM> dec;
+    dec.init(g, sm.st[i], sm.wid[i]);
+    M acc = 0;
+    uint32_t k = 0;
+    for (; k + 4 <= d; k += 4) {
+      const uint32_t u0 = dec.next(), u1 = dec.next(), u2 = dec.next(), u3 = dec.next();
+      acc |= (M)(fin[u0] | fin[u1] | fin[u2] | fin[u3]);
+      if ((M)(acc & need) == need) break;
+    }
+    if ((M)(acc & need) != need)
+      for (; k < d; k++) acc |= fin[dec.next()];
+    finish(i, acc);
+  }
+
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  for (uint32_t h = wp; h < sm.nheavy; h += TNT / 32) {
+    const int i = sm.hlist[h];
+    const uint32_t d = sm.deg[i], w = sm.wid[i];
+    const uint64_t start = sm.st[i];
+    const M need = need_sm[i];
+    M acc = 0;
+    uint32_t carry = 0;
+    for (uint32_t base = 0; base < d; base += 32) {
+      const uint32_t idx = base + lane;
+      const bool ok = idx < d;
+      uint32_t val = ok ? field_at<IDM>(g, start, w, idx) : 0u;
+      if (IDM == ID_LOCAL_GAP) {
+        val = warp_incl_scan<uint32_t>(val) + carry;
+        carry = __shfl_sync(LG_FULL_MASK, val, 31);
+      }
+      if (ok) acc |= fin[val];
+      acc = warp_or<M>(acc);
+      if ((M)(acc & need) == need) break;
+    }
+    if (lane == 0) finish(i, acc);
+  }
+
+  __syncthreads();
+  if (threadIdx.x == 0 && qn) {
+    qbase = atomicAdd(&a.counters[0], qn);
+    atomicAdd(&a.counters[1], newpairs);
+  }
+  __syncthreads();
+  for (uint32_t t = threadIdx.x; t < qn; t += TNT) a.queue_out[qbase + t] = qbuf[t];
+}
+
+// top-down step: one warp per frontier vertex
+template <int IDM, int OFF, typename M>
+__global__ void __launch_bounds__(256) k_bfs_push(GView g, BfsArgs a) {
+  M* vis = reinterpret_cast<M*>(a.vis);
+  const M* __restrict__ fin = reinterpret_cast<const M*>(a.front_in);
+  M* fout = reinterpret_cast<M*>(a.front_out);
+  const int lane = threadIdx.x & 31;
+  const uint32_t nd = a.level + 1;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  uint32_t pairs = 0;
+  for (uint64_t q = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); q < a.queue_in_len; q += warps) {
+    const uint32_t v = a.queue_in[q];
+    const M m = fin[v];
+    uint64_t x0, x1, start;
+    uint32_t d, w;
+    offset_pair<OFF>(g, v, x0, x1);
+    vgeo<IDM>(g, x0, x1, start, d, w);
+    uint32_t carry = 0;
+    for (uint32_t base = 0; base < d; base += 32) {
+      const uint32_t idx = base + lane;
+      const bool ok = idx < d;
+      uint32_t u = ok ? field_at<IDM>(g, start, w, idx) : 0u;
+      if (IDM == ID_LOCAL_GAP) {
+        u = warp_incl_scan<uint32_t>(u) + carry;
+        carry = __shfl_sync(LG_FULL_MASK, u, 31);
+      }
+      bool app = false;
+      if (ok) {
+        M nb = (M)(m & (M)~vis[u]);
+        if (nb) {
+          const M old = atomic_or_mask<M>(vis + u, nb);
+          nb = (M)(nb & (M)~old);
+          if (nb) {
+            const M oldf = atomic_or_mask<M>(fout + u, nb);
+            app = (oldf == 0);
+            write_depths<M>(a.depth, g.n, u, nb, nd);
+            pairs += __popcll((unsigned long long)nb);
+          }
+        }
+      }
+      const uint32_t b = __ballot_sync(LG_FULL_MASK, app);
+      if (b) {
+        uint32_t basepos = 0;
+        if (lane == 0) basepos = atomicAdd(&a.counters[0], (uint32_t)__popc(b));
+        basepos = __shfl_sync(LG_FULL_MASK, basepos, 0);
+        if (app) a.queue_out[basepos + __popc(b & lane_lt_mask())] = u;
+      }
+    }
+  }
+  pairs = warp_sum<uint32_t>(pairs);
+  if (lane == 0 && pairs) atomicAdd(&a.counters[1], pairs);
+}
+
+// ===========================================================================
+// neighbor queries (getNeighbors of Listing 3): one warp per query
+// ===========================================================================
+template <int IDM, int OFF>
+__global__ void __launch_bounds__(256) k_nbr_degrees(GView g, NbrArgs a) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t q = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); q < a.k; q += warps) {
+    const uint32_t vo = a.vertices[q];
+    if (vo >= g.n) {
+      if (lane == 0) { set_err(a.err, DERR_QUERY); a.out_offsets[q] = 0; }
+      continue;
+    }
+    const uint64_t v = g.perm ? (uint64_t)g.perm[vo] : vo;
+    uint64_t x0, x1, start;
+    uint32_t d, w;
+    offset_pair<OFF>(g, v, x0, x1);
+    vgeo<IDM>(g, x0, x1, start, d, w);
+    if (lane == 0) a.out_offsets[q] = d;
+  }
+}
+
+template <int IDM, int OFF>
+__global__ void __launch_bounds__(256) k_nbr_decode(GView g, NbrArgs a) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t q = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); q < a.k; q += warps) {
+    const uint32_t vo = a.vertices[q];
+    if (vo >= g.n) continue;
+    const uint64_t v = g.perm ? (uint64_t)g.perm[vo] : vo;
+    uint64_t x0, x1, start;
+    uint32_t d, w;
+    offset_pair<OFF>(g, v, x0, x1);
+    vgeo<IDM>(g, x0, x1, start, d, w);
+    const uint64_t o = a.out_offsets[q];
+    uint32_t carry = 0;
+    for (uint32_t base = 0; base < d; base += 32) {
+      const uint32_t idx = base + lane;
+      const bool ok = idx < d;
+      uint32_t u = ok ? field_at<IDM>(g, start, w, idx) : 0u;
+      if (IDM == ID_LOCAL_GAP) {
+        u = warp_incl_scan<uint32_t>(u) + carry;
+        carry = __shfl_sync(LG_FULL_MASK, u, 31);
+      }
+      if (ok) {
+        a.out_ids[o + idx] = g.inv_perm ? g.inv_perm[u] : u;
+        if (a.out_weights) {
+          uint32_t wt = 0;
+          if (IDM == ID_GLOBAL && g.omega) wt = weight_at(g, start, idx);
+          if (IDM == ID_CSR32 && g.W32) wt = __ldg(g.W32 + (start >> 5) + idx);
+          a.out_weights[o + idx] = wt;
+        }
+      }
+    }
+  }
+}
+
+// ===========================================================================
+// launchers
+// ===========================================================================
+inline unsigned tiles_of(uint64_t n) { return (unsigned)((n + TV - 1) / TV); }
+
+template <int IDM, int OFF>
+cudaError_t launch_pr_init(const GView& g, const PrArgs& a, cudaStream_t st) {
+  k_pr_init<IDM, OFF><<<tiles_of(g.n), TNT, 0, st>>>(g, a);
+  count_launch();
+  return cudaGetLastError();
+}
+template <int IDM, int OFF>
+cudaError_t launch_pr_pull(const GView& g, const PrArgs& a, cudaStream_t st) {
+  k_pr_pull<IDM, OFF><<<tiles_of(g.n), TNT, 0, st>>>(g, a);
+  count_launch();
+  return cudaGetLastError();
+}
+template <int IDM, int OFF>
+cudaError_t launch_bfs_pull(const GView& g, const BfsArgs& a, int mb, cudaStream_t st) {
+  if (mb == 2) { k_bfs_pull<IDM, OFF, uint16_t><<<tiles_of(g.n), TNT, 0, st>>>(g, a); count_launch(); }
+  else if (mb == 4) { k_bfs_pull<IDM, OFF, uint32_t><<<tiles_of(g.n), TNT, 0, st>>>(g, a); count_launch(); }
+  else { k_bfs_pull<IDM, OFF, uint64_t><<<tiles_of(g.n), TNT, 0, st>>>(g, a); count_launch(); }
+  return cudaGetLastError();
+}
+template <int IDM, int OFF>
+cudaError_t launch_bfs_push(const GView& g, const BfsArgs& a, int mb, cudaStream_t st) {
+  if (a.queue_in_len == 0) return cudaSuccess;
+  const unsigned grid = grid_for(a.queue_in_len, 8, 152 * 16);
+  if (mb == 2) { k_bfs_push<IDM, OFF, uint16_t><<<grid, 256, 0, st>>>(g, a); count_launch(); }
+  else if (mb == 4) { k_bfs_push<IDM, OFF, uint32_t><<<grid, 256, 0, st>>>(g, a); count_launch(); }
+  else { k_bfs_push<IDM, OFF, uint64_t><<<grid, 256, 0, st>>>(g, a); count_launch(); }
+  return cudaGetLastError();
+}
+template <int IDM, int OFF>
+cudaError_t launch_nbr_degrees(const GView& g, const NbrArgs& a, cudaStream_t st) {
+  if (a.k == 0) return cudaSuccess;
+  k_nbr_degrees<IDM, OFF><<<grid_for(a.k, 8, 152 * 16), 256, 0, st>>>(g, a);
+  count_launch();
+  return cudaGetLastError();
+}
+template <int IDM, int OFF>
+cudaError_t launch_nbr_decode(const GView& g, const NbrArgs& a, cudaStream_t st) {
+  if (a.k == 0) return cudaSuccess;
+  k_nbr_decode<IDM, OFF><<<grid_for(a.k, 8, 152 * 16), 256, 0, st>>>(g, a);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <int IDM, int OFF>
+const TravOps* make_ops() {
+  static const TravOps ops = {
+      &launch_pr_init<IDM, OFF>,  &launch_pr_pull<IDM, OFF>,     &launch_bfs_pull<IDM, OFF>,
+      &launch_bfs_push<IDM, OFF>, &launch_nbr_degrees<IDM, OFF>, &launch_nbr_decode<IDM, OFF>,
+  };
+  return &ops;
+}
+
+}  // namespace lg

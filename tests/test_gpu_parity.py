@@ -1,0 +1,310 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Bit-exact: packed A streams, offsets (packed and Elias-Fano, with samples),
+permutations, decoded neighborhoods and BFS depths.  PageRank (FP32 on the GPU,
+FP64 in the oracle): max relative error per vertex <= 1e-4 after the fixed
+iteration count.
+"""
+import itertools
+
+import numpy as np
+import pytest
+import torch
+
+import gen
+import oracle
+import paper_2010_15879_gb300 as lg
+from helpers import all_graphs, csr_from_edges
+
+pytestmark = pytest.mark.gpu
+
+PR_RTOL = 1e-4
+MODES = [(lg.LG_ID_GLOBAL, oracle.ID_GLOBAL), (lg.LG_ID_LOCAL, oracle.ID_LOCAL),
+         (lg.LG_ID_LOCAL_GAP, oracle.ID_LOCAL_GAP)]
+OFFS = [(lg.LG_OFF_PACKED, oracle.OFF_PACKED), (lg.LG_OFF_EF, oracle.OFF_EF)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    lg.load(auto_build=True)
+    torch.cuda.init()
+
+
+def dev(a, dt):
+    return torch.from_numpy(np.ascontiguousarray(a).view(dt)).cuda()
+
+
+def encode_both(n, rp, col, w=None, mode=0, off=0, relabel=False, sample=512, weight_bits=0):
+    g = lg.lg_encode(dev(rp, np.int64), dev(col, np.int32) if len(col) else torch.empty(0, dtype=torch.int32,
+                                                                                         device="cuda"),
+                     None if w is None else dev(w, np.int32), id_mode=MODES[mode][0], off_mode=OFFS[off][0],
+                     relabel=relabel, select_sample=sample, weight_bits=weight_bits)
+    e = oracle.encode(n, rp, col, w, id_mode=MODES[mode][1], off_mode=OFFS[off][1], relabel=relabel,
+                      sample=sample, weight_bits=weight_bits)
+    return g, e
+
+
+def assert_arrays_equal(g, e):
+    a = lg.lg_arrays_get(g)
+    st = lg.lg_stats_get(g)
+    assert st["bits_A"] == e.bits_A and st["s"] == e.s
+    assert np.array_equal(a["A"], e.A), "A stream"
+    if e.off_mode == oracle.OFF_PACKED:
+        assert st["w_O"] == e.w_O
+        assert np.array_equal(a["O"], e.O), "packed offsets"
+    else:
+        assert st["ef_l"] == e.ef_l
+        assert np.array_equal(a["ef_low"], e.ef_low), "EF low bits"
+        assert np.array_equal(a["ef_high"], e.ef_high), "EF high bits"
+        assert np.array_equal(a["ef_samples"], e.samples), "EF samples"
+    if e.relabel:
+        assert np.array_equal(a["perm"], e.perm) and np.array_equal(a["inv_perm"], e.inv_perm)
+
+
+def assert_neighbors(g, rp, col, n, w=None, vertices=None):
+    vs = np.arange(n, dtype=np.uint32) if vertices is None else np.asarray(vertices, dtype=np.uint32)
+    if w is None:
+        off, ids = lg.lg_neighbors(g, dev(vs, np.int32))
+    else:
+        off, ids, wts = lg.lg_neighbors(g, dev(vs, np.int32), with_weights=True)
+    off = off.cpu().numpy().view(np.uint64)
+    ids = ids.cpu().numpy().view(np.uint32)
+    deg = (rp[vs.astype(np.int64) + 1] - rp[vs]).astype(np.uint64)
+    assert np.array_equal(np.diff(off), deg)
+    want = np.concatenate([col[rp[v]:rp[v + 1]] for v in vs]) if len(vs) else np.zeros(0, np.uint32)
+    assert np.array_equal(ids, want)
+    if w is not None:
+        ww = np.concatenate([w[rp[v]:rp[v + 1]] for v in vs]) if len(vs) else np.zeros(0, np.uint32)
+        assert np.array_equal(wts.cpu().numpy().view(np.uint32), ww)
+
+
+def assert_bfs(g, n, rp, col, sources):
+    d = lg.lg_bfs(g, dev(np.asarray(sources, dtype=np.uint32), np.int32)).cpu().numpy().view(np.uint32)
+    for i, s in enumerate(sources):
+        want = oracle.bfs(n, rp, col, int(s))
+        assert np.array_equal(d[i], want), f"BFS depths from source {s}"
+
+
+def assert_pagerank(g, n, rp, col, iters=20, personalize=None, damping=0.85):
+    r = lg.lg_pagerank(g, damping, iters, personalize=personalize).cpu().numpy().astype(np.float64)
+    want = oracle.pagerank(n, rp, col, damping, iters, -1 if personalize is None else personalize)
+    nz = want > 0
+    rel = np.abs(r[nz] - want[nz]) / want[nz]
+    assert rel.max(initial=0.0) <= PR_RTOL, f"PageRank max rel err {rel.max():.3e}"
+    assert np.all(np.abs(r[~nz]) <= 1e-30)
+
+
+# ------------------------------------------------------------------ tiny graphs, exhaustive
+@pytest.mark.parametrize("n", [1, 2, 3, 4])
+def test_exhaustive_tiny_graphs_all_modes(n):
+    for edges in all_graphs(n):
+        rp, col, _ = csr_from_edges(n, edges)
+        for mode, off, relabel in itertools.product(range(3), range(2), (False, True)):
+            g, e = encode_both(n, rp, col, mode=mode, off=off, relabel=relabel, sample=64)
+            assert_arrays_equal(g, e)
+            assert_neighbors(g, rp, col, n)
+            g.free()
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_five_vertex_graphs_sampled(seed):
+    rng = np.random.default_rng(seed)
+    graphs = list(all_graphs(5))
+    for idx in rng.choice(len(graphs), size=40, replace=False):
+        rp, col, _ = csr_from_edges(5, graphs[idx])
+        for mode, off in itertools.product(range(3), range(2)):
+            g, e = encode_both(5, rp, col, mode=mode, off=off, relabel=bool(idx & 1), sample=64)
+            assert_arrays_equal(g, e)
+            assert_neighbors(g, rp, col, 5)
+            assert_bfs(g, 5, rp, col, list(range(5)))
+            assert_pagerank(g, 5, rp, col, iters=7)
+
+
+# ------------------------------------------------------------------ special shapes
+SHAPES = {
+    "single_vertex": (1, []),
+    "no_edges": (37, []),
+    "isolated_runs": (700, [(0, 699), (5, 6), (650, 3)]),
+    "star": (2000, [(0, i) for i in range(1, 2000)]),
+    "path": (1500, [(i, i + 1) for i in range(1499)]),
+    "complete": (64, [(i, j) for i in range(64) for j in range(i + 1, 64)]),
+    "pow2_n": (1024, [(i, (i * 37 + 11) % 1024) for i in range(1024)]),
+    "pow2_plus1_n": (1025, [(i, (i * 37 + 11) % 1025) for i in range(1025)]),
+}
+
+
+@pytest.mark.parametrize("shape", sorted(SHAPES))
+@pytest.mark.parametrize("mode,off", list(itertools.product(range(3), range(2))))
+def test_special_shapes(shape, mode, off):
+    n, edges = SHAPES[shape]
+    rp, col, _ = csr_from_edges(n, edges)
+    for relabel in (False, True):
+        g, e = encode_both(n, rp, col, mode=mode, off=off, relabel=relabel, sample=64)
+        assert_arrays_equal(g, e)
+        assert_neighbors(g, rp, col, n)
+        srcs = sorted({0, n - 1, n // 2})
+        assert_bfs(g, n, rp, col, srcs)
+        assert_pagerank(g, n, rp, col, iters=10)
+        g.free()
+
+
+# ------------------------------------------------------------------ R-MAT scale 16 (the small config)
+@pytest.fixture(scope="module")
+def rmat16():
+    return gen.rmat_s16_ef16()
+
+
+@pytest.mark.parametrize("mode,off", list(itertools.product(range(3), range(2))))
+def test_rmat16_streams_and_decode(rmat16, mode, off):
+    g0 = rmat16
+    for relabel in (False, True):
+        g, e = encode_both(g0.n, g0.row_ptr, g0.col, mode=mode, off=off, relabel=relabel)
+        assert_arrays_equal(g, e)
+        assert_neighbors(g, g0.row_ptr, g0.col, g0.n)
+        g.free()
+
+
+def test_rmat16_global_packed_widths(rmat16):
+    g, e = encode_both(rmat16.n, rmat16.row_ptr, rmat16.col, mode=0, off=0)
+    st = lg.lg_stats_get(g)
+    assert st["s"] == 16 and st["w_O"] == 21
+    assert st["bits_A"] == 16 * rmat16.arcs
+
+
+@pytest.mark.parametrize("mode,off", [(0, 0), (2, 1), (1, 1), (0, 1)])
+def test_rmat16_bfs_64_sources(rmat16, mode, off):
+    g0 = rmat16
+    src = gen.sources(g0, 64, seed=1)
+    g, _ = encode_both(g0.n, g0.row_ptr, g0.col, mode=mode, off=off, relabel=(mode == 2))
+    assert_bfs(g, g0.n, g0.row_ptr, g0.col, src)
+
+
+@pytest.mark.parametrize("S", [1, 3, 16, 17, 33, 64, 65, 100])
+def test_rmat16_bfs_source_counts(rmat16, S):
+    g0 = rmat16
+    src = gen.sources(g0, S, seed=S)
+    g, _ = encode_both(g0.n, g0.row_ptr, g0.col, mode=2, off=1, relabel=True)
+    assert_bfs(g, g0.n, g0.row_ptr, g0.col, src)
+
+
+@pytest.mark.parametrize("mode,off", list(itertools.product(range(3), range(2))))
+def test_rmat16_pagerank_20(rmat16, mode, off):
+    g0 = rmat16
+    g, _ = encode_both(g0.n, g0.row_ptr, g0.col, mode=mode, off=off, relabel=(off == 1))
+    assert_pagerank(g, g0.n, g0.row_ptr, g0.col, iters=20)
+
+
+def test_rmat16_personalized_pagerank(rmat16):
+    g0 = rmat16
+    g, _ = encode_both(g0.n, g0.row_ptr, g0.col, mode=2, off=1, relabel=True)
+    for s in gen.sources(g0, 3, seed=5):
+        assert_pagerank(g, g0.n, g0.row_ptr, g0.col, iters=10, personalize=int(s))
+
+
+def test_csr32_baseline_same_kernels(rmat16):
+    g0 = rmat16
+    for relabel in (False, True):
+        g = lg.lg_encode(dev(g0.row_ptr, np.int64), dev(g0.col, np.int32), id_mode=lg.LG_ID_CSR32, relabel=relabel)
+        assert_neighbors(g, g0.row_ptr, g0.col, g0.n)
+        assert_bfs(g, g0.n, g0.row_ptr, g0.col, gen.sources(g0, 16, seed=2))
+        assert_pagerank(g, g0.n, g0.row_ptr, g0.col, iters=20)
+
+
+# ------------------------------------------------------------------ weights
+@pytest.mark.parametrize("wbits,maxw", [(0, 1), (0, 255), (0, 256), (24, 200), (32, 7)])
+def test_weighted_global(wbits, maxw):
+    g0 = gen.rmat(11, 8, seed=7, weighted=True)
+    w = (g0.weights.astype(np.uint64) * maxw // 255).astype(np.uint32)
+    w[w == 0] = 1 if maxw >= 1 else 0
+    w[np.argmax(g0.col)] = maxw  # make the maximum appear (both arcs need not agree for decode parity)
+    for off in range(2):
+        g, e = encode_both(g0.n, g0.row_ptr, g0.col, w, mode=0, off=off, weight_bits=wbits)
+        assert_arrays_equal(g, e)
+        assert_neighbors(g, g0.row_ptr, g0.col, g0.n, w=w)
+        assert_bfs(g, g0.n, g0.row_ptr, g0.col, [0, 5])
+    g = lg.lg_encode(dev(g0.row_ptr, np.int64), dev(g0.col, np.int32), dev(w, np.int32), id_mode=lg.LG_ID_CSR32)
+    assert_neighbors(g, g0.row_ptr, g0.col, g0.n, w=w)
+
+
+def test_weighted_relabel_and_35_bit_records():
+    g0 = gen.rmat(12, 16, seed=8, weighted=True)
+    g, e = encode_both(g0.n, g0.row_ptr, g0.col, g0.weights, mode=0, off=1, relabel=True, weight_bits=23)
+    assert lg.lg_stats_get(g)["s"] + 23 == 35
+    assert_arrays_equal(g, e)
+    assert_neighbors(g, g0.row_ptr, g0.col, g0.n, w=g0.weights)
+
+
+# ------------------------------------------------------------------ queries and errors
+def test_neighbors_random_queries_with_repeats(rmat16):
+    g0 = rmat16
+    rng = np.random.default_rng(3)
+    q = rng.integers(0, g0.n, size=1000).astype(np.uint32)
+    q[:10] = q[0]
+    for mode, off in itertools.product(range(3), range(2)):
+        g, _ = encode_both(g0.n, g0.row_ptr, g0.col, mode=mode, off=off, relabel=(mode > 0))
+        assert_neighbors(g, g0.row_ptr, g0.col, g0.n, vertices=q)
+
+
+def test_neighbors_capacity_and_range_errors(rmat16):
+    g0 = rmat16
+    g, _ = encode_both(g0.n, g0.row_ptr, g0.col, mode=2, off=1)
+    lib = lg.load()
+    vs = dev(np.array([1, 2, 3], dtype=np.uint32), np.int32)
+    off = torch.empty(4, dtype=torch.int64, device="cuda")
+    ids = torch.empty(1, dtype=torch.int32, device="cuda")
+    st = torch.cuda.current_stream().cuda_stream
+    rc = lib.lg_neighbors(g.handle, vs.data_ptr(), 3, off.data_ptr(), ids.data_ptr(), None, 0, st)
+    assert rc == 4  # LG_ERANGE, offsets written
+    deg = g0.row_ptr[[2, 3, 4]] - g0.row_ptr[[1, 2, 3]]
+    assert np.array_equal(np.diff(off.cpu().numpy()), deg.astype(np.int64))
+    bad = dev(np.array([g0.n], dtype=np.uint32), np.int32)
+    with pytest.raises(lg.LgError) as ei:
+        lg.lg_neighbors(g, bad)
+    assert ei.value.status == 1
+    with pytest.raises(lg.LgError):
+        lg.lg_bfs(g, bad)
+    with pytest.raises(lg.LgError):
+        lg.lg_pagerank(g, 0.85, 3, personalize=g0.n)
+
+
+def test_invalid_csr_is_rejected_without_fault():
+    rp, col, _ = csr_from_edges(6, [(0, 1), (1, 2), (2, 3)])
+    bad_cases = []
+    c = col.copy(); c[0] = 99; bad_cases.append((rp, c))              # id out of range
+    c = col.copy(); c[1], c[2] = c[2], c[1]; bad_cases.append((rp, c))  # row out of order
+    r = rp.copy(); r[2] = r[1] - 1 if r[1] else 0; bad_cases.append((r, col))  # row_ptr decreasing
+    r = rp.copy(); r[-1] = 10**9; bad_cases.append((r, col))          # row_ptr past the end
+    for r, c in bad_cases:
+        with pytest.raises(lg.LgError) as ei:
+            lg.lg_encode(dev(r, np.int64), dev(c, np.int32), id_mode=lg.LG_ID_LOCAL_GAP, off_mode=lg.LG_OFF_EF)
+        assert ei.value.status == 1
+    # asymmetric input is caught when asked
+    rp2 = np.array([0, 1, 1], dtype=np.uint64)
+    col2 = np.array([1], dtype=np.uint32)
+    with pytest.raises(lg.LgError):
+        lg.lg_encode(dev(rp2, np.int64), dev(col2, np.int32), check_symmetric=True)
+    # the device is still usable afterwards
+    g = lg.lg_encode(dev(rp, np.int64), dev(col, np.int32))
+    assert_neighbors(g, rp, col, 6)
+
+
+def test_unsupported_and_bad_options():
+    rp, col, _ = csr_from_edges(4, [(0, 1)])
+    w = np.array([3, 3], dtype=np.uint32)
+    with pytest.raises(lg.LgError) as ei:
+        lg.lg_encode(dev(rp, np.int64), dev(col, np.int32), dev(w, np.int32), id_mode=lg.LG_ID_LOCAL)
+    assert ei.value.status == 6
+    with pytest.raises(lg.LgError):
+        lg.lg_encode(dev(rp, np.int64), dev(col, np.int32), off_mode=lg.LG_OFF_EF, select_sample=100)
+    with pytest.raises(lg.LgError):
+        lg.lg_encode(dev(rp, np.int64), dev(col, np.int32), dev(w, np.int32), weight_bits=1)
+
+
+def test_pagerank_zero_iterations_and_sum_rule(rmat16):
+    g0 = rmat16
+    g, _ = encode_both(g0.n, g0.row_ptr, g0.col, mode=2, off=1, relabel=True)
+    r0 = lg.lg_pagerank(g, 0.85, 0).cpu().numpy()
+    assert np.allclose(r0, 1.0 / g0.n)
+    r = lg.lg_pagerank(g, 0.85, 20).cpu().numpy().astype(np.float64)
+    iso = g0.degrees() == 0
+    assert abs(r.sum() - (1.0 - iso.sum() * 0.85 / g0.n)) < 1e-3
