@@ -83,7 +83,8 @@ typedef struct {
                                   64 per select sample)                                     */
     uint64_t bytes_A, bytes_O; /* device bytes held, with padding and guard words           */
     uint64_t bytes_perm;       /* device bytes of the permutation (0 without relabel)       */
-    uint64_t bytes_total;      /* bytes_A + bytes_O + bytes_perm                            */
+    uint64_t bytes_total;      /* bytes_A + bytes_O + bytes_perm + bytes_schedule (+ CSR32
+                                  weights)                                                  */
     uint64_t max_degree;
     uint32_t id_mode, off_mode, relabel, weighted;
     uint32_t s;                /* global ID width, max(1, bits(n - 1))                      */
@@ -93,6 +94,8 @@ typedef struct {
     uint32_t ef_l;             /* Elias-Fano low-bit count (0 for packed)                   */
     uint32_t select_sample;
     double bits_per_arc;       /* (bits_A + bits_O) / arcs                                  */
+    uint64_t bytes_schedule;   /* device bytes of the heavy-vertex decode schedule (derived
+                                  from A and O at encode time; not part of the format)      */
 } lg_stats;
 
 /* Read-only device views of the encoded arrays, for inspection and parity

@@ -51,7 +51,7 @@ class _Stats(ctypes.Structure):
                 ("bytes_O", _u64), ("bytes_perm", _u64), ("bytes_total", _u64), ("max_degree", _u64),
                 ("id_mode", _u32), ("off_mode", _u32), ("relabel", _u32), ("weighted", _u32), ("s", _u32),
                 ("H", _u32), ("omega", _u32), ("w_O", _u32), ("ef_l", _u32), ("select_sample", _u32),
-                ("bits_per_arc", _dbl)]
+                ("bits_per_arc", _dbl), ("bytes_schedule", _u64)]
 
 
 class _Arrays(ctypes.Structure):

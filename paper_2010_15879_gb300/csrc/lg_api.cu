@@ -11,6 +11,7 @@
 #include <new>
 
 #include "lg_internal.h"
+#include "lg_traverse.cuh"
 
 namespace {
 
@@ -85,9 +86,15 @@ uint32_t env_u32(const char* name, uint32_t dflt) {
   if (!s || !*s) return dflt;
   return (uint32_t)strtoul(s, nullptr, 10);
 }
-uint32_t heavy_min() {
-  static const uint32_t v = env_u32("LG_HEAVY_MIN", 128);
-  return v ? v : 128;
+// Light/heavy degree limit and the split size of the heavy-vertex schedule,
+// read at every encode (LG_HEAVY_MIN, LG_HEAVY_SEG).
+uint32_t heavy_min_env() {
+  const uint32_t v = env_u32("LG_HEAVY_MIN", 256);
+  return v ? v : 256;
+}
+uint32_t heavy_seg_env() {
+  const uint32_t v = env_u32("LG_HEAVY_SEG", 4096);
+  return v >= 32 ? v : 4096;
 }
 uint32_t pull_divisor() {
   static const uint32_t v = env_u32("LG_BFS_PULL_DIV", 64);
@@ -120,7 +127,78 @@ GView make_view(const lg_graph* g) {
   v.ef_high_words32 = (g->ef_high_bits + 31) / 32;
   v.s = g->s; v.H = g->H; v.omega = g->omega; v.r = g->r; v.w_O = g->w_O; v.ef_l = g->ef_l;
   v.sample_log2 = g->sample_log2;
+  v.items = g->items;
+  v.multi = g->multi;
+  v.n_items = g->n_items;
+  v.n_multi = g->n_multi;
+  v.heavy_min = g->heavy_min;
+  v.heavy_seg = g->heavy_seg;
   return v;
+}
+
+// ---------------------------------------------------------------- split vertices
+// A vertex split into several heavy items: its items' partial sums are added
+// in item order (deterministic), then the vertex is finished.
+__global__ void k_pr_finish_multi(GView g, PrArgs a) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.n_multi; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t first = g.multi[i];
+    const HeavyItem h = g.items[first];
+    float s = 0.f;
+    for (uint32_t k = 0; k < h.nitems; k++) s += a.part[first + k];
+    pr_finish(g, a, h.v, h.deg, s);
+  }
+}
+
+cudaError_t pr_finish_multi(const GView& g, const PrArgs& a, cudaStream_t st) {
+  if (g.n_multi == 0) return cudaSuccess;
+  k_pr_finish_multi<<<grid_for(g.n_multi, 256, 4096), 256, 0, st>>>(g, a);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <typename M>
+__global__ void k_bfs_finish_multi(GView g, BfsArgs a) {
+  M* hacc = reinterpret_cast<M*>(a.hacc);
+  const M* vis = reinterpret_cast<const M*>(a.vis);
+  M* fout = reinterpret_cast<M*>(a.front_out);
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.n_multi; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t v = g.items[g.multi[i]].v;
+    const M need = (M)((M)a.all_mask & (M)~vis[v]);
+    const M acc = hacc[i];
+    hacc[i] = 0;
+    if (need == 0) fout[v] = 0;
+    else bfs_finish<M>(g, a, v, need, acc, nullptr, nullptr, nullptr);
+  }
+}
+
+cudaError_t bfs_finish_multi(const GView& g, const BfsArgs& a, int mb, cudaStream_t st) {
+  if (g.n_multi == 0) return cudaSuccess;
+  const unsigned grid = grid_for(g.n_multi, 256, 4096);
+  if (mb == 2) { k_bfs_finish_multi<uint16_t><<<grid, 256, 0, st>>>(g, a); count_launch(); }
+  else if (mb == 4) { k_bfs_finish_multi<uint32_t><<<grid, 256, 0, st>>>(g, a); count_launch(); }
+  else { k_bfs_finish_multi<uint64_t><<<grid, 256, 0, st>>>(g, a); count_launch(); }
+  return cudaGetLastError();
+}
+
+// carries of split gap-coded vertices: exclusive sums of the item sums, in order
+__global__ void k_plan_carry_scan(HeavyItem* items, const uint32_t* multi, uint64_t n_multi, const uint32_t* segsum) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_multi; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t first = multi[i];
+    const uint32_t k = items[first].nitems;
+    uint32_t run = 0;
+    for (uint32_t j = 0; j < k; j++) {
+      items[first + j].carry = run;
+      run += segsum[first + j];
+    }
+  }
+}
+
+cudaError_t plan_carry_scan(HeavyItem* items, const uint32_t* multi, uint64_t n_multi, const uint32_t* segsum,
+                            cudaStream_t st) {
+  if (n_multi == 0) return cudaSuccess;
+  k_plan_carry_scan<<<grid_for(n_multi, 256, 4096), 256, 0, st>>>(items, multi, n_multi, segsum);
+  count_launch();
+  return cudaGetLastError();
 }
 
 const TravOps* trav_ops(int id_mode, int off_mode) {
@@ -226,6 +304,7 @@ extern "C" void lg_free(lg_graph* g) {
   cudaDeviceSynchronize();
   cudaFree(g->A); cudaFree(g->O); cudaFree(g->ef_low); cudaFree(g->ef_high); cudaFree(g->ef_samples);
   cudaFree(g->perm); cudaFree(g->inv_perm); cudaFree(g->W);
+  cudaFree(g->items); cudaFree(g->multi);
   delete g;
 }
 
@@ -238,7 +317,8 @@ extern "C" lg_status lg_stats_get(const lg_graph* g, lg_stats* out) {
   out->bytes_A = g->words_A * 8;
   out->bytes_O = (g->words_O + g->words_ef_low + g->words_ef_high + g->words_ef_samples) * 8;
   out->bytes_perm = g->perm ? 2 * g->n * sizeof(uint32_t) : 0;
-  out->bytes_total = out->bytes_A + out->bytes_O + out->bytes_perm + (g->W ? g->arcs * 4 : 0);
+  out->bytes_schedule = g->n_items * sizeof(HeavyItem) + g->n_multi * sizeof(uint32_t);
+  out->bytes_total = out->bytes_A + out->bytes_O + out->bytes_perm + out->bytes_schedule + (g->W ? g->arcs * 4 : 0);
   out->max_degree = g->max_degree;
   out->id_mode = g->id_mode; out->off_mode = g->off_mode; out->relabel = g->relabel; out->weighted = g->weighted;
   out->s = g->s; out->H = g->H; out->omega = g->omega; out->w_O = g->w_O; out->ef_l = g->ef_l;
@@ -256,6 +336,52 @@ extern "C" lg_status lg_arrays_get(const lg_graph* g, lg_arrays* out) {
   out->ef_high = g->ef_high; out->words_ef_high = g->words_ef_high;
   out->ef_samples = g->ef_samples; out->words_ef_samples = g->words_ef_samples;
   out->perm = g->perm; out->inv_perm = g->inv_perm;
+  return LG_OK;
+}
+
+// Heavy-vertex schedule, derived from the encoded arrays: every vertex of
+// degree > heavy_min becomes ceil(d / HEAVY_SEG) items, listed in vertex order.
+static lg_status build_schedule(lg_graph* g, cudaStream_t st) {
+  g->heavy_min = heavy_min_env();
+  g->heavy_seg = heavy_seg_env();
+  const uint64_t ntiles = (g->n + LG_TILE_V - 1) / LG_TILE_V;
+  Tmp t_cnt(st), t_mcnt(st), t_off(st), t_moff(st), t_stmp(st), t_seg(st);
+  LG_TRY(t_cnt.alloc(ntiles * sizeof(uint32_t)));
+  LG_TRY(t_mcnt.alloc(ntiles * sizeof(uint32_t)));
+  LG_TRY(t_off.alloc((ntiles + 1) * sizeof(uint64_t)));
+  LG_TRY(t_moff.alloc((ntiles + 1) * sizeof(uint64_t)));
+  LG_TRY(t_stmp.alloc(scan_tmp_words(ntiles) * sizeof(uint64_t)));
+  PlanArgs p;
+  memset(&p, 0, sizeof(p));
+  p.tile_count = t_cnt.as<uint32_t>();
+  p.multi_count = t_mcnt.as<uint32_t>();
+  p.tile_off = t_off.as<uint64_t>();
+  p.multi_off = t_moff.as<uint64_t>();
+  GView v = make_view(g);
+  const TravOps* ops = trav_ops((int)g->id_mode, (int)g->off_mode);
+  LG_TRY(ops->plan_count(v, p, st));
+  LG_TRY(scan_excl_u32(p.tile_count, ntiles, t_off.as<uint64_t>(), t_stmp.as<uint64_t>(), st));
+  LG_TRY(scan_excl_u32(p.multi_count, ntiles, t_moff.as<uint64_t>(), t_stmp.as<uint64_t>(), st));
+  uint64_t tot[2] = {0, 0};
+  LG_TRY(cudaMemcpyAsync(&tot[0], t_off.as<uint64_t>() + ntiles, 8, cudaMemcpyDeviceToHost, st));
+  LG_TRY(cudaMemcpyAsync(&tot[1], t_moff.as<uint64_t>() + ntiles, 8, cudaMemcpyDeviceToHost, st));
+  LG_TRY(cudaStreamSynchronize(st));
+  g->n_items = tot[0];
+  g->n_multi = tot[1];
+  if (g->n_items == 0) return LG_OK;
+  LG_TRY(cudaMalloc((void**)&g->items, g->n_items * sizeof(HeavyItem)));
+  if (g->n_multi) LG_TRY(cudaMalloc((void**)&g->multi, g->n_multi * sizeof(uint32_t)));
+  p.items = g->items;
+  p.multi = g->multi;
+  LG_TRY(ops->plan_fill(v, p, st));
+  if (g->n_multi && g->id_mode == ID_LOCAL_GAP) {
+    LG_TRY(t_seg.alloc(g->n_items * sizeof(uint32_t)));
+    p.segsum = t_seg.as<uint32_t>();
+    v = make_view(g);
+    LG_TRY(ops->plan_carry(v, p, st));
+    LG_TRY(plan_carry_scan(g->items, g->multi, g->n_multi, p.segsum, st));
+  }
+  LG_TRY(cudaStreamSynchronize(st));
   return LG_OK;
 }
 
@@ -327,7 +453,7 @@ static lg_status encode_impl(lg_graph* g, const uint64_t* row_ptr, const uint32_
     }
     g->off_mode = OFF_ROWPTR;
     LG_TRY(cudaStreamSynchronize(st));
-    return LG_OK;
+    return build_schedule(g, st);
   }
 
   // ---- A stream
@@ -384,7 +510,7 @@ static lg_status encode_impl(lg_graph* g, const uint64_t* row_ptr, const uint32_
     g->bits_O = g->ef_low_bits + g->ef_high_bits + 64 * g->n_samples;
   }
   LG_TRY(cudaStreamSynchronize(st));
-  return LG_OK;
+  return build_schedule(g, st);
 }
 
 extern "C" lg_status lg_encode(const uint64_t* row_ptr, const uint32_t* col, const uint32_t* weights, uint64_t n,
@@ -473,7 +599,7 @@ extern "C" lg_status lg_bfs(const lg_graph* g, const uint32_t* sources, uint32_t
   const uint64_t n = g->n;
   const uint32_t maxb = S >= 64 ? 64 : S;
   const int mb = maxb <= 16 ? 2 : (maxb <= 32 ? 4 : 8);
-  Tmp t_src(st), t_vis(st), t_fa(st), t_fb(st), t_qa(st), t_qb(st), t_small(st), t_depth(st);
+  Tmp t_src(st), t_vis(st), t_fa(st), t_fb(st), t_qa(st), t_qb(st), t_small(st), t_depth(st), t_hacc(st);
   LG_TRY(t_src.alloc(S * sizeof(uint32_t)));
   LG_TRY(t_vis.alloc(n * mb + 16));
   LG_TRY(t_fa.alloc(n * mb + 16));
@@ -482,6 +608,8 @@ extern "C" lg_status lg_bfs(const lg_graph* g, const uint32_t* sources, uint32_t
   LG_TRY(t_qb.alloc(n * sizeof(uint32_t)));
   LG_TRY(t_small.alloc(64));
   if (g->relabel) LG_TRY(t_depth.alloc((uint64_t)maxb * n * sizeof(uint32_t)));
+  LG_TRY(t_hacc.alloc(g->n_multi * mb + 16));
+  LG_TRY(cudaMemsetAsync(t_hacc.p, 0, g->n_multi * mb + 16, st));
   int* d_err = t_small.as<int>();
   uint32_t* counters = reinterpret_cast<uint32_t*>(t_small.as<char>() + 16);
   LG_TRY(cudaMemsetAsync(t_small.p, 0, 64, st));
@@ -518,14 +646,18 @@ extern "C" lg_status lg_bfs(const lg_graph* g, const uint32_t* sources, uint32_t
     a.all_mask = Sb == 64 ? ~0ull : ((1ull << Sb) - 1ull);
     a.S = Sb;
     a.counters = counters;
-    a.heavy_min = heavy_min();
+    a.hacc = t_hacc.p;
     a.err = d_err;
     for (uint32_t level = 0; nq > 0; level++) {
       LG_TRY(cudaMemsetAsync(counters, 0, 8, st));
       a.front_in = cur; a.front_out = nxt; a.level = level;
       a.queue_in = qcur; a.queue_in_len = nq; a.queue_out = qnxt;
-      if ((uint64_t)nq > pull_threshold) LG_TRY(ops->bfs_pull(v, a, mb, st));
-      else LG_TRY(ops->bfs_push(v, a, mb, st));
+      if ((uint64_t)nq > pull_threshold) {
+        LG_TRY(ops->bfs_pull(v, a, mb, st));
+        LG_TRY(bfs_finish_multi(v, a, mb, st));
+      } else {
+        LG_TRY(ops->bfs_push(v, a, mb, st));
+      }
       LG_TRY(cudaMemcpyAsync(hc, counters, 8, cudaMemcpyDeviceToHost, st));
       // the frontier just consumed becomes the next output buffer: clear it
       if ((uint64_t)nq * 16 < n) {
@@ -575,9 +707,10 @@ extern "C" lg_status lg_pagerank(const lg_graph* g, float damping, uint32_t iter
       personal = personal_orig;
     }
   }
-  Tmp ca(st), cb(st);
+  Tmp ca(st), cb(st), tpart(st);
   LG_TRY(ca.alloc(n * sizeof(float)));
   LG_TRY(cb.alloc(n * sizeof(float)));
+  if (g->n_multi) LG_TRY(tpart.alloc(g->n_items * sizeof(float)));
   const GView v = make_view(g);
   const TravOps* ops = trav_ops((int)g->id_mode, (int)g->off_mode);
   PrArgs a;
@@ -586,7 +719,7 @@ extern "C" lg_status lg_pagerank(const lg_graph* g, float damping, uint32_t iter
   a.personal = personal;
   a.base_all = personal < 0 ? (1.0f - damping) / (float)n : (1.0f - damping);
   a.r0_all = 1.0f / (float)n;
-  a.heavy_min = heavy_min();
+  a.part = tpart.as<float>();
   a.ranks_out = ranks;
   a.contrib_out = ca.as<float>();
   LG_TRY(ops->pr_init(v, a, st));
@@ -597,6 +730,7 @@ extern "C" lg_status lg_pagerank(const lg_graph* g, float damping, uint32_t iter
     a.contrib_out = nxt;
     a.last = (t + 1 == iters);
     LG_TRY(ops->pr_pull(v, a, st));
+    LG_TRY(pr_finish_multi(v, a, st));
     float* tt = cur; cur = nxt; nxt = tt;
   }
   return LG_OK;

@@ -7,8 +7,8 @@
 // 32-bit words and use one funnel shift per field.
 //
 // Every stream allocation is padded to an even number of u64 words and
-// followed by two zero guard words, so any read of word i+1 (or of the 16-byte
-// chunk holding word i) for a data word i stays inside the allocation.
+// followed by two zero guard words, so any read of word i+1, or of the aligned
+// 32-byte sector holding word i, for a data word i stays inside the allocation.
 #pragma once
 
 #include <cstdint>
@@ -32,6 +32,24 @@ enum DevErr : int {
   DERR_INTERNAL = 64,   // a structural invariant did not hold (bounded loop ran out)
 };
 
+constexpr int LG_TILE_V = 512;  // vertices per tile of the pull kernels
+
+// One unit of the heavy-vertex schedule: fields [f0, f0 + nf) of vertex v.
+// Vertices whose degree exceeds the light limit are split into items of at
+// most heavy_seg fields so that no single warp walks a whole hub; `carry` is
+// the absolute neighbor ID just before field f0 (gap-coded IDs only).
+struct HeavyItem {
+  uint64_t bit;        // stream bit of the vertex's first field
+  uint32_t v;          // stored label
+  uint32_t f0, nf;     // field range
+  uint32_t carry;      // running ID before f0 (local-gap mode)
+  uint32_t deg;        // degree of v
+  uint32_t first;      // index of the vertex's first item
+  uint32_t nitems;     // items of this vertex
+  uint32_t w;          // field width (gap width for local-gap)
+  uint32_t slot;       // index among the split vertices (0xffffffff if not split)
+};
+
 // Read-only view of an encoded graph, passed by value to kernels.
 struct GView {
   const uint32_t* A32;        // A stream as 32-bit words (CSR32: the col array)
@@ -43,9 +61,14 @@ struct GView {
   const uint32_t* perm;       // original -> stored (nullptr without relabel)
   const uint32_t* inv_perm;   // stored -> original
   const uint32_t* W32;        // CSR32 only: 32-bit weights beside the IDs (nullptr if none)
+  const HeavyItem* items;     // heavy-vertex schedule (nullptr if none)
+  const uint32_t* multi;      // first item of every vertex split into > 1 item
   uint64_t n, arcs;
   uint64_t ef_high_words32;   // number of valid 32-bit words of the high vector
+  uint64_t n_items, n_multi;
   uint32_t s, H, omega, r, w_O, ef_l, sample_log2;
+  uint32_t heavy_min;         // degrees above this are in the schedule
+  uint32_t heavy_seg;         // max fields per schedule item
 };
 
 __device__ __forceinline__ uint32_t bits_u32(uint32_t x) { return 32u - __clz(x); }
@@ -86,41 +109,82 @@ __device__ __forceinline__ uint32_t select_in_u32(uint32_t x, uint32_t r) {
 __device__ __forceinline__ uint4 ldg128(const uint32_t* p) { return __ldg(reinterpret_cast<const uint4*>(p)); }
 
 // ---------------------------------------------------------------------------
-// Sequential bit reader: one thread walks a run of fields.  Refills 32 bits at
-// a time from a 16-byte register chunk, so a warp whose lanes walk different
-// runs issues one 128-bit load per ~128 bits consumed per lane.
+// L2 eviction priority (a per-instruction cache policy, no device state): the
+// compressed stream is read once per sweep and marked evict-first, so it does
+// not push the gathered per-vertex arrays out of L2.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t policy_stream() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_keep() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint4 ldg128_stream(const uint32_t* p, uint64_t pol) {
+  uint4 v;
+  asm("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+      : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+      : "l"(p), "l"(pol));
+  return v;
+}
+// Gathers of per-vertex arrays use the default read-only path: on this GPU a
+// no-allocate L1 hint made 392M random 4-byte gathers 3.5x slower (measured),
+// so L1 allocation is kept for them.
+__device__ __forceinline__ float ldg_gather(const float* p, uint64_t) { return __ldg(p); }
+__device__ __forceinline__ uint16_t ldg_gather(const uint16_t* p, uint64_t) { return __ldg(p); }
+__device__ __forceinline__ uint32_t ldg_gather(const uint32_t* p, uint64_t) { return __ldg(p); }
+__device__ __forceinline__ uint64_t ldg_gather(const uint64_t* p, uint64_t) {
+  return (uint64_t)__ldg(reinterpret_cast<const unsigned long long*>(p));
+}
+
+// ---------------------------------------------------------------------------
+// Sequential bit reader: one thread walks a run of fields.  The stream is
+// fetched in whole 32-byte sectors (two 128-bit loads of one aligned sector)
+// into eight register words, and moved into a 64-bit bit buffer 32 bits at a
+// time, so a warp whose lanes walk different runs issues one sector request
+// per lane per 256 bits consumed.
 // ---------------------------------------------------------------------------
 struct BitReader {
   const uint32_t* A;
+  uint64_t pol;       // L2 policy of the stream loads
   uint64_t wnext;     // index of the next 32-bit word to append to buf
   uint64_t buf;       // unread bits, LSB first
   uint32_t nb;        // number of valid bits in buf
-  uint4 q;            // words wnext.. of the current 16-byte chunk (shifted down)
-  uint32_t nq;        // valid words in q
+  uint4 q0, q1;       // next words of the current sector, q0 first (shifted down)
+  uint32_t n0, n1;    // valid words in q0, q1
 
-  __device__ __forceinline__ void load_chunk() {
-    const uint64_t c = wnext & ~3ull;
-    uint4 v = ldg128(A + c);
-    const uint32_t skip = (uint32_t)(wnext - c);
-    // drop words before wnext
-    if (skip >= 1) { v.x = v.y; v.y = v.z; v.z = v.w; }
-    if (skip >= 2) { v.x = v.y; v.y = v.z; }
-    if (skip >= 3) { v.x = v.y; }
-    q = v;
-    nq = 4u - skip;
+  __device__ __forceinline__ void load_sector() {
+    const uint64_t c = wnext & ~7ull;
+    uint4 a = ldg128_stream(A + c, pol);
+    uint4 b = ldg128_stream(A + c + 4, pol);
+    uint32_t skip = (uint32_t)(wnext - c);
+    if (skip >= 4) { a = b; n1 = 0; skip -= 4; } else { n1 = 4; }
+    if (skip >= 1) { a.x = a.y; a.y = a.z; a.z = a.w; }
+    if (skip >= 2) { a.x = a.y; a.y = a.z; }
+    if (skip >= 3) { a.x = a.y; }
+    q0 = a;
+    q1 = b;
+    n0 = 4u - skip;
   }
   __device__ __forceinline__ void push_word() {
-    if (nq == 0) load_chunk();
-    buf |= (uint64_t)q.x << nb;
+    if (n0 == 0) {
+      if (n1) { q0 = q1; n0 = n1; n1 = 0; }
+      else load_sector();
+    }
+    buf |= (uint64_t)q0.x << nb;
     nb += 32;
-    q.x = q.y; q.y = q.z; q.z = q.w;
-    nq--;
+    q0.x = q0.y; q0.y = q0.z; q0.z = q0.w;
+    n0--;
     wnext++;
   }
-  __device__ __forceinline__ void init(const uint32_t* base, uint64_t bit) {
+  __device__ __forceinline__ void init(const uint32_t* base, uint64_t bit, uint64_t policy) {
     A = base;
+    pol = policy;
     wnext = bit >> 5;
-    buf = 0; nb = 0; nq = 0;
+    buf = 0; nb = 0; n0 = 0; n1 = 0;
     push_word();
     const uint32_t sh = (uint32_t)bit & 31u;
     buf >>= sh;
@@ -130,7 +194,7 @@ struct BitReader {
   __device__ __forceinline__ uint32_t get(uint32_t w) {
     if (nb < w) push_word();
     const uint32_t v = (uint32_t)buf & mask_lo(w);
-    buf = (w >= 64) ? 0 : (buf >> w);
+    buf >>= w;
     nb -= w;
     return v;
   }

@@ -108,41 +108,54 @@ cudaError_t scan_excl_u32(const uint32_t* in, uint64_t n, uint64_t* out, uint64_
 // =========================================================================
 // validation (one warp per row; never reads outside the given arrays)
 // =========================================================================
+// One warp takes 32 consecutive rows: lane l loads row l's bounds, then the
+// warp walks the rows with lanes over the entries.
 __global__ void __launch_bounds__(256) k_validate(const uint64_t* __restrict__ rp, const uint32_t* __restrict__ col,
                                                   const uint32_t* __restrict__ w, uint64_t n, uint64_t arcs,
                                                   uint32_t wbits, int* err, unsigned long long* max_deg,
                                                   uint32_t* max_w) {
   const int lane = threadIdx.x & 31;
   const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-  uint32_t wmax = 0;
+  uint32_t wmax = 0, dmax = 0;
   int flags = 0;
-  for (uint64_t v = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); v < n; v += warps) {
-    const uint64_t lo = rp[v], hi = rp[v + 1];
-    const bool bad = hi < lo || hi > arcs || (v == 0 && lo != 0) || (v == n - 1 && hi != arcs);
-    if (bad) { flags |= DERR_ROWPTR; continue; }
-    if (lane == 0) atomicMax(max_deg, (unsigned long long)(hi - lo));
-    for (uint64_t j = lo + lane; j < hi; j += 32) {
-      const uint32_t c = col[j];
-      if (c >= n) flags |= DERR_COL_RANGE;
-      if (j > lo && col[j - 1] >= c) flags |= DERR_UNSORTED;
-      if (w) {
-        const uint32_t x = w[j];
-        wmax = max(wmax, x);
-        if (wbits && wbits < 32 && (x >> wbits)) flags |= DERR_WEIGHT;
+  for (uint64_t v0 = ((uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; v0 < n; v0 += warps * 32) {
+    const uint64_t mv = v0 + lane;
+    uint64_t mlo = 0, mhi = 0;
+    if (mv < n) { mlo = rp[mv]; mhi = rp[mv + 1]; }
+    const bool mbad = mv < n && (mhi < mlo || mhi > arcs || (mv == 0 && mlo != 0) || (mv == n - 1 && mhi != arcs) ||
+                                 mhi - mlo > n);
+    if (mbad) flags |= DERR_ROWPTR;
+    if (mv < n && !mbad) dmax = max(dmax, (uint32_t)(mhi - mlo));
+    const uint32_t badmask = __ballot_sync(LG_FULL_MASK, mbad);
+    const int rows = (int)min((uint64_t)32, n - v0);
+    for (int r = 0; r < rows; r++) {
+      const uint64_t lo = __shfl_sync(LG_FULL_MASK, mlo, r), hi = __shfl_sync(LG_FULL_MASK, mhi, r);
+      if (badmask >> r & 1u) continue;
+      for (uint64_t j = lo + lane; j < hi; j += 32) {
+        const uint32_t c = col[j];
+        if (c >= n) flags |= DERR_COL_RANGE;
+        if (j > lo && col[j - 1] >= c) flags |= DERR_UNSORTED;
+        if (w) {
+          const uint32_t x = w[j];
+          wmax = max(wmax, x);
+          if (wbits && wbits < 32 && (x >> wbits)) flags |= DERR_WEIGHT;
+        }
       }
     }
   }
   flags = __reduce_or_sync(LG_FULL_MASK, flags);
   wmax = __reduce_max_sync(LG_FULL_MASK, wmax);
+  dmax = __reduce_max_sync(LG_FULL_MASK, dmax);
   if (lane == 0) {
     if (flags) atomicOr(err, flags);
     if (w) atomicMax(max_w, wmax);
+    if (dmax) atomicMax(max_deg, (unsigned long long)dmax);
   }
 }
 
 cudaError_t enc_validate(const uint64_t* rp, const uint32_t* col, const uint32_t* w, uint64_t n, uint64_t arcs,
                          uint32_t wbits, int* err, unsigned long long* max_deg, uint32_t* max_w, cudaStream_t st) {
-  k_validate<<<grid_for(n, 8, 152 * 64), 256, 0, st>>>(rp, col, w, n, arcs, wbits, err, max_deg, max_w);
+  k_validate<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(rp, col, w, n, arcs, wbits, err, max_deg, max_w);
   count_launch();
   return cudaGetLastError();
 }
@@ -184,28 +197,35 @@ __global__ void __launch_bounds__(256) k_local_lengths(const uint64_t* __restric
                                                        uint64_t* __restrict__ len) {
   const int lane = threadIdx.x & 31;
   const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-  for (uint64_t v = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); v < n; v += warps) {
-    const uint64_t lo = rp[v], hi = rp[v + 1], d = hi - lo;
-    uint32_t w = 0;
-    if (!gap) {
-      if (d > 0) w = max(1u, bits_u32(col[hi - 1]));
-    } else if (d >= 2) {
-      uint32_t mg = 0;
-      for (uint64_t j = lo + 1 + lane; j < hi; j += 32) mg = max(mg, col[j] - col[j - 1]);
-      mg = __reduce_max_sync(LG_FULL_MASK, mg);
-      w = max(1u, bits_u32(mg));
+  for (uint64_t v0 = ((uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; v0 < n; v0 += warps * 32) {
+    const uint64_t mv = v0 + lane;
+    uint64_t mlo = 0, mhi = 0;
+    if (mv < n) { mlo = rp[mv]; mhi = rp[mv + 1]; }
+    uint32_t mw = 0;  // lane l ends with the width of row v0 + l
+    if (!gap && mv < n && mhi > mlo) mw = max(1u, bits_u32(col[mhi - 1]));
+    const int rows = (int)min((uint64_t)32, n - v0);
+    if (gap) {
+      for (int r = 0; r < rows; r++) {
+        const uint64_t lo = __shfl_sync(LG_FULL_MASK, mlo, r), hi = __shfl_sync(LG_FULL_MASK, mhi, r);
+        if (hi - lo < 2) continue;
+        uint32_t mg = 0;
+        for (uint64_t j = lo + 1 + lane; j < hi; j += 32) mg = max(mg, col[j] - col[j - 1]);
+        mg = __reduce_max_sync(LG_FULL_MASK, mg);
+        if (lane == r) mw = max(1u, bits_u32(mg));
+      }
     }
-    if (lane == 0) {
-      wid[v] = (uint8_t)w;
-      len[v] = gap ? (uint64_t)H + (d >= 1 ? s : 0) + (d >= 2 ? (d - 1) * (uint64_t)w : 0)
-                   : (uint64_t)H + d * (uint64_t)w;
+    if (mv < n) {
+      const uint64_t d = mhi - mlo;
+      wid[mv] = (uint8_t)mw;
+      len[mv] = gap ? (uint64_t)H + (d >= 1 ? s : 0) + (d >= 2 ? (d - 1) * (uint64_t)mw : 0)
+                    : (uint64_t)H + d * (uint64_t)mw;
     }
   }
 }
 
 cudaError_t enc_local_lengths(const uint64_t* rp, const uint32_t* col, uint64_t n, int gap, uint32_t s, uint32_t H,
                               uint8_t* wid, uint64_t* len, cudaStream_t st) {
-  k_local_lengths<<<grid_for(n, 8, 152 * 64), 256, 0, st>>>(rp, col, n, gap, s, H, wid, len);
+  k_local_lengths<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(rp, col, n, gap, s, H, wid, len);
   count_launch();
   return cudaGetLastError();
 }
@@ -281,47 +301,55 @@ cudaError_t enc_pack_u64(const uint64_t* vals, uint64_t count, uint32_t w, uint6
 // =========================================================================
 constexpr int PW = 1024;
 
-__device__ __forceinline__ void put_clip(unsigned long long* win, uint64_t w0, uint64_t wcnt, uint64_t p,
-                                         uint32_t wbits, uint64_t val) {
+// OR a w <= 32 bit field at stream bit p into the window (32-bit words
+// [w0, w0 + wcnt) of the stream), dropping the parts outside it
+__device__ __forceinline__ void put_clip(uint32_t* win, uint64_t w0, uint64_t wcnt, uint64_t p, uint32_t wbits,
+                                         uint32_t val) {
   if (wbits == 0) return;
-  const uint64_t q0 = p >> 6;
-  const uint32_t sh = (uint32_t)p & 63u;
-  if (q0 >= w0 && q0 < w0 + wcnt) atomicOr(&win[q0 - w0], (unsigned long long)(val << sh));
-  if (sh + wbits > 64) {
+  const uint64_t q0 = p >> 5;
+  const uint32_t sh = (uint32_t)p & 31u;
+  if (q0 >= w0 && q0 < w0 + wcnt) atomicOr(&win[q0 - w0], val << sh);
+  if (sh + wbits > 32) {
     const uint64_t q1 = q0 + 1;
-    if (q1 >= w0 && q1 < w0 + wcnt) atomicOr(&win[q1 - w0], (unsigned long long)(val >> (64 - sh)));
+    if (q1 >= w0 && q1 < w0 + wcnt) atomicOr(&win[q1 - w0], val >> (32 - sh));
+  }
+}
+
+// first[w] = the vertex whose bit range holds the first bit of window w
+// (x strictly increasing in the local modes: every neighborhood has a header)
+__global__ void k_window_first(const uint64_t* __restrict__ x, uint64_t n, uint64_t nwin,
+                               uint32_t* __restrict__ first) {
+  constexpr uint64_t WB = (uint64_t)PW * 64;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t a = x[v], b = x[v + 1];  // bits [a, b)
+    for (uint64_t w = (a + WB - 1) / WB; w * WB < b && w < nwin; w++) first[w] = (uint32_t)v;
   }
 }
 
 __global__ void __launch_bounds__(256) k_pack_local(const uint64_t* __restrict__ rp, const uint32_t* __restrict__ col,
                                                     const uint64_t* __restrict__ x, const uint8_t* __restrict__ wid,
-                                                    uint64_t n, int gap, uint32_t s, uint32_t H,
-                                                    uint64_t* __restrict__ out, uint64_t data_words) {
-  __shared__ unsigned long long win[PW];
-  __shared__ uint64_t vrange[2];
+                                                    const uint32_t* __restrict__ first, uint64_t n, int gap,
+                                                    uint32_t s, uint32_t H, uint64_t* __restrict__ out,
+                                                    uint64_t data_words) {
+  __shared__ uint32_t win[2 * PW];
   const uint64_t w0 = (uint64_t)blockIdx.x * PW;
   const uint64_t wcnt = min((uint64_t)PW, data_words - w0);
   const uint64_t b0 = w0 * 64, b1 = (w0 + wcnt) * 64;
-  for (int i = threadIdx.x; i < PW; i += blockDim.x) win[i] = 0;
-  if (threadIdx.x == 0) {
-    // last v with x[v] <= b0, and first v with x[v] >= b1 (x strictly increasing)
-    uint64_t lo = 0, hi = n;
-    while (lo < hi) { uint64_t m = (lo + hi + 1) >> 1; if (x[m] <= b0) lo = m; else hi = m - 1; }
-    vrange[0] = lo;
-    uint64_t a = lo, b = n;
-    while (a < b) { uint64_t m = (a + b) >> 1; if (x[m] < b1) a = m + 1; else b = m; }
-    vrange[1] = a;
-  }
+  const uint64_t v0w = 2 * w0, v0c = 2 * wcnt;  // the window in 32-bit words
+  for (int i = threadIdx.x; i < 2 * PW; i += blockDim.x) win[i] = 0;
   __syncthreads();
-  const uint64_t vb = vrange[0], ve = vrange[1];
+  // vertices overlapping [b0, b1): from the owner of b0 up to (and including)
+  // the owner of the next window's first bit
+  const uint64_t vb = first[blockIdx.x];
+  const uint64_t ve = (blockIdx.x + 1 < gridDim.x) ? (uint64_t)first[blockIdx.x + 1] + 1 : n;
   const int lane = threadIdx.x & 31, wid_ = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (uint64_t v = vb + wid_; v < ve && v < n; v += nw) {
     const uint64_t lo = rp[v], d = rp[v + 1] - lo;
     const uint32_t wv = wid[v];
     const uint64_t base = x[v];
     if (lane == 0) {
-      put_clip(win, w0, wcnt, base, H, wv);
-      if (gap && d >= 1) put_clip(win, w0, wcnt, base + H, s, col[lo]);
+      put_clip(win, v0w, v0c, base, H, wv);
+      if (gap && d >= 1) put_clip(win, v0w, v0c, base + H, s, col[lo]);
     }
     // fields k = 0.. of width wv starting at fs: IDs (local) or differences (gap)
     const uint64_t fs = base + H + (gap ? s : 0);
@@ -330,20 +358,29 @@ __global__ void __launch_bounds__(256) k_pack_local(const uint64_t* __restrict__
     const uint64_t klo = b0 > fs ? (b0 - fs) / wv : 0;
     const uint64_t khi = min(nf, b1 > fs ? (b1 - fs + wv - 1) / wv : 0);
     for (uint64_t k = klo + lane; k < khi; k += 32) {
-      const uint64_t val = gap ? (uint64_t)(col[lo + k + 1] - col[lo + k]) : (uint64_t)col[lo + k];
-      put_clip(win, w0, wcnt, fs + k * wv, wv, val);
+      const uint32_t val = gap ? col[lo + k + 1] - col[lo + k] : col[lo + k];
+      put_clip(win, v0w, v0c, fs + k * wv, wv, val);
     }
   }
   __syncthreads();
-  for (uint64_t i = threadIdx.x; i < wcnt; i += blockDim.x) out[w0 + i] = win[i];
+  for (uint64_t i = threadIdx.x; i < wcnt; i += blockDim.x)
+    out[w0 + i] = (uint64_t)win[2 * i] | ((uint64_t)win[2 * i + 1] << 32);
 }
 
 cudaError_t enc_pack_local(const uint64_t* rp, const uint32_t* col, const uint64_t* x, const uint8_t* wid, uint64_t n,
                            int gap, uint32_t s, uint32_t H, uint64_t* out, uint64_t data_words, cudaStream_t st) {
   if (data_words == 0) return cudaSuccess;
-  k_pack_local<<<grid_for(data_words, PW), 256, 0, st>>>(rp, col, x, wid, n, gap, s, H, out, data_words);
+  const uint64_t nwin = (data_words + PW - 1) / PW;
+  uint32_t* first = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&first, nwin * sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
+  k_window_first<<<grid_for(n, 256, 152 * 32), 256, 0, st>>>(x, n, nwin, first);
   count_launch();
-  return cudaGetLastError();
+  k_pack_local<<<(unsigned)nwin, 256, 0, st>>>(rp, col, x, wid, first, n, gap, s, H, out, data_words);
+  count_launch();
+  e = cudaGetLastError();
+  cudaFreeAsync(first, st);
+  return e;
 }
 
 // =========================================================================

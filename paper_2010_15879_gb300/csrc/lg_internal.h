@@ -23,6 +23,10 @@ struct lg_graph {
   uint64_t *ef_samples; uint64_t words_ef_samples;
   uint32_t *perm, *inv_perm;
   uint32_t *W;          // CSR32 weights (nullptr otherwise)
+  // heavy-vertex schedule, derived from the encoded arrays at encode time
+  lg::HeavyItem *items; uint64_t n_items;
+  uint32_t *multi;      uint64_t n_multi;
+  uint32_t heavy_min, heavy_seg;
 };
 
 namespace lg {
@@ -92,6 +96,16 @@ cudaError_t enc_ef_samples(const uint64_t* x, uint64_t N, uint32_t l, uint32_t s
                            uint64_t ns, cudaStream_t st);
 
 // ------------------------------------------------------------------ traversal
+struct PlanArgs {
+  uint32_t* tile_count;      // items per tile (count pass) / multi vertices per tile
+  const uint64_t* tile_off;  // exclusive prefix of tile_count (fill pass)
+  const uint64_t* multi_off; // exclusive prefix of multi vertices per tile
+  uint32_t* multi_count;
+  HeavyItem* items;
+  uint32_t* multi;
+  uint32_t* segsum;          // per item: sum of its (gap) values
+};
+
 struct PrArgs {
   const float* contrib_in;   // r_{t-1}[u] / d_u, stored labels
   float* contrib_out;        // r_t[v] / d_v
@@ -101,7 +115,7 @@ struct PrArgs {
   float damp;
   int64_t personal;          // stored label of the personalization source, -1 = global
   float r0_all;              // 1/n (initial rank, global)
-  uint32_t heavy_min;        // degree above which a vertex is decoded by a whole warp
+  float* part;               // per heavy item partial sums (split vertices)
 };
 
 struct BfsArgs {
@@ -116,7 +130,7 @@ struct BfsArgs {
   uint32_t queue_in_len;
   uint32_t* queue_out;       // vertices of the next frontier
   uint32_t* counters;        // [0] next queue length, [1] new (vertex, source) pairs
-  uint32_t heavy_min;
+  void* hacc;                // per split vertex: OR of its items' frontier masks
   int* err;
 };
 
@@ -136,7 +150,16 @@ struct TravOps {
   cudaError_t (*bfs_push)(const GView&, const BfsArgs&, int mask_bytes, cudaStream_t);
   cudaError_t (*nbr_degrees)(const GView&, const NbrArgs&, cudaStream_t);
   cudaError_t (*nbr_decode)(const GView&, const NbrArgs&, cudaStream_t);
+  cudaError_t (*plan_count)(const GView&, const PlanArgs&, cudaStream_t);
+  cudaError_t (*plan_fill)(const GView&, const PlanArgs&, cudaStream_t);
+  cudaError_t (*plan_carry)(const GView&, const PlanArgs&, cudaStream_t);
 };
+
+// finishing kernels for vertices split into several heavy items (lg_api.cu)
+cudaError_t pr_finish_multi(const GView& g, const PrArgs& a, cudaStream_t st);
+cudaError_t bfs_finish_multi(const GView& g, const BfsArgs& a, int mask_bytes, cudaStream_t st);
+cudaError_t plan_carry_scan(HeavyItem* items, const uint32_t* multi, uint64_t n_multi, const uint32_t* segsum,
+                            cudaStream_t st);
 
 const TravOps* trav_ops(int id_mode, int off_mode);
 const TravOps* trav_ops_global_packed();

@@ -135,69 +135,78 @@ cudaError_t radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, u
 constexpr uint32_t SEG_SMALL = 32;    // one warp per row, bitonic network in registers
 constexpr uint32_t SEG_MEDIUM = 8192; // one CTA per row, bitonic in shared memory
 
-// warp bitonic sort of one (key, val) per lane, ascending
-__device__ __forceinline__ void warp_bitonic(uint32_t& key, uint32_t& val) {
+template <bool VALS>
+__device__ __forceinline__ void warp_bitonic_t(uint32_t& key, uint32_t& val) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int k = 2; k <= 32; k <<= 1) {
 #pragma unroll
     for (int j = k >> 1; j > 0; j >>= 1) {
       const uint32_t ok = __shfl_xor_sync(LG_FULL_MASK, key, j);
-      const uint32_t ov = __shfl_xor_sync(LG_FULL_MASK, val, j);
+      uint32_t ov = 0;
+      if (VALS) ov = __shfl_xor_sync(LG_FULL_MASK, val, j);
       const bool up = ((lane & k) == 0);
       const bool lower = ((lane & j) == 0);
-      // lower lane keeps the min when sorting up
       const bool take_other = lower ? (up ? (ok < key) : (ok > key)) : (up ? (ok > key) : (ok < key));
-      if (take_other) { key = ok; val = ov; }
+      if (take_other) { key = ok; if (VALS) val = ov; }
     }
   }
 }
 
+// rows of <= 32 keys: one warp per row, 32 rows per warp batch
+template <bool VALS>
 __global__ void __launch_bounds__(256) k_seg_small(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                                                    const uint64_t* __restrict__ off, uint64_t rows) {
   const int lane = threadIdx.x & 31;
   const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-  for (uint64_t r = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += warps) {
-    const uint64_t lo = off[r], d = off[r + 1] - lo;
-    if (d <= 1 || d > SEG_SMALL) continue;
-    uint32_t key = lane < d ? keys[lo + lane] : 0xffffffffu;
-    uint32_t val = (lane < d && vals) ? vals[lo + lane] : 0u;
-    warp_bitonic(key, val);
-    if (lane < d) {
-      keys[lo + lane] = key;
-      if (vals) vals[lo + lane] = val;
+  for (uint64_t r0 = ((uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; r0 < rows; r0 += warps * 32) {
+    const uint64_t mr = r0 + lane;
+    uint64_t mlo = 0, md = 0;
+    if (mr < rows) { mlo = off[mr]; md = off[mr + 1] - mlo; }
+    uint32_t todo = __ballot_sync(LG_FULL_MASK, md > 1 && md <= SEG_SMALL);
+    while (todo) {
+      const int r = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const uint64_t lo = __shfl_sync(LG_FULL_MASK, mlo, r), d = __shfl_sync(LG_FULL_MASK, md, r);
+      uint32_t key = lane < d ? keys[lo + lane] : 0xffffffffu;
+      uint32_t val = (VALS && lane < d) ? vals[lo + lane] : 0u;
+      warp_bitonic_t<VALS>(key, val);
+      if (lane < d) {
+        keys[lo + lane] = key;
+        if (VALS) vals[lo + lane] = val;
+      }
     }
   }
 }
 
-__global__ void __launch_bounds__(256) k_seg_medium(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
-                                                    const uint64_t* __restrict__ off, const uint32_t* __restrict__ list,
-                                                    uint32_t nlist) {
+// one CTA per row, bitonic network in shared memory over P = 2^k >= d keys
+// (padded with UINT32_MAX); blockDim = min(P/2, 256), each thread owns pairs
+__global__ void __launch_bounds__(256) k_seg_bitonic(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                                     const uint64_t* __restrict__ off, const uint32_t* __restrict__ list,
+                                                     uint32_t nlist, uint32_t P) {
   extern __shared__ uint32_t sm[];
   uint32_t* sk = sm;
-  uint32_t* sv = sm + SEG_MEDIUM;
+  uint32_t* sv = sm + P;
+  const uint32_t half = P >> 1;
   for (uint32_t li = blockIdx.x; li < nlist; li += gridDim.x) {
     const uint64_t r = list[li];
     const uint64_t lo = off[r];
     const uint32_t d = (uint32_t)(off[r + 1] - lo);
-    uint32_t P = 64;
-    while (P < d) P <<= 1;
     for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
       sk[i] = i < d ? keys[lo + i] : 0xffffffffu;
-      sv[i] = (i < d && vals) ? vals[lo + i] : 0u;
+      if (vals) sv[i] = i < d ? vals[lo + i] : 0u;
     }
     __syncthreads();
     for (uint32_t k = 2; k <= P; k <<= 1) {
       for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-        for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
-          const uint32_t ixj = i ^ j;
-          if (ixj > i) {
-            const bool up = (i & k) == 0;
-            const uint32_t a = sk[i], b = sk[ixj];
-            if (up ? (a > b) : (a < b)) {
-              sk[i] = b; sk[ixj] = a;
-              const uint32_t t = sv[i]; sv[i] = sv[ixj]; sv[ixj] = t;
-            }
+        for (uint32_t t = threadIdx.x; t < half; t += blockDim.x) {
+          const uint32_t i = ((t & ~(j - 1)) << 1) | (t & (j - 1));
+          const uint32_t ixj = i + j;
+          const bool up = (i & k) == 0;
+          const uint32_t a = sk[i], b = sk[ixj];
+          if (up ? (a > b) : (a < b)) {
+            sk[i] = b; sk[ixj] = a;
+            if (vals) { const uint32_t tv = sv[i]; sv[i] = sv[ixj]; sv[ixj] = tv; }
           }
         }
         __syncthreads();
@@ -211,13 +220,35 @@ __global__ void __launch_bounds__(256) k_seg_medium(uint32_t* __restrict__ keys,
   }
 }
 
-// rows by size class: medium rows listed, large rows listed separately
-__global__ void k_seg_classify(const uint64_t* __restrict__ off, uint64_t rows, uint32_t* med, uint32_t* nmed,
-                               uint32_t* big, uint32_t* nbig) {
+// size class of a row: 0 = warp path (d <= 32), 1..8 = P = 64..8192, 9 = radix
+__device__ __forceinline__ int seg_class(uint64_t d) {
+  if (d <= SEG_SMALL) return 0;
+  if (d > SEG_MEDIUM) return 9;
+  int c = 1;
+  uint64_t P = 64;
+  while (P < d) { P <<= 1; c++; }
+  return c;
+}
+
+constexpr int SEG_NCLASS = 10;
+
+__global__ void k_seg_count(const uint64_t* __restrict__ off, uint64_t rows, uint32_t* __restrict__ cnt) {
+  __shared__ uint32_t c[SEG_NCLASS];
+  if (threadIdx.x < SEG_NCLASS) c[threadIdx.x] = 0;
+  __syncthreads();
   for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t d = off[r + 1] - off[r];
-    if (d > SEG_SMALL && d <= SEG_MEDIUM) med[atomicAdd(nmed, 1u)] = (uint32_t)r;
-    else if (d > SEG_MEDIUM) big[atomicAdd(nbig, 1u)] = (uint32_t)r;
+    const int k = seg_class(off[r + 1] - off[r]);
+    if (k) atomicAdd(&c[k], 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x < SEG_NCLASS && c[threadIdx.x]) atomicAdd(&cnt[threadIdx.x], c[threadIdx.x]);
+}
+
+__global__ void k_seg_fill(const uint64_t* __restrict__ off, uint64_t rows, const uint32_t* __restrict__ base,
+                           uint32_t* __restrict__ cursor, uint32_t* __restrict__ list) {
+  for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += (uint64_t)gridDim.x * blockDim.x) {
+    const int k = seg_class(off[r + 1] - off[r]);
+    if (k) list[base[k] + atomicAdd(&cursor[k], 1u)] = (uint32_t)r;
   }
 }
 
@@ -252,72 +283,85 @@ __global__ void k_seg_big_sizes(const uint64_t* __restrict__ off, const uint32_t
     sizes[b] = off[big[b] + 1] - off[big[b]];
 }
 
+static cudaError_t seg_sort_big(uint32_t* keys, uint32_t* vals, const uint64_t* off, const uint32_t* big,
+                                uint32_t nbig, cudaStream_t st) {
+  uint64_t *sizes = nullptr, *boff = nullptr, *ck = nullptr, *ck2 = nullptr, *stmp = nullptr;
+  uint32_t *cv = nullptr, *cv2 = nullptr;
+  void* rtmp = nullptr;
+  uint64_t nb_total = 0;
+  cudaError_t e = cudaMallocAsync((void**)&sizes, nbig * sizeof(uint64_t), st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&boff, (nbig + 1) * sizeof(uint64_t), st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&stmp, scan_tmp_words(nbig) * sizeof(uint64_t), st);
+  if (e == cudaSuccess) {
+    k_seg_big_sizes<<<grid_for(nbig, 256, 1024), 256, 0, st>>>(off, big, nbig, sizes);
+    count_launch();
+    e = scan_excl_u64(sizes, nbig, boff, stmp, st);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&nb_total, boff + nbig, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&ck, nb_total * sizeof(uint64_t), st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&ck2, nb_total * sizeof(uint64_t), st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&cv, nb_total * sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&cv2, nb_total * sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&rtmp, radix_tmp_bytes(nb_total), st);
+  if (e == cudaSuccess) {
+    k_seg_big_gather<<<grid_for(nbig, 1, 4096), 256, 0, st>>>(keys, vals, off, big, boff, nbig, ck, cv);
+    count_launch();
+    e = radix_sort_u64(ck, cv, ck2, cv2, nb_total, 32 + host_bits(nbig), rtmp, st);
+  }
+  if (e == cudaSuccess) {
+    k_seg_big_scatter<<<grid_for(nbig, 1, 4096), 256, 0, st>>>(keys, vals, off, big, boff, nbig, ck, cv);
+    count_launch();
+    e = cudaGetLastError();
+  }
+  cudaFreeAsync(sizes, st); cudaFreeAsync(boff, st); cudaFreeAsync(stmp, st);
+  cudaFreeAsync(ck, st); cudaFreeAsync(ck2, st); cudaFreeAsync(cv, st); cudaFreeAsync(cv2, st);
+  cudaFreeAsync(rtmp, st);
+  return e;
+}
+
 cudaError_t segmented_sort(uint32_t* keys, uint32_t* vals, const uint64_t* off, uint64_t rows, uint64_t total,
                            uint64_t max_row, cudaStream_t st) {
   if (rows == 0 || total == 0 || max_row <= 1) return cudaSuccess;
   cudaError_t e;
-  k_seg_small<<<grid_for(rows, 8, 152 * 64), 256, 0, st>>>(keys, vals, off, rows);
+  if (vals) k_seg_small<true><<<grid_for(rows, 256, 152 * 16), 256, 0, st>>>(keys, vals, off, rows);
+  else k_seg_small<false><<<grid_for(rows, 256, 152 * 16), 256, 0, st>>>(keys, vals, off, rows);
   count_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (max_row <= SEG_SMALL) return cudaSuccess;
-  uint32_t *list = nullptr, *cnt = nullptr;
-  const uint64_t cap = rows;
-  if ((e = cudaMallocAsync((void**)&list, 2 * cap * sizeof(uint32_t) + 16, st)) != cudaSuccess) return e;
-  if ((e = cudaMallocAsync((void**)&cnt, 2 * sizeof(uint32_t), st)) != cudaSuccess) { cudaFreeAsync(list, st); return e; }
-  uint32_t* big = list + cap;
-  cudaMemsetAsync(cnt, 0, 2 * sizeof(uint32_t), st);
-  k_seg_classify<<<grid_for(rows, 256, 152 * 16), 256, 0, st>>>(off, rows, list, cnt, big, cnt + 1);
+  // rows by power-of-two size class
+  uint32_t* meta = nullptr;  // cnt[10], base[10], cursor[10]
+  if ((e = cudaMallocAsync((void**)&meta, 3 * SEG_NCLASS * sizeof(uint32_t), st)) != cudaSuccess) return e;
+  cudaMemsetAsync(meta, 0, 3 * SEG_NCLASS * sizeof(uint32_t), st);
+  k_seg_count<<<grid_for(rows, 256, 152 * 16), 256, 0, st>>>(off, rows, meta);
   count_launch();
-  uint32_t h[2] = {0, 0};
-  cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, st);
-  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) { cudaFreeAsync(list, st); cudaFreeAsync(cnt, st); return e; }
-  if (h[0]) {
-    const size_t smem = 2 * SEG_MEDIUM * sizeof(uint32_t);
-    cudaFuncSetAttribute(k_seg_medium, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_seg_medium<<<grid_for(h[0], 1, 152 * 8), 256, smem, st>>>(keys, vals, off, list, h[0]);
+  uint32_t cnt[SEG_NCLASS], base[SEG_NCLASS];
+  cudaMemcpyAsync(cnt, meta, sizeof(cnt), cudaMemcpyDeviceToHost, st);
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) { cudaFreeAsync(meta, st); return e; }
+  uint32_t tot = 0;
+  for (int k = 0; k < SEG_NCLASS; k++) { base[k] = tot; tot += cnt[k]; }
+  uint32_t* list = nullptr;
+  if ((e = cudaMallocAsync((void**)&list, (tot ? tot : 1) * sizeof(uint32_t), st)) != cudaSuccess) {
+    cudaFreeAsync(meta, st);
+    return e;
+  }
+  cudaMemcpyAsync(meta + SEG_NCLASS, base, sizeof(base), cudaMemcpyHostToDevice, st);
+  k_seg_fill<<<grid_for(rows, 256, 152 * 16), 256, 0, st>>>(off, rows, meta + SEG_NCLASS, meta + 2 * SEG_NCLASS, list);
+  count_launch();
+  for (int k = 1; k <= 8 && e == cudaSuccess; k++) {
+    if (!cnt[k]) continue;
+    const uint32_t P = 32u << k;
+    const unsigned threads = P / 2 < 256 ? P / 2 : 256;
+    const size_t smem = (size_t)P * sizeof(uint32_t) * (vals ? 2 : 1);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_seg_bitonic, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_seg_bitonic<<<grid_for(cnt[k], 1, 152 * 32), threads, smem, st>>>(keys, vals, off, list + base[k], cnt[k], P);
     count_launch();
-    if ((e = cudaGetLastError()) != cudaSuccess) { cudaFreeAsync(list, st); cudaFreeAsync(cnt, st); return e; }
+    e = cudaGetLastError();
   }
-  if (h[1]) {
-    const uint32_t nbig = h[1];
-    uint64_t *sizes = nullptr, *boff = nullptr, *ck = nullptr, *ck2 = nullptr, *stmp = nullptr;
-    uint32_t *cv = nullptr, *cv2 = nullptr;
-    void* rtmp = nullptr;
-    // total elements of big rows is at most `total`
-    e = cudaMallocAsync((void**)&sizes, nbig * sizeof(uint64_t), st);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&boff, (nbig + 1) * sizeof(uint64_t), st);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&stmp, scan_tmp_words(nbig) * sizeof(uint64_t), st);
-    uint64_t nb_total = 0;
-    if (e == cudaSuccess) {
-      k_seg_big_sizes<<<grid_for(nbig, 256, 1024), 256, 0, st>>>(off, big, nbig, sizes);
-      count_launch();
-      e = scan_excl_u64(sizes, nbig, boff, stmp, st);
-    }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&nb_total, boff + nbig, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&ck, nb_total * sizeof(uint64_t), st);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&ck2, nb_total * sizeof(uint64_t), st);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&cv, nb_total * sizeof(uint32_t), st);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&cv2, nb_total * sizeof(uint32_t), st);
-    if (e == cudaSuccess) e = cudaMallocAsync(&rtmp, radix_tmp_bytes(nb_total), st);
-    if (e == cudaSuccess) {
-      k_seg_big_gather<<<grid_for(nbig, 1, 4096), 256, 0, st>>>(keys, vals, off, big, boff, nbig, ck, cv);
-      count_launch();
-      e = radix_sort_u64(ck, cv, ck2, cv2, nb_total, 32 + host_bits(nbig), rtmp, st);
-    }
-    if (e == cudaSuccess) {
-      k_seg_big_scatter<<<grid_for(nbig, 1, 4096), 256, 0, st>>>(keys, vals, off, big, boff, nbig, ck, cv);
-      count_launch();
-      e = cudaGetLastError();
-    }
-    cudaFreeAsync(sizes, st); cudaFreeAsync(boff, st); cudaFreeAsync(stmp, st);
-    cudaFreeAsync(ck, st); cudaFreeAsync(ck2, st); cudaFreeAsync(cv, st); cudaFreeAsync(cv2, st);
-    cudaFreeAsync(rtmp, st);
-    if (e != cudaSuccess) { cudaFreeAsync(list, st); cudaFreeAsync(cnt, st); return e; }
-  }
+  if (e == cudaSuccess && cnt[9]) e = seg_sort_big(keys, vals, off, list + base[9], cnt[9], st);
   cudaFreeAsync(list, st);
-  cudaFreeAsync(cnt, st);
-  return cudaGetLastError();
+  cudaFreeAsync(meta, st);
+  return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
 // =========================================================================
@@ -340,18 +384,31 @@ __global__ void k_dm_perm(const uint32_t* __restrict__ inv, uint64_t n, uint32_t
     newdeg[i] = (uint32_t)(rp[v + 1] - rp[v]);
   }
 }
+// One warp takes 32 consecutive new rows: lane l loads row l's source and
+// destination bounds, then the warp copies the rows, mapping IDs through perm.
 __global__ void __launch_bounds__(256) k_dm_scatter(const uint64_t* __restrict__ rp, const uint32_t* __restrict__ col,
                                                     const uint32_t* __restrict__ w, const uint32_t* __restrict__ inv,
                                                     const uint32_t* __restrict__ perm, const uint64_t* __restrict__ nrp,
                                                     uint32_t* __restrict__ ncol, uint32_t* __restrict__ nw, uint64_t n) {
   const int lane = threadIdx.x & 31;
   const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-  for (uint64_t i = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
-    const uint32_t v = inv[i];
-    const uint64_t lo = rp[v], d = rp[v + 1] - lo, o = nrp[i];
-    for (uint64_t k = lane; k < d; k += 32) {
-      ncol[o + k] = perm[col[lo + k]];
-      if (w) nw[o + k] = w[lo + k];
+  for (uint64_t i0 = ((uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; i0 < n; i0 += warps * 32) {
+    const uint64_t mi = i0 + lane;
+    uint64_t mlo = 0, md = 0, mo = 0;
+    if (mi < n) {
+      const uint32_t v = inv[mi];
+      mlo = rp[v];
+      md = rp[v + 1] - mlo;
+      mo = nrp[mi];
+    }
+    const int rows = (int)min((uint64_t)32, n - i0);
+    for (int r = 0; r < rows; r++) {
+      const uint64_t lo = __shfl_sync(LG_FULL_MASK, mlo, r), d = __shfl_sync(LG_FULL_MASK, md, r);
+      const uint64_t o = __shfl_sync(LG_FULL_MASK, mo, r);
+      for (uint64_t k = lane; k < d; k += 32) {
+        ncol[o + k] = perm[col[lo + k]];
+        if (w) nw[o + k] = w[lo + k];
+      }
     }
   }
 }
@@ -380,7 +437,7 @@ cudaError_t enc_dm_relabel(const uint64_t* rp, const uint32_t* col, const uint32
     e = scan_excl_u32(newdeg, n, nrp, stmp, st);
   }
   if (e == cudaSuccess) {
-    k_dm_scatter<<<grid_for(n, 8, 152 * 64), 256, 0, st>>>(rp, col, w, inv_perm, perm, nrp, ncol, nw, n);
+    k_dm_scatter<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(rp, col, w, inv_perm, perm, nrp, ncol, nw, n);
     count_launch();
     e = cudaGetLastError();
   }

@@ -1,19 +1,24 @@
 // Graph kernels with the Log(Graph) decoder fused in (Sections 3.7.2-3.7.3 for
 // the access path, Section 7.1.2 for BFS and PageRank).
 //
-// Pull sweeps (PageRank, bottom-up BFS) walk the vertices in tiles of TV = 512
-// consecutive stored labels, one CTA per tile:
-//   1. offsets x_v of the tile (packed fields, CSR row_ptr, or an Elias-Fano
-//      block decode: the tile starts on a select sample, the CTA popcounts the
-//      high-bit words it spans and every thread selects one vertex's one);
-//   2. per vertex: degree and field width from the offsets and the
-//      neighborhood header;
-//   3. vertices of degree <= heavy_min are split over the threads in contiguous
-//      runs of nearly equal field counts, each thread decoding its own run with
-//      a sequential bit reader (one 128-bit load per ~128 bits, a funnel shift
-//      and a mask per field, a running sum for gap-coded IDs);
-//   4. vertices of higher degree are decoded by a whole warp, lane i taking
-//      field i of each 32-field chunk (gap-coded IDs by a warp prefix sum).
+// Pull sweeps (PageRank, bottom-up BFS) are one launch with two kinds of CTA:
+//   * heavy CTAs walk the heavy-vertex schedule built at encode time: vertices
+//     of degree > heavy_min split into items of <= heavy_seg fields, one warp per
+//     item, lane i decoding field i of each 32-field chunk with 4 chunks in
+//     flight (gap-coded IDs by a warp prefix sum from the item's carry);
+//   * tile CTAs take 512 consecutive stored labels each:
+//     1. offsets x_v of the tile (packed fields, CSR row_ptr, or an
+//        Elias-Fano block decode: the tile starts on a select sample, the CTA
+//        popcounts the high-bit words it spans and every thread selects one
+//        vertex's one);
+//     2. per vertex: degree and field width from the offsets and the
+//        neighborhood header;
+//     3. light vertices (degree <= heavy_min) are split over the threads in
+//        contiguous runs of nearly equal field counts, each thread decoding
+//        its run with a sequential bit reader (one 32-byte sector per 256 bits,
+//        a shift and a mask per field, a running sum for gap-coded IDs, four
+//        gathers in flight).
+// Vertices split into several items are finished by a small second kernel.
 // Push steps and neighbor queries decode one random vertex per warp.
 #pragma once
 
@@ -21,9 +26,8 @@
 
 namespace lg {
 
-constexpr int TV = 512;   // vertices per tile
-constexpr int TNT = 256;  // threads per tile CTA
-
+constexpr int TV = LG_TILE_V;  // vertices per tile
+constexpr int TNT = 256;       // threads per tile CTA
 // ---------------------------------------------------------------------------
 // small helpers
 // ---------------------------------------------------------------------------
@@ -215,8 +219,8 @@ struct SeqDec {
   BitReader br;
   uint32_t w, s, omega, id;
   bool first;
-  __device__ __forceinline__ void init(const GView& g, uint64_t start, uint32_t width) {
-    br.init(g.A32, start);
+  __device__ __forceinline__ void init(const GView& g, uint64_t start, uint32_t width, uint64_t pol) {
+    br.init(g.A32, start, pol);
     w = width; s = g.s; omega = g.omega; id = 0; first = true;
   }
   __device__ __forceinline__ uint32_t next() {
@@ -248,6 +252,30 @@ __device__ __forceinline__ uint32_t weight_at(const GView& g, uint64_t start, ui
   return ext32(g.A32, start + i * g.r + g.s, g.omega);
 }
 
+// Lane-parallel decode of U chunks of 32 fields starting at field `base`
+// (fields >= f1 read as 0).  Gap-coded IDs are prefix-summed across the warp
+// with `carry` = the absolute ID before field `base`; carry is advanced.  All
+// field loads of the U chunks are independent, so they are in flight together.
+template <int IDM, int U>
+__device__ __forceinline__ void warp_ids(const GView& g, uint64_t start, uint32_t w, uint32_t base, uint32_t f1,
+                                         uint32_t& carry, uint32_t (&val)[U]) {
+  const uint32_t lane = threadIdx.x & 31u;
+#pragma unroll
+  for (int u = 0; u < U; u++) {
+    const uint32_t idx = base + 32u * u + lane;
+    val[u] = idx < f1 ? field_at<IDM>(g, start, w, idx) : 0u;
+  }
+  if (IDM == ID_LOCAL_GAP) {
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      val[u] = warp_incl_scan<uint32_t>(val[u]) + carry;
+      carry = __shfl_sync(LG_FULL_MASK, val[u], 31);
+    }
+  }
+}
+
+constexpr int HEAVY_U = 4;  // chunks of 32 fields in flight per warp
+
 // ---------------------------------------------------------------------------
 // tile phases shared by the pull kernels
 // ---------------------------------------------------------------------------
@@ -257,20 +285,17 @@ struct TileSmem {
   uint32_t deg[TV];
   uint32_t fpre[TV + 1];   // field prefix over the compacted light list
   uint16_t clist[TV];      // compacted light vertices (local index)
-  uint16_t hlist[TV];      // heavy vertices
   uint8_t wid[TV];
-  uint32_t nlight, nheavy, nfields;
+  uint32_t nlight, nfields;
   uint64_t red64[TNT / 32];
   TileScratch ts;
 };
 
-// Phase 2: geometry of each vertex; `keep(i, d)` says whether vertex i has work
-// (else the caller handles it as trivial); light/heavy split and the compacted,
-// prefix-summed light list.
+// Phase 2: geometry of each vertex; light vertices (0 < degree <= heavy_min)
+// that `keep(i)` accepts form the compacted, field-prefix-summed list.
+// Heavier vertices are left to the heavy schedule.
 template <int IDM, typename Keep>
-__device__ __forceinline__ void tile_classify(const GView& g, TileSmem& sm, int cnt, uint32_t heavy_min, Keep keep) {
-  if (threadIdx.x == 0) sm.nheavy = 0;
-  __syncthreads();
+__device__ __forceinline__ void tile_classify(const GView& g, TileSmem& sm, int cnt, Keep keep) {
   uint32_t lc = 0, lf = 0;
   bool light[TV / TNT];
 #pragma unroll
@@ -281,10 +306,7 @@ __device__ __forceinline__ void tile_classify(const GView& g, TileSmem& sm, int 
       uint64_t start; uint32_t d, w;
       vgeo<IDM>(g, sm.xs[i], sm.xs[i + 1], start, d, w);
       sm.st[i] = start; sm.deg[i] = d; sm.wid[i] = (uint8_t)w;
-      if (d > 0 && keep(i, d)) {
-        if (d <= heavy_min) { light[q] = true; lc++; lf += d; }
-        else sm.hlist[atomicAdd(&sm.nheavy, 1u)] = (uint16_t)i;
-      }
+      if (d > 0 && d <= g.heavy_min && keep(i)) { light[q] = true; lc++; lf += d; }
     }
   }
   uint64_t total;
@@ -322,6 +344,11 @@ __device__ __forceinline__ void light_range(const TileSmem& sm, uint32_t& jb, ui
   je = a;
 }
 
+// number of CTAs that work on the heavy schedule (one item per warp)
+__host__ __device__ inline unsigned heavy_blocks(uint64_t n_items) {
+  return (unsigned)((n_items + (TNT / 32) - 1) / (TNT / 32));
+}
+
 // ===========================================================================
 // PageRank
 // ===========================================================================
@@ -341,111 +368,157 @@ __global__ void __launch_bounds__(TNT) k_pr_init(GView g, PrArgs a) {
   }
 }
 
+__device__ __forceinline__ void pr_finish(const GView& g, const PrArgs& a, uint64_t v, uint32_t d, float sum) {
+  const float base = a.personal < 0 ? a.base_all : ((int64_t)v == a.personal ? a.base_all : 0.0f);
+  const float r = base + a.damp * sum;
+  a.contrib_out[v] = d ? r / (float)d : 0.0f;
+  if (a.last) a.ranks_out[g.inv_perm ? (uint64_t)g.inv_perm[v] : v] = r;
+}
+
+// One launch = one iteration.  Blocks [0, HB) take the heavy schedule (a warp
+// per item); the other blocks take one tile of 512 vertices each.
 template <int IDM, int OFF>
-__global__ void __launch_bounds__(TNT) k_pr_pull(GView g, PrArgs a) {
+__global__ void __launch_bounds__(TNT, 6) k_pr_pull(GView g, PrArgs a) {
   __shared__ TileSmem sm;
-  const uint64_t v0 = (uint64_t)blockIdx.x * TV;
-  const int cnt = (int)min((uint64_t)TV, g.n - v0);
-  tile_offsets<OFF>(g, v0, cnt, sm.xs, sm.ts);
-  __syncthreads();
-  tile_classify<IDM>(g, sm, cnt, a.heavy_min, [](int, uint32_t) { return true; });
   const float* __restrict__ c = a.contrib_in;
-
-  auto finish = [&](uint64_t v, uint32_t d, float sum) {
-    const float base = a.personal < 0 ? a.base_all : ((int64_t)v == a.personal ? a.base_all : 0.0f);
-    const float r = base + a.damp * sum;
-    a.contrib_out[v] = d ? r / (float)d : 0.0f;
-    if (a.last) a.ranks_out[g.inv_perm ? (uint64_t)g.inv_perm[v] : v] = r;
-  };
-
-  // zero-degree vertices keep the teleport term only
-  for (int i = threadIdx.x; i < cnt; i += TNT)
-    if (sm.deg[i] == 0) finish(v0 + i, 0, 0.0f);
-
-  // light vertices: sequential decode of contiguous runs
-  uint32_t jb, je;
-  light_range(sm, jb, je);
-  for (uint32_t j = jb; j < je; j++) {
-    const int i = sm.clist[j];
-    const uint32_t d = sm.deg[i];
-    SeqDec<IDM> dec;
-    dec.init(g, sm.st[i], sm.wid[i]);
-    float s0 = 0.f, s1 = 0.f;
-    uint32_t k = 0;
-    for (; k + 4 <= d; k += 4) {
-      const uint32_t u0 = dec.next(), u1 = dec.next(), u2 = dec.next(), u3 = dec.next();
-      const float f0 = __ldg(c + u0), f1 = __ldg(c + u1), f2 = __ldg(c + u2), f3 = __ldg(c + u3);
-      s0 += f0 + f1;
-      s1 += f2 + f3;
-    }
-    for (; k < d; k++) s0 += __ldg(c + dec.next());
-    finish(v0 + i, d, s0 + s1);
-  }
-
-  // heavy vertices: one warp each, compensated (Kahan) lane sums
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  for (uint32_t h = wp; h < sm.nheavy; h += TNT / 32) {
-    const int i = sm.hlist[h];
-    const uint32_t d = sm.deg[i], w = sm.wid[i];
-    const uint64_t start = sm.st[i];
+  const unsigned hb = heavy_blocks(g.n_items);
+  const int lane = threadIdx.x & 31;
+  const uint64_t pstream = policy_stream(), pkeep = policy_keep();
+  if (blockIdx.x < hb) {
+    const uint64_t it = (uint64_t)blockIdx.x * (TNT / 32) + (threadIdx.x >> 5);
+    if (it >= g.n_items) return;
+    const HeavyItem h = g.items[it];
+    const uint32_t f1 = h.f0 + h.nf;
+    uint32_t carry = h.carry;
     float acc = 0.f, comp = 0.f;
-    uint32_t carry = 0;
-    for (uint32_t base = 0; base < d; base += 32) {
-      const uint32_t idx = base + lane;
-      const bool ok = idx < d;
-      uint32_t val = ok ? field_at<IDM>(g, start, w, idx) : 0u;
-      if (IDM == ID_LOCAL_GAP) {
-        val = warp_incl_scan<uint32_t>(val) + carry;
-        carry = __shfl_sync(LG_FULL_MASK, val, 31);
-      }
-      if (ok) {
-        const float y = __ldg(c + val) - comp;
+    for (uint32_t base = h.f0; base < f1; base += 32 * HEAVY_U) {
+      uint32_t id[HEAVY_U];
+      warp_ids<IDM, HEAVY_U>(g, h.bit, h.w, base, f1, carry, id);
+      float x[HEAVY_U];
+#pragma unroll
+      for (int u = 0; u < HEAVY_U; u++) x[u] = (base + 32u * u + lane < f1) ? ldg_gather(c + id[u], pkeep) : 0.f;
+#pragma unroll
+      for (int u = 0; u < HEAVY_U; u++) {  // compensated (Kahan) lane sums
+        const float y = x[u] - comp;
         const float t = acc + y;
         comp = (t - acc) - y;
         acc = t;
       }
     }
     acc = warp_sum<float>(acc);
-    if (lane == 0) finish(v0 + i, d, acc);
+    if (lane == 0) {
+      if (h.nitems == 1) pr_finish(g, a, h.v, h.deg, acc);
+      else a.part[it] = acc;
+    }
+    return;
+  }
+  const uint64_t v0 = (uint64_t)(blockIdx.x - hb) * TV;
+  const int cnt = (int)min((uint64_t)TV, g.n - v0);
+  tile_offsets<OFF>(g, v0, cnt, sm.xs, sm.ts);
+  __syncthreads();
+  tile_classify<IDM>(g, sm, cnt, [](int) { return true; });
+
+  // zero-degree vertices keep the teleport term only
+  for (int i = threadIdx.x; i < cnt; i += TNT)
+    if (sm.deg[i] == 0) pr_finish(g, a, v0 + i, 0, 0.0f);
+
+  // light vertices: sequential decode of contiguous runs, 4 gathers in flight
+  uint32_t jb, je;
+  light_range(sm, jb, je);
+  for (uint32_t j = jb; j < je; j++) {
+    const int i = sm.clist[j];
+    const uint32_t d = sm.deg[i];
+    SeqDec<IDM> dec;
+    dec.init(g, sm.st[i], sm.wid[i], pstream);
+    float s0 = 0.f, s1 = 0.f;
+    uint32_t k = 0;
+    for (; k + 4 <= d; k += 4) {  // four gathers in flight
+      const uint32_t u0 = dec.next(), u1 = dec.next(), u2 = dec.next(), u3 = dec.next();
+      const float f0 = ldg_gather(c + u0, pkeep), f1 = ldg_gather(c + u1, pkeep);
+      const float f2 = ldg_gather(c + u2, pkeep), f3 = ldg_gather(c + u3, pkeep);
+      s0 += f0 + f1;
+      s1 += f2 + f3;
+    }
+    for (; k < d; k++) s0 += ldg_gather(c + dec.next(), pkeep);
+    pr_finish(g, a, v0 + i, d, s0 + s1);
   }
 }
 
 // ===========================================================================
 // BFS (multi-source, bit-parallel): bit s of a mask is source s
 // ===========================================================================
+template <typename M>
+__device__ __forceinline__ void bfs_finish(const GView& g, const BfsArgs& a, uint64_t v, M need, M found,
+                                           uint32_t* qbuf, uint32_t* qn, uint32_t* pairs) {
+  M* vis = reinterpret_cast<M*>(a.vis);
+  M* fout = reinterpret_cast<M*>(a.front_out);
+  const M nb = (M)(found & need);
+  fout[v] = nb;
+  if (nb) {
+    vis[v] = (M)(vis[v] | nb);
+    write_depths<M>(a.depth, g.n, v, nb, a.level + 1);
+    if (qbuf) {
+      qbuf[atomicAdd(qn, 1u)] = (uint32_t)v;
+      atomicAdd(pairs, (uint32_t)__popcll((unsigned long long)nb));
+    } else {
+      a.queue_out[atomicAdd(&a.counters[0], 1u)] = (uint32_t)v;
+      atomicAdd(&a.counters[1], (uint32_t)__popcll((unsigned long long)nb));
+    }
+  }
+}
+
 template <int IDM, int OFF, typename M>
-__global__ void __launch_bounds__(TNT) k_bfs_pull(GView g, BfsArgs a) {
+__global__ void __launch_bounds__(TNT, 6) k_bfs_pull(GView g, BfsArgs a) {
   __shared__ TileSmem sm;
   __shared__ M need_sm[TV];
   __shared__ uint32_t qbuf[TV];
   __shared__ uint32_t qn, newpairs, qbase;
-  const uint64_t v0 = (uint64_t)blockIdx.x * TV;
-  const int cnt = (int)min((uint64_t)TV, g.n - v0);
-  M* vis = reinterpret_cast<M*>(a.vis);
+  const M* vis = reinterpret_cast<const M*>(a.vis);
   const M* __restrict__ fin = reinterpret_cast<const M*>(a.front_in);
   M* fout = reinterpret_cast<M*>(a.front_out);
   const M all = (M)a.all_mask;
+  const unsigned hb = heavy_blocks(g.n_items);
+  const int lane = threadIdx.x & 31;
+  const uint64_t pstream = policy_stream(), pkeep = policy_keep();
+  if (blockIdx.x < hb) {
+    const uint64_t it = (uint64_t)blockIdx.x * (TNT / 32) + (threadIdx.x >> 5);
+    if (it >= g.n_items) return;
+    const HeavyItem h = g.items[it];
+    const M need = (M)(all & (M)~vis[h.v]);
+    if (need == 0) {
+      if (h.nitems == 1 && lane == 0) fout[h.v] = 0;
+      return;
+    }
+    const uint32_t f1 = h.f0 + h.nf;
+    uint32_t carry = h.carry;
+    M acc = 0;
+    for (uint32_t base = h.f0; base < f1; base += 32 * HEAVY_U) {
+      uint32_t id[HEAVY_U];
+      warp_ids<IDM, HEAVY_U>(g, h.bit, h.w, base, f1, carry, id);
+      M x[HEAVY_U];
+#pragma unroll
+      for (int u = 0; u < HEAVY_U; u++) x[u] = (base + 32u * u + lane < f1) ? ldg_gather(fin + id[u], pkeep) : (M)0;
+#pragma unroll
+      for (int u = 0; u < HEAVY_U; u++) acc |= x[u];
+      acc = warp_or<M>(acc);
+      if ((M)(acc & need) == need) break;
+    }
+    if (lane == 0) {
+      if (h.nitems == 1) bfs_finish<M>(g, a, h.v, need, acc, nullptr, nullptr, nullptr);
+      else atomic_or_mask<M>(reinterpret_cast<M*>(a.hacc) + h.slot, acc);
+    }
+    return;
+  }
   if (threadIdx.x == 0) { qn = 0; newpairs = 0; }
+  const uint64_t v0 = (uint64_t)(blockIdx.x - hb) * TV;
+  const int cnt = (int)min((uint64_t)TV, g.n - v0);
   for (int i = threadIdx.x; i < cnt; i += TNT) need_sm[i] = (M)(all & (M)~vis[v0 + i]);
   tile_offsets<OFF>(g, v0, cnt, sm.xs, sm.ts);
   __syncthreads();
-  tile_classify<IDM>(g, sm, cnt, a.heavy_min, [&](int i, uint32_t) { return need_sm[i] != 0; });
-  const uint32_t nd = a.level + 1;
-
-  auto finish = [&](int i, M found) {
-    const uint64_t v = v0 + i;
-    const M nb = found & need_sm[i];
-    fout[v] = nb;
-    if (nb) {
-      vis[v] = (M)(vis[v] | nb);
-      write_depths<M>(a.depth, g.n, v, nb, nd);
-      qbuf[atomicAdd(&qn, 1u)] = (uint32_t)v;
-      atomicAdd(&newpairs, (uint32_t)__popcll((unsigned long long)nb));
-    }
-  };
+  tile_classify<IDM>(g, sm, cnt, [&](int i) { return need_sm[i] != 0; });
 
   for (int i = threadIdx.x; i < cnt; i += TNT)
-    if (sm.deg[i] == 0 || need_sm[i] == 0) fout[v0 + i] = 0;
+    if (sm.deg[i] == 0 || (sm.deg[i] <= g.heavy_min && need_sm[i] == 0)) fout[v0 + i] = 0;
 
   uint32_t jb, je;
   light_range(sm, jb, je);
@@ -454,40 +527,18 @@ __global__ void __launch_bounds__(TNT) k_bfs_pull(GView g, BfsArgs a) {
     const uint32_t d = sm.deg[i];
     const M need = need_sm[i];
     SeqDec<IDM> dec;
-    dec.init(g, sm.st[i], sm.wid[i]);
+    dec.init(g, sm.st[i], sm.wid[i], pstream);
     M acc = 0;
     uint32_t k = 0;
-    for (; k + 4 <= d; k += 4) {
+    for (; k + 4 <= d; k += 4) {  // early exit once every unvisited source is found
       const uint32_t u0 = dec.next(), u1 = dec.next(), u2 = dec.next(), u3 = dec.next();
-      acc |= (M)(fin[u0] | fin[u1] | fin[u2] | fin[u3]);
+      acc |= (M)(ldg_gather(fin + u0, pkeep) | ldg_gather(fin + u1, pkeep) | ldg_gather(fin + u2, pkeep) |
+                 ldg_gather(fin + u3, pkeep));
       if ((M)(acc & need) == need) break;
     }
     if ((M)(acc & need) != need)
-      for (; k < d; k++) acc |= fin[dec.next()];
-    finish(i, acc);
-  }
-
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  for (uint32_t h = wp; h < sm.nheavy; h += TNT / 32) {
-    const int i = sm.hlist[h];
-    const uint32_t d = sm.deg[i], w = sm.wid[i];
-    const uint64_t start = sm.st[i];
-    const M need = need_sm[i];
-    M acc = 0;
-    uint32_t carry = 0;
-    for (uint32_t base = 0; base < d; base += 32) {
-      const uint32_t idx = base + lane;
-      const bool ok = idx < d;
-      uint32_t val = ok ? field_at<IDM>(g, start, w, idx) : 0u;
-      if (IDM == ID_LOCAL_GAP) {
-        val = warp_incl_scan<uint32_t>(val) + carry;
-        carry = __shfl_sync(LG_FULL_MASK, val, 31);
-      }
-      if (ok) acc |= fin[val];
-      acc = warp_or<M>(acc);
-      if ((M)(acc & need) == need) break;
-    }
-    if (lane == 0) finish(i, acc);
+      for (; k < d; k++) acc |= ldg_gather(fin + dec.next(), pkeep);
+    bfs_finish<M>(g, a, v0 + i, need, acc, qbuf, &qn, &newpairs);
   }
 
   __syncthreads();
@@ -517,34 +568,34 @@ __global__ void __launch_bounds__(256) k_bfs_push(GView g, BfsArgs a) {
     offset_pair<OFF>(g, v, x0, x1);
     vgeo<IDM>(g, x0, x1, start, d, w);
     uint32_t carry = 0;
-    for (uint32_t base = 0; base < d; base += 32) {
-      const uint32_t idx = base + lane;
-      const bool ok = idx < d;
-      uint32_t u = ok ? field_at<IDM>(g, start, w, idx) : 0u;
-      if (IDM == ID_LOCAL_GAP) {
-        u = warp_incl_scan<uint32_t>(u) + carry;
-        carry = __shfl_sync(LG_FULL_MASK, u, 31);
-      }
-      bool app = false;
-      if (ok) {
-        M nb = (M)(m & (M)~vis[u]);
+    for (uint32_t base = 0; base < d; base += 32 * HEAVY_U) {
+      uint32_t id[HEAVY_U];
+      warp_ids<IDM, HEAVY_U>(g, start, w, base, d, carry, id);
+      M cur[HEAVY_U];
+#pragma unroll
+      for (int u = 0; u < HEAVY_U; u++) cur[u] = (base + 32u * u + lane < d) ? vis[id[u]] : (M)~(M)0;
+#pragma unroll
+      for (int u = 0; u < HEAVY_U; u++) {
+        const uint32_t u_id = id[u];
+        bool app = false;
+        M nb = (M)(m & (M)~cur[u]);
         if (nb) {
-          const M old = atomic_or_mask<M>(vis + u, nb);
+          const M old = atomic_or_mask<M>(vis + u_id, nb);
           nb = (M)(nb & (M)~old);
           if (nb) {
-            const M oldf = atomic_or_mask<M>(fout + u, nb);
+            const M oldf = atomic_or_mask<M>(fout + u_id, nb);
             app = (oldf == 0);
-            write_depths<M>(a.depth, g.n, u, nb, nd);
+            write_depths<M>(a.depth, g.n, u_id, nb, nd);
             pairs += __popcll((unsigned long long)nb);
           }
         }
-      }
-      const uint32_t b = __ballot_sync(LG_FULL_MASK, app);
-      if (b) {
-        uint32_t basepos = 0;
-        if (lane == 0) basepos = atomicAdd(&a.counters[0], (uint32_t)__popc(b));
-        basepos = __shfl_sync(LG_FULL_MASK, basepos, 0);
-        if (app) a.queue_out[basepos + __popc(b & lane_lt_mask())] = u;
+        const uint32_t b = __ballot_sync(LG_FULL_MASK, app);
+        if (b) {
+          uint32_t basepos = 0;
+          if (lane == 0) basepos = atomicAdd(&a.counters[0], (uint32_t)__popc(b));
+          basepos = __shfl_sync(LG_FULL_MASK, basepos, 0);
+          if (app) a.queue_out[basepos + __popc(b & lane_lt_mask())] = u_id;
+        }
       }
     }
   }
@@ -588,24 +639,115 @@ __global__ void __launch_bounds__(256) k_nbr_decode(GView g, NbrArgs a) {
     vgeo<IDM>(g, x0, x1, start, d, w);
     const uint64_t o = a.out_offsets[q];
     uint32_t carry = 0;
-    for (uint32_t base = 0; base < d; base += 32) {
-      const uint32_t idx = base + lane;
-      const bool ok = idx < d;
-      uint32_t u = ok ? field_at<IDM>(g, start, w, idx) : 0u;
-      if (IDM == ID_LOCAL_GAP) {
-        u = warp_incl_scan<uint32_t>(u) + carry;
-        carry = __shfl_sync(LG_FULL_MASK, u, 31);
-      }
-      if (ok) {
-        a.out_ids[o + idx] = g.inv_perm ? g.inv_perm[u] : u;
-        if (a.out_weights) {
-          uint32_t wt = 0;
-          if (IDM == ID_GLOBAL && g.omega) wt = weight_at(g, start, idx);
-          if (IDM == ID_CSR32 && g.W32) wt = __ldg(g.W32 + (start >> 5) + idx);
-          a.out_weights[o + idx] = wt;
+    for (uint32_t base = 0; base < d; base += 64) {
+      uint32_t id[2];
+      warp_ids<IDM, 2>(g, start, w, base, d, carry, id);
+#pragma unroll
+      for (int u = 0; u < 2; u++) {
+        const uint32_t idx = base + 32u * u + lane;
+        if (idx < d) {
+          a.out_ids[o + idx] = g.inv_perm ? g.inv_perm[id[u]] : id[u];
+          if (a.out_weights) {
+            uint32_t wt = 0;
+            if (IDM == ID_GLOBAL && g.omega) wt = weight_at(g, start, idx);
+            if (IDM == ID_CSR32 && g.W32) wt = __ldg(g.W32 + (start >> 5) + idx);
+            a.out_weights[o + idx] = wt;
+          }
         }
       }
     }
+  }
+}
+
+// ===========================================================================
+// heavy-vertex schedule, built once per graph from the encoded arrays
+// ===========================================================================
+__device__ __forceinline__ uint32_t items_of(const GView& g, uint32_t d) {
+  return d > g.heavy_min ? (d + g.heavy_seg - 1) / g.heavy_seg : 0u;
+}
+
+template <int IDM, int OFF>
+__global__ void __launch_bounds__(TNT) k_plan_count(GView g, PlanArgs p) {
+  __shared__ TileSmem sm;
+  const uint64_t v0 = (uint64_t)blockIdx.x * TV;
+  const int cnt = (int)min((uint64_t)TV, g.n - v0);
+  tile_offsets<OFF>(g, v0, cnt, sm.xs, sm.ts);
+  __syncthreads();
+  uint64_t mine = 0;
+  for (int i = threadIdx.x; i < cnt; i += TNT) {
+    uint64_t start; uint32_t d, w;
+    vgeo<IDM>(g, sm.xs[i], sm.xs[i + 1], start, d, w);
+    const uint32_t k = items_of(g, d);
+    mine += ((uint64_t)k << 32) | (k > 1 ? 1u : 0u);
+  }
+  uint64_t total;
+  block_excl_scan<uint64_t, TNT>(mine, total, sm.red64);
+  if (threadIdx.x == 0) {
+    p.tile_count[blockIdx.x] = (uint32_t)(total >> 32);
+    p.multi_count[blockIdx.x] = (uint32_t)total;
+  }
+}
+
+template <int IDM, int OFF>
+__global__ void __launch_bounds__(TNT) k_plan_fill(GView g, PlanArgs p) {
+  __shared__ TileSmem sm;
+  const uint64_t v0 = (uint64_t)blockIdx.x * TV;
+  const int cnt = (int)min((uint64_t)TV, g.n - v0);
+  tile_offsets<OFF>(g, v0, cnt, sm.xs, sm.ts);
+  __syncthreads();
+  uint64_t st_[TV / TNT];
+  uint32_t d_[TV / TNT], w_[TV / TNT];
+  uint64_t mine = 0;
+#pragma unroll
+  for (int q = 0; q < TV / TNT; q++) {
+    const int i = threadIdx.x * (TV / TNT) + q;
+    d_[q] = 0;
+    if (i < cnt) vgeo<IDM>(g, sm.xs[i], sm.xs[i + 1], st_[q], d_[q], w_[q]);
+    const uint32_t k = items_of(g, d_[q]);
+    mine += ((uint64_t)k << 32) | (k > 1 ? 1u : 0u);
+  }
+  uint64_t total;
+  const uint64_t pre = block_excl_scan<uint64_t, TNT>(mine, total, sm.red64);
+  uint64_t it = p.tile_off[blockIdx.x] + (pre >> 32);
+  uint64_t slot = p.multi_off[blockIdx.x] + (uint32_t)pre;
+#pragma unroll
+  for (int q = 0; q < TV / TNT; q++) {
+    const uint32_t k = items_of(g, d_[q]);
+    if (k == 0) continue;
+    const uint64_t first = it;
+    for (uint32_t j = 0; j < k; j++) {
+      HeavyItem h;
+      h.bit = st_[q];
+      h.v = (uint32_t)(v0 + threadIdx.x * (TV / TNT) + q);
+      h.f0 = j * g.heavy_seg;
+      h.nf = min(g.heavy_seg, d_[q] - h.f0);
+      h.carry = 0;
+      h.deg = d_[q];
+      h.first = (uint32_t)first;
+      h.nitems = k;
+      h.w = w_[q];
+      h.slot = k > 1 ? (uint32_t)slot : 0xffffffffu;
+      p.items[it++] = h;
+    }
+    if (k > 1) p.multi[slot++] = (uint32_t)first;
+  }
+}
+
+// per item of a split vertex: the sum of its values (for gap-coded IDs the
+// first item's sum is its last ID, later items' sums are sums of differences)
+template <int IDM, int OFF>
+__global__ void __launch_bounds__(256) k_plan_carry(GView g, PlanArgs p) {
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t it = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < g.n_items; it += warps) {
+    const HeavyItem h = g.items[it];
+    if (h.nitems == 1) continue;
+    uint32_t carry = 0;
+    const uint32_t f1 = h.f0 + h.nf;
+    for (uint32_t base = h.f0; base < f1; base += 32 * HEAVY_U) {
+      uint32_t id[HEAVY_U];
+      warp_ids<IDM, HEAVY_U>(g, h.bit, h.w, base, f1, carry, id);
+    }
+    if ((threadIdx.x & 31) == 0) p.segsum[it] = carry;
   }
 }
 
@@ -622,15 +764,16 @@ cudaError_t launch_pr_init(const GView& g, const PrArgs& a, cudaStream_t st) {
 }
 template <int IDM, int OFF>
 cudaError_t launch_pr_pull(const GView& g, const PrArgs& a, cudaStream_t st) {
-  k_pr_pull<IDM, OFF><<<tiles_of(g.n), TNT, 0, st>>>(g, a);
+  k_pr_pull<IDM, OFF><<<heavy_blocks(g.n_items) + tiles_of(g.n), TNT, 0, st>>>(g, a);
   count_launch();
   return cudaGetLastError();
 }
 template <int IDM, int OFF>
 cudaError_t launch_bfs_pull(const GView& g, const BfsArgs& a, int mb, cudaStream_t st) {
-  if (mb == 2) { k_bfs_pull<IDM, OFF, uint16_t><<<tiles_of(g.n), TNT, 0, st>>>(g, a); count_launch(); }
-  else if (mb == 4) { k_bfs_pull<IDM, OFF, uint32_t><<<tiles_of(g.n), TNT, 0, st>>>(g, a); count_launch(); }
-  else { k_bfs_pull<IDM, OFF, uint64_t><<<tiles_of(g.n), TNT, 0, st>>>(g, a); count_launch(); }
+  const unsigned grid = heavy_blocks(g.n_items) + tiles_of(g.n);
+  if (mb == 2) { k_bfs_pull<IDM, OFF, uint16_t><<<grid, TNT, 0, st>>>(g, a); count_launch(); }
+  else if (mb == 4) { k_bfs_pull<IDM, OFF, uint32_t><<<grid, TNT, 0, st>>>(g, a); count_launch(); }
+  else { k_bfs_pull<IDM, OFF, uint64_t><<<grid, TNT, 0, st>>>(g, a); count_launch(); }
   return cudaGetLastError();
 }
 template <int IDM, int OFF>
@@ -656,12 +799,32 @@ cudaError_t launch_nbr_decode(const GView& g, const NbrArgs& a, cudaStream_t st)
   count_launch();
   return cudaGetLastError();
 }
+template <int IDM, int OFF>
+cudaError_t launch_plan_count(const GView& g, const PlanArgs& p, cudaStream_t st) {
+  k_plan_count<IDM, OFF><<<tiles_of(g.n), TNT, 0, st>>>(g, p);
+  count_launch();
+  return cudaGetLastError();
+}
+template <int IDM, int OFF>
+cudaError_t launch_plan_fill(const GView& g, const PlanArgs& p, cudaStream_t st) {
+  k_plan_fill<IDM, OFF><<<tiles_of(g.n), TNT, 0, st>>>(g, p);
+  count_launch();
+  return cudaGetLastError();
+}
+template <int IDM, int OFF>
+cudaError_t launch_plan_carry(const GView& g, const PlanArgs& p, cudaStream_t st) {
+  if (g.n_items == 0) return cudaSuccess;
+  k_plan_carry<IDM, OFF><<<grid_for(g.n_items, 8, 152 * 16), 256, 0, st>>>(g, p);
+  count_launch();
+  return cudaGetLastError();
+}
 
 template <int IDM, int OFF>
 const TravOps* make_ops() {
   static const TravOps ops = {
-      &launch_pr_init<IDM, OFF>,  &launch_pr_pull<IDM, OFF>,     &launch_bfs_pull<IDM, OFF>,
-      &launch_bfs_push<IDM, OFF>, &launch_nbr_degrees<IDM, OFF>, &launch_nbr_decode<IDM, OFF>,
+      &launch_pr_init<IDM, OFF>,    &launch_pr_pull<IDM, OFF>,     &launch_bfs_pull<IDM, OFF>,
+      &launch_bfs_push<IDM, OFF>,   &launch_nbr_degrees<IDM, OFF>, &launch_nbr_decode<IDM, OFF>,
+      &launch_plan_count<IDM, OFF>, &launch_plan_fill<IDM, OFF>,   &launch_plan_carry<IDM, OFF>,
   };
   return &ops;
 }

@@ -308,3 +308,45 @@ def test_pagerank_zero_iterations_and_sum_rule(rmat16):
     r = lg.lg_pagerank(g, 0.85, 20).cpu().numpy().astype(np.float64)
     iso = g0.degrees() == 0
     assert abs(r.sum() - (1.0 - iso.sum() * 0.85 / g0.n)) < 1e-3
+
+
+# ------------------------------------------------------------------ heavy-vertex schedule
+@pytest.fixture
+def small_schedule(monkeypatch):
+    """Force most vertices onto the warp schedule and split them into many items."""
+    monkeypatch.setenv("LG_HEAVY_MIN", "6")
+    monkeypatch.setenv("LG_HEAVY_SEG", "40")
+
+
+@pytest.mark.parametrize("mode,off", list(itertools.product(range(3), range(2))))
+def test_heavy_schedule_paths(rmat16, small_schedule, mode, off):
+    g0 = rmat16
+    g, e = encode_both(g0.n, g0.row_ptr, g0.col, mode=mode, off=off, relabel=(mode == 2))
+    st = lg.lg_stats_get(g)
+    assert st["bytes_schedule"] > 0
+    assert_arrays_equal(g, e)  # the schedule is derived data, the format is unchanged
+    assert_bfs(g, g0.n, g0.row_ptr, g0.col, gen.sources(g0, 20, seed=4))
+    assert_pagerank(g, g0.n, g0.row_ptr, g0.col, iters=20)
+
+
+def test_heavy_schedule_csr32(rmat16, small_schedule):
+    g0 = rmat16
+    g = lg.lg_encode(dev(g0.row_ptr, np.int64), dev(g0.col, np.int32), id_mode=lg.LG_ID_CSR32)
+    assert_bfs(g, g0.n, g0.row_ptr, g0.col, gen.sources(g0, 5, seed=6))
+    assert_pagerank(g, g0.n, g0.row_ptr, g0.col, iters=20)
+
+
+@pytest.mark.parametrize("mode,off", list(itertools.product(range(3), range(2))))
+def test_split_hubs_default_schedule(mode, off):
+    # two hubs of degree 9000 and 5000 (3 and 2 items at 4096 fields), leaves
+    # shared between them, and a tail path
+    n = 12000
+    edges = [(0, i) for i in range(1, 9001)] + [(1, i) for i in range(4000, 9000)]
+    edges += [(i, i + 1) for i in range(9001, n - 1)]
+    rp, col, _ = csr_from_edges(n, edges)
+    for relabel in (False, True):
+        g, e = encode_both(n, rp, col, mode=mode, off=off, relabel=relabel)
+        assert_arrays_equal(g, e)
+        assert_neighbors(g, rp, col, n, vertices=[0, 1, 2, 4500, 9001, n - 1])
+        assert_bfs(g, n, rp, col, [0, 4500, n - 1])
+        assert_pagerank(g, n, rp, col, iters=15)
