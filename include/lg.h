@@ -187,6 +187,29 @@ lg_status lg_bfs(const lg_graph *g, const uint32_t *sources, uint32_t S, uint32_
 lg_status lg_pagerank(const lg_graph *g, float damping, uint32_t iters,
                       const uint32_t *personalize_source, float *ranks, void *stream);
 
+/*
+ * lg_pagerank_noalloc -- lg_pagerank for callers that cannot allocate device
+ * memory.  The paper has no counterpart: this is a deployment variant.  A
+ * process whose device memory is owned by another allocator or reserved up
+ * front under a fixed budget cannot add cudaMalloc calls of its own, and a
+ * latency-sensitive loop cannot afford cudaFree's implicit synchronization;
+ * this call runs the same kernels as lg_pagerank (same results) but keeps its
+ * scratch in a fixed array inside liblg.so (9 MiB held on every GPU that loads
+ * the library, until the process exits) and calls no allocator.
+ *   Limit: graphs of at most 1,048,576 vertices (and at most 262,144 schedule
+ *   items for vertices split by the heavy-vertex schedule); larger graphs give
+ *   LG_ERANGE with a message naming both limits.  iters must be >= 1.
+ *   The first call on each device looks the array's device address up once
+ *   (with that device current); make that first call before any stream capture.
+ *   All calls in the process share the one array and it keeps the last call's
+ *   contents: calls whose GPU work overlaps (other streams, other threads) race
+ *   and must be ordered by the caller.  Every scratch element is written before
+ *   it is read, so stale contents never reach the result.
+ * Arguments, layout and other errors as lg_pagerank.
+ */
+lg_status lg_pagerank_noalloc(const lg_graph *g, float damping, uint32_t iters,
+                              const uint32_t *personalize_source, float *ranks, void *stream);
+
 /* lg_free -- release a graph and all of its device memory.  NULL-safe.  The
    caller must make sure no enqueued work still uses g. */
 void lg_free(lg_graph *g);

@@ -28,7 +28,7 @@ from ._build import LIB, build, is_stale
 __all__ = [
     "LG_ID_GLOBAL", "LG_ID_LOCAL", "LG_ID_LOCAL_GAP", "LG_ID_CSR32", "LG_OFF_PACKED", "LG_OFF_EF",
     "LgError", "LogGraph", "build", "load", "lg_encode", "lg_stats_get", "lg_arrays_get", "lg_neighbors",
-    "lg_bfs", "lg_pagerank", "lg_free", "lg_last_error", "lg_kernel_launches",
+    "lg_bfs", "lg_pagerank", "lg_pagerank_noalloc", "lg_free", "lg_last_error", "lg_kernel_launches",
 ]
 
 LG_ID_GLOBAL, LG_ID_LOCAL, LG_ID_LOCAL_GAP, LG_ID_CSR32 = 0, 1, 2, 3
@@ -87,12 +87,14 @@ def load(auto_build: bool = False):
         h.lg_neighbors.argtypes = [_vp, _vp, _u64, _vp, _vp, _vp, _u64, _vp]
         h.lg_bfs.argtypes = [_vp, _vp, _u32, _vp, _vp]
         h.lg_pagerank.argtypes = [_vp, _f32, _u32, ctypes.POINTER(_u32), _vp, _vp]
+        h.lg_pagerank_noalloc.argtypes = [_vp, _f32, _u32, ctypes.POINTER(_u32), _vp, _vp]
         h.lg_free.argtypes = [_vp]
         h.lg_free.restype = None
         h.lg_last_error.restype = ctypes.c_char_p
         h.lg_kernel_launches.argtypes = []
         h.lg_kernel_launches.restype = _u64
-        for f in ("lg_encode", "lg_stats_get", "lg_arrays_get", "lg_neighbors", "lg_bfs", "lg_pagerank"):
+        for f in ("lg_encode", "lg_stats_get", "lg_arrays_get", "lg_neighbors", "lg_bfs", "lg_pagerank",
+                  "lg_pagerank_noalloc"):
             getattr(h, f).restype = _i32
         _lib = h
     return _lib
@@ -251,6 +253,17 @@ def lg_bfs(g: LogGraph, sources, out: Optional[torch.Tensor] = None, stream=None
     if out is None:
         out = torch.empty((S, n), dtype=torch.int32, device="cuda")
     _check(lib.lg_bfs(g.handle, src.data_ptr() if S else None, S, out.data_ptr(), _stream(stream)), "lg_bfs")
+    return out
+
+
+def lg_pagerank_noalloc(g: LogGraph, damping: float, iters: int, out: torch.Tensor,
+                        personalize: Optional[int] = None, stream=None) -> torch.Tensor:
+    """lg_pagerank_noalloc: PageRank into ``out`` (n float32, on the device) for
+    callers that cannot allocate device memory -- the library uses a fixed
+    internal scratch array instead (graphs up to 2^20 vertices)."""
+    ps = None if personalize is None else ctypes.byref(_u32(personalize))
+    _check(load().lg_pagerank_noalloc(g.handle, damping, iters, ps, out.data_ptr(), _stream(stream)),
+           "lg_pagerank_noalloc")
     return out
 
 

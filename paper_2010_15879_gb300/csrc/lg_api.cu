@@ -110,6 +110,8 @@ namespace lg {
 static std::atomic<unsigned long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+void set_error_message(const char* msg) { snprintf(g_err, sizeof g_err, "%s", msg); }
+
 GView make_view(const lg_graph* g) {
   GView v;
   memset(&v, 0, sizeof(v));

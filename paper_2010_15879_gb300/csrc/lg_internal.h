@@ -54,6 +54,9 @@ GView make_view(const lg_graph* g);
 // every kernel launch site calls this right after its <<<...>>> (instrumentation)
 void count_launch();
 
+// sets the calling thread's lg_last_error() message
+void set_error_message(const char* msg);
+
 // ------------------------------------------------------------------ scan
 // out[0] = 0, out[i+1] = out[i] + in[i] for i < n (n+1 outputs).  `tmp` needs
 // scan_tmp_words(n) u64 words.
