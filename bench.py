@@ -51,9 +51,55 @@ WORKLOADS = {
                dict(id_mode=0, off_mode=0, relabel=False), 64, 20),
     "rmat27": ("R-MAT scale 27, edge factor 16, weights in [1,255] at 8 bits; global 27-bit IDs + "
                "Elias-Fano offsets",
-               lambda: gen.rmat_s27_ef16_weighted(seed=5),
+               None,  # built on the device (gen.rmat_gpu)
                dict(id_mode=0, off_mode=1, relabel=False, weight_bits=8), 16, 20),
 }
+
+
+class Workload:
+    """The input graph on the device (and on the host, made on demand)."""
+
+    def __init__(self, name, dev):
+        import torch
+
+        self.desc, make, self.opts, self.S, self.T = WORKLOADS[name]
+        t0 = time.time()
+        if make is None:
+            rp, col, w = gen.rmat_gpu(27, 16, seed=5, weighted=True)
+            self.rp_d, self.col_d, self.w_d = rp, col, w
+            self._host = None
+            self.name = "rmat_s27_ef16_seed5"
+        else:
+            g0 = make()
+            self._host = (g0.row_ptr, g0.col, g0.weights if "weight_bits" in self.opts else None)
+            self.rp_d = torch.from_numpy(g0.row_ptr.view(np.int64)).to(dev)
+            self.col_d = torch.from_numpy(g0.col.view(np.int32)).to(dev)
+            self.w_d = None if self._host[2] is None else torch.from_numpy(self._host[2].view(np.int32)).to(dev)
+            self.name = g0.name
+        self.n = self.rp_d.numel() - 1
+        self.arcs = self.col_d.numel()
+        self.deg_d = self.rp_d[1:] - self.rp_d[:-1]
+        log(f"generated {self.name}: n={self.n} arcs={self.arcs} in {time.time() - t0:.1f}s")
+
+    def host(self):
+        """(row_ptr u64, col u32, weights u32 or None) numpy arrays."""
+        if self._host is None:
+            w = None if self.w_d is None else self.w_d.cpu().numpy().view(np.uint32)
+            self._host = (self.rp_d.cpu().numpy().view(np.uint64), self.col_d.cpu().numpy().view(np.uint32), w)
+        return self._host
+
+    def sources(self):
+        class _G:
+            pass
+        _G.n, _G.row_ptr = self.n, self.host()[0]
+        return gen.sources(_G, self.S, seed=7)
+
+    def teps_bfs(self, depths):
+        """Graph500 traversed edges summed over the sources (on the device)."""
+        total = 0
+        for row in depths:
+            total += int(self.deg_d[row != -1].sum().item()) // 2
+        return total
 HBM_FALLBACK_GBS = 6800.0
 
 
@@ -143,12 +189,20 @@ class ClockSampler:
                 "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": reasons}
 
 
-def teps_bfs(depths_u32: np.ndarray, deg: np.ndarray) -> int:
-    """Graph500 traversed edges: sum of degrees of reached vertices / 2, per source."""
-    total = 0
-    for row in depths_u32:
-        total += int(deg[row != 0xFFFFFFFF].sum()) // 2
-    return total
+def combine_replicas(step_ms, e2e_ms, te_step, world, device=None):
+    """Whole-job numbers for `world` independent replicas (one graph per GPU, no
+    collective on the data path): every rank traverses te_step edges per step,
+    the job's step time is the slowest rank's (max over ranks), and the value
+    is all ranks' edges over that time.  Needs an initialized process group
+    when world > 1."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([step_ms, e2e_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms, e2e_ms = float(t[0]), float(t[1])
+    return (step_ms, e2e_ms, world * te_step / (step_ms * 1e-3) / 1e9,
+            world * te_step / (e2e_ms * 1e-3) / 1e9)
 
 
 # --------------------------------------------------------------------- GPU arm
@@ -160,20 +214,13 @@ def run_lg(args, rank, world):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     lg.load(auto_build=True)
-    desc, make, opts, S, T = WORKLOADS[args.workload]
-    t0 = time.time()
-    g0 = make()
-    log(f"[rank {rank}] generated {g0.name}: n={g0.n} arcs={g0.arcs} in {time.time() - t0:.1f}s")
-    deg = g0.degrees()
-    src_h = gen.sources(g0, S, seed=7)
-    rp_h = torch.from_numpy(g0.row_ptr.view(np.int64))
-    col_h = torch.from_numpy(g0.col.view(np.int32))
-    w_h = None if g0.weights is None or "weight_bits" not in opts else torch.from_numpy(g0.weights.view(np.int32))
-    rp_d, col_d = rp_h.to(dev), col_h.to(dev)
-    w_d = None if w_h is None else w_h.to(dev)
+    wl = Workload(args.workload, dev)
+    desc, opts, S, T = wl.desc, wl.opts, wl.S, wl.T
+    src_h = wl.sources()
+    rp_d, col_d, w_d = wl.rp_d, wl.col_d, wl.w_d
     src_d = torch.from_numpy(src_h.view(np.int32)).to(dev)
-    depths = torch.empty((S, g0.n), dtype=torch.int32, device=dev)
-    ranks = torch.empty(g0.n, dtype=torch.float32, device=dev)
+    depths = torch.empty((S, wl.n), dtype=torch.int32, device=dev)
+    ranks = torch.empty(wl.n, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     def barrier():
@@ -218,24 +265,30 @@ def run_lg(args, rank, world):
             f"bfs {np.median(bfs):.2f}, pr {np.median(pr):.2f})")
         return dict(ms=ms, enc=enc, bfs=bfs, pr=pr, stats=st, launches=launches)
 
-    # correctness-independent TEPS accounting from one BFS run
+    # TEPS accounting from one BFS run
     step(opts)
     torch.cuda.synchronize(dev)
-    te_bfs = teps_bfs(depths.cpu().numpy().view(np.uint32), deg)
-    te_pr = g0.arcs * T
+    te_bfs = wl.teps_bfs(depths)
+    te_pr = wl.arcs * T
     te_step = te_bfs + te_pr
 
     with ClockSampler(dev.index) as clk:
         res = timed(opts, "log(graph)")
     clocks = clk.summary()
     csr = timed(dict(id_mode=3, relabel=False), "csr32")
+    # the same CSR in the DM order, when the compressed arm relabels (ordering alone changes locality)
+    csr_dm = timed(dict(id_mode=3, relabel=True), "csr32 in DM order") if opts.get("relabel") else None
 
     # e2e: host CSR in pinned memory -> device -> hot path -> results to pinned host
+    rp_hn, col_hn, w_hn = wl.host()
+    rp_h = torch.from_numpy(rp_hn.view(np.int64))
+    col_h = torch.from_numpy(col_hn.view(np.int32))
+    w_h = None if w_hn is None else torch.from_numpy(w_hn.view(np.int32))
     rp_p, col_p = rp_h.pin_memory(), col_h.pin_memory()
     w_p = None if w_h is None else w_h.pin_memory()
     src_p = torch.from_numpy(src_h.view(np.int32)).pin_memory()
-    dep_p = torch.empty((S, g0.n), dtype=torch.int32).pin_memory()
-    rk_p = torch.empty(g0.n, dtype=torch.float32).pin_memory()
+    dep_p = torch.empty((S, wl.n), dtype=torch.int32).pin_memory()
+    rk_p = torch.empty(wl.n, dtype=torch.float32).pin_memory()
 
     def e2e_step():
         g = lg.lg_encode(rp_p, col_p, w_p, **opts)
@@ -258,7 +311,7 @@ def run_lg(args, rank, world):
     barrier()
     e2e_ms = e0.elapsed_time(e1) / args.steps
     h2d = rp_h.numel() * 8 + col_h.numel() * 4 + (0 if w_h is None else w_h.numel() * 4) + S * 4
-    d2h = S * g0.n * 4 + g0.n * 4
+    d2h = S * wl.n * 4 + wl.n * 4
 
     step_ms = res["ms"] / args.steps
     st = res["stats"]
@@ -269,7 +322,7 @@ def run_lg(args, rank, world):
     # algorithmic bytes of one PageRank pull launch: the compressed A and O
     # payload, a 4 B contribution gather per arc and a 4 B contribution write
     # per vertex
-    alg_bytes = (st["bits_A"] + st["bits_O"]) // 8 + 4 * g0.arcs + 4 * g0.n
+    alg_bytes = (st["bits_A"] + st["bits_O"]) // 8 + 4 * wl.arcs + 4 * wl.n
     peak, peak_kind = peaks()
     achieved = alg_bytes / (pr_ms_iter * 1e-3) / 1e9
 
@@ -278,19 +331,14 @@ def run_lg(args, rank, world):
         "value": None, "unit": "GTEPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u32 ids / fp32 ranks", "data": "synthetic (seeded generator; no dataset)",
-        "config": {"workload": desc, "n": g0.n, "arcs": g0.arcs, "bfs_sources": S, "pr_iters": T,
+        "config": {"workload": desc, "n": wl.n, "arcs": wl.arcs, "bfs_sources": S, "pr_iters": T,
                    "damping": 0.85, "l2": "inputs larger than L2 (CSR %.2f GB)" %
-                   ((g0.n + 1) * 8 / 1e9 + g0.arcs * 4 / 1e9), "parallelism": f"replicas x{world}"},
+                   ((wl.n + 1) * 8 / 1e9 + wl.arcs * 4 / 1e9), "parallelism": f"replicas x{world}"},
     }
-    local = {"te_step": te_step, "step_ms": step_ms, "e2e_ms": e2e_ms}
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([step_ms, e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms, e2e_ms = float(t[0]), float(t[1])
+    step_ms, e2e_ms, value, e2e_value = combine_replicas(step_ms, e2e_ms, te_step, world, dev)
     out["ms_per_step"] = step_ms
-    out["value"] = world * te_step / (step_ms * 1e-3) / 1e9
-    out["e2e"] = {"value": world * te_step / (e2e_ms * 1e-3) / 1e9, "unit": "GTEPS", "ms_per_step": e2e_ms,
+    out["value"] = value
+    out["e2e"] = {"value": e2e_value, "unit": "GTEPS", "ms_per_step": e2e_ms,
                   "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
     out["gpu_launches"] = int(res["launches"])
     out["detail"] = {
@@ -302,9 +350,14 @@ def run_lg(args, rank, world):
                   "bfs_ms": csr_bfs_ms, "pr_ms_per_iter": csr_pr_ms_iter,
                   "bfs_gteps": te_bfs / (csr_bfs_ms * 1e-3) / 1e9,
                   "pr_gteps": te_pr / (csr_pr_ms_iter * T * 1e-3) / 1e9,
-                  "bytes_payload": 4 * g0.arcs + 8 * (g0.n + 1),
+                  "bytes_payload": 4 * wl.arcs + 8 * (wl.n + 1),
                   "value": te_step / (csr["ms"] / args.steps * 1e-3) / 1e9},
-        "bytes_vs_csr32": ((st["bits_A"] + st["bits_O"]) / 8) / (4 * g0.arcs + 8 * (g0.n + 1)),
+        "csr32_dm_order": None if csr_dm is None else {
+            "note": "the same uncompressed CSR relabeled by the same DM permuter",
+            "step_ms": csr_dm["ms"] / args.steps, "encode_ms": float(np.median(csr_dm["enc"])),
+            "bfs_ms": float(np.median(csr_dm["bfs"])), "pr_ms_per_iter": float(np.median(csr_dm["pr"])) / T,
+            "value": te_step / (csr_dm["ms"] / args.steps * 1e-3) / 1e9},
+        "bytes_vs_csr32": ((st["bits_A"] + st["bits_O"]) / 8) / (4 * wl.arcs + 8 * (wl.n + 1)),
         "bfs_gteps_vs_csr32": csr_bfs_ms / bfs_ms, "pr_gteps_vs_csr32": csr_pr_ms_iter / pr_ms_iter,
     }
     out["roofline"] = {"kernel": "k_pr_pull (PageRank pull iteration, decode fused)", "bound": "hbm",
@@ -314,28 +367,31 @@ def run_lg(args, rank, world):
                        "traffic": ncu_traffic(args.workload)}
     out["clocks"] = clocks
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(g0, src_h, T, min_seconds=10.0)
+        rp_hn, col_hn, _ = wl.host()
+        out["cpu_baseline"] = cpu_baseline(wl.n, rp_hn, col_hn, src_h, min_seconds=10.0,
+                                           bfs_only=(args.workload == "rmat27"))
     return out, rank
 
 
 # ------------------------------------------------------------------ CPU oracle
-def cpu_baseline(g0, src_h, T, min_seconds=10.0, max_units=None):
+def cpu_baseline(n, rp, col, src_h, min_seconds=10.0, max_units=None, bfs_only=False):
     """The oracle as it stands (single-threaded C) on a bounded sample: BFS from
     the first sources and whole PageRank iterations, until about min_seconds."""
     import oracle
 
-    deg = g0.degrees()
+    deg = np.diff(rp).astype(np.int64)
     te = 0
     t0 = time.time()
     nb = npr = 0
     while True:
         s = int(src_h[nb % len(src_h)])
-        d = oracle.bfs(g0.n, g0.row_ptr, g0.col, s)
+        d = oracle.bfs(n, rp, col, s)
         te += int(deg[d != 0xFFFFFFFF].sum()) // 2
         nb += 1
-        oracle.pagerank(g0.n, g0.row_ptr, g0.col, 0.85, 1)
-        te += g0.arcs
-        npr += 1
+        if not bfs_only:
+            oracle.pagerank(n, rp, col, 0.85, 1)
+            te += col.shape[0]
+            npr += 1
         el = time.time() - t0
         if el >= min_seconds or (max_units and nb >= max_units):
             break
@@ -351,13 +407,10 @@ def profile_pass(args):
     import paper_2010_15879_gb300 as lg
 
     lg.load(auto_build=True)
-    desc, make, opts, S, T = WORKLOADS[args.workload]
-    T = args.pr_iters if args.pr_iters is not None else T
-    g0 = make()
-    rp = torch.from_numpy(g0.row_ptr.view(np.int64)).cuda()
-    col = torch.from_numpy(g0.col.view(np.int32)).cuda()
-    w = None if g0.weights is None or "weight_bits" not in opts else torch.from_numpy(g0.weights.view(np.int32)).cuda()
-    src = torch.from_numpy(gen.sources(g0, S, seed=7).view(np.int32)).cuda()
+    wl = Workload(args.workload, torch.device("cuda", 0))
+    opts, T = wl.opts, (args.pr_iters if args.pr_iters is not None else wl.T)
+    rp, col, w = wl.rp_d, wl.col_d, wl.w_d
+    src = torch.from_numpy(wl.sources().view(np.int32)).cuda()
     arms = {"lg": opts, "csr32": dict(id_mode=3, relabel=False)}
     for name in (["lg", "csr32"] if args.profile == "both" else [args.profile]):
         g = lg.lg_encode(rp, col, w, **arms[name])
@@ -369,26 +422,35 @@ def profile_pass(args):
 
 
 def run_reference(args, rank, world):
-    desc, make, opts, S, T = WORKLOADS[args.workload]
-    g0 = make()
-    src_h = gen.sources(g0, S, seed=7)
+    import torch
+
+    dev = torch.device("cuda", 0) if (args.workload == "rmat27" and torch.cuda.is_available()) else None
+    if args.workload == "rmat27":
+        wl = Workload(args.workload, dev)
+        n, (rp, col, _), src_h, desc, S, T = wl.n, wl.host(), wl.sources(), wl.desc, wl.S, wl.T
+    else:
+        desc, make, opts, S, T = WORKLOADS[args.workload]
+        g0 = make()
+        n, rp, col = g0.n, g0.row_ptr, g0.col
+        src_h = gen.sources(g0, S, seed=7)
+    bfs_only = args.workload == "rmat27"
     for _ in range(args.warmup):
-        cpu_baseline(g0, src_h, T, min_seconds=0.0, max_units=1)
+        cpu_baseline(n, rp, col, src_h, min_seconds=0.0, max_units=1, bfs_only=bfs_only)
     t0 = time.time()
     vals = []
     for _ in range(args.steps):
-        vals.append(cpu_baseline(g0, src_h, T, min_seconds=0.0, max_units=1))
+        vals.append(cpu_baseline(n, rp, col, src_h, min_seconds=0.0, max_units=1, bfs_only=bfs_only))
     el = time.time() - t0
     v = float(np.mean([x["value"] for x in vals]))
+    sample = "per step: 1 BFS source" + ("" if bfs_only else " + 1 PageRank iteration") + " of the same graph"
     out = {"impl": "reference", "metric": "GTEPS (BFS 16 sources + PageRank 20 iterations, Log(Graph) "
                                           "compressed, full step incl. encode)",
            "value": v, "unit": "GTEPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64 ranks / u32 depths", "data": "synthetic (seeded generator)",
-           "config": {"workload": desc, "n": g0.n, "arcs": g0.arcs, "bfs_sources": S, "pr_iters": T,
+           "config": {"workload": desc, "n": n, "arcs": int(col.shape[0]), "bfs_sources": S, "pr_iters": T,
                       "parallelism": "host cores"},
-           "cpu_baseline": {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle",
-                            "sample": "per step: 1 BFS source + 1 PageRank iteration of the same graph"},
+           "cpu_baseline": {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": sample},
            "e2e": {"value": v, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     return out, rank
 

@@ -27,8 +27,11 @@ import numpy as np
 _DIR = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_DIR, "lggen.c")
 _LIB = os.path.join(_DIR, "liblggen.so")
+_GPU_SRC = os.path.join(_DIR, "lggen_gpu.cu")
+_GPU_LIB = os.path.join(_DIR, "liblggen_gpu.so")
 _lock = threading.Lock()
 _handle = None
+_gpu_handle = None
 
 
 class _Csr(ctypes.Structure):
@@ -51,6 +54,34 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+def build_gpu(force: bool = False) -> str:
+    """Compile ``liblggen_gpu.so`` (nvcc, sm_103a) for the device-side R-MAT builder."""
+    if force or not os.path.exists(_GPU_LIB) or os.path.getmtime(_GPU_LIB) < os.path.getmtime(_GPU_SRC):
+        import shutil
+        nvcc = os.environ.get("NVCC") or shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+        tmp = _GPU_LIB + f".tmp{os.getpid()}"
+        subprocess.check_call([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-Xcompiler", "-fPIC",
+                               "-shared", "-o", tmp, _GPU_SRC])
+        os.replace(tmp, _GPU_LIB)
+    return _GPU_LIB
+
+
+def _gpu_lib():
+    global _gpu_handle
+    with _lock:
+        if _gpu_handle is None:
+            build_gpu()
+            h = ctypes.CDLL(_GPU_LIB)
+            u64, i32, dbl, vp = ctypes.c_uint64, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+            h.lggen_gpu_rmat_count.argtypes = [i32, u64, dbl, dbl, dbl, u64, vp, vp, vp]
+            h.lggen_gpu_rmat_scatter.argtypes = [i32, u64, dbl, dbl, dbl, u64, vp, vp, vp, vp]
+            h.lggen_gpu_weights.argtypes = [vp, vp, u64, u64, vp, vp]
+            for f in (h.lggen_gpu_rmat_count, h.lggen_gpu_rmat_scatter, h.lggen_gpu_weights):
+                f.restype = i32
+            _gpu_handle = h
+    return _gpu_handle
+
+
 def _lib():
     global _handle
     with _lock:
@@ -64,6 +95,8 @@ def _lib():
             h.lggen_from_edges.argtypes = [u64, u64, p(u32), p(u32), i32, u64, p(_Csr)]
             h.lggen_sources.argtypes = [u64, p(u64), u32, u64, p(u32)]
             h.lggen_free.argtypes = [p(_Csr)]
+            h.lggen_rmat_perm.argtypes = [i32, u64, p(u32)]
+            h.lggen_rmat_perm.restype = i32
             h.lggen_hash.argtypes = [u64, u64, u64, u64]
             h.lggen_hash.restype = u64
             for f in (h.lggen_rmat, h.lggen_community, h.lggen_from_edges, h.lggen_sources):
@@ -90,14 +123,44 @@ class Graph:
         return np.diff(self.row_ptr).astype(np.int64)
 
 
+class _Owner:
+    """Keeps the C-allocated arrays alive while numpy views exist; frees them after."""
+
+    def __init__(self, c: _Csr):
+        self.c = c
+
+    def __del__(self):
+        try:
+            _lib().lggen_free(ctypes.byref(self.c))
+        except Exception:
+            pass
+
+
+def _view(ptr, count, owner):
+    a = np.ctypeslib.as_array(ptr, shape=(max(count, 1),))[:count]
+    # tie the buffer's lifetime to `owner` through the array's base chain
+    holder = np.ndarray(shape=a.shape, dtype=a.dtype, buffer=a)
+    holder.flags.writeable = True
+    return holder if owner is None else _OwnedArray(holder, owner)
+
+
+class _OwnedArray(np.ndarray):
+    def __new__(cls, arr, owner):
+        obj = np.asarray(arr).view(cls)
+        obj._owner = owner
+        return obj
+
+    def __array_finalize__(self, obj):
+        self._owner = getattr(obj, "_owner", None)
+
+
 def _take(c: _Csr, name: str) -> Graph:
+    """Wraps the generator's arrays without copying (large graphs need tens of GB)."""
     n, arcs = int(c.n), int(c.arcs)
-    rp = np.ctypeslib.as_array(c.row_ptr, shape=(n + 1,)).copy()
-    col = np.ctypeslib.as_array(c.col, shape=(max(arcs, 1),))[:arcs].copy()
-    w = None
-    if bool(c.w):
-        w = np.ctypeslib.as_array(c.w, shape=(max(arcs, 1),))[:arcs].copy()
-    _lib().lggen_free(ctypes.byref(c))
+    owner = _Owner(c)
+    rp = _view(c.row_ptr, n + 1, owner)
+    col = _view(c.col, arcs, owner)
+    w = _view(c.w, arcs, owner) if bool(c.w) else None
     return Graph(n=n, row_ptr=rp, col=col, weights=w, name=name)
 
 
@@ -114,6 +177,68 @@ def rmat(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19, c:
     _check(_lib().lggen_rmat(scale, edge_factor, a, b, c, seed, int(weighted), int(permute),
                              threads, ctypes.byref(out)), "lggen_rmat")
     return _take(out, f"rmat_s{scale}_ef{edge_factor}_seed{seed}")
+
+
+def rmat_gpu(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19, c: float = 0.19,
+             seed: int = 1, weighted: bool = False, permute: bool = True, chunk: int = 1 << 28):
+    """The same graph as :func:`rmat`, built on the current CUDA device (for
+    scales that take too long on the host).  Returns torch tensors
+    ``(row_ptr int64[n+1], col int32[arcs], weights int32[arcs] or None)`` on the
+    device holding uint64 / uint32 values; plumbing steps (prefix sums, the
+    chunked row sorts, deduplication) use torch."""
+    import torch
+
+    lib = _gpu_lib()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    st = torch.cuda.current_stream().cuda_stream
+    n, m = 1 << scale, edge_factor << scale
+    perm = None
+    if permute:
+        ph = np.empty(n, dtype=np.uint32)
+        _check(_lib().lggen_rmat_perm(scale, seed, ph.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))),
+               "lggen_rmat_perm")
+        perm = torch.from_numpy(ph.view(np.int32)).to(dev)
+    pptr = None if perm is None else perm.data_ptr()
+    deg = torch.zeros(n, dtype=torch.int64, device=dev)
+    _check(lib.lggen_gpu_rmat_count(scale, m, a, a + b, a + b + c, seed, pptr, deg.data_ptr(), st), "rmat_count")
+    rp = torch.zeros(n + 1, dtype=torch.int64, device=dev)
+    torch.cumsum(deg, 0, out=rp[1:])
+    total = int(rp[-1].item())
+    col = torch.empty(total, dtype=torch.int32, device=dev)
+    cursor = rp[:-1].clone()
+    _check(lib.lggen_gpu_rmat_scatter(scale, m, a, a + b, a + b + c, seed, pptr, cursor.data_ptr(),
+                                      col.data_ptr(), st), "rmat_scatter")
+    del cursor, perm
+    # sort each row and drop duplicate arcs, rows taken in chunks of <= `chunk` arcs
+    rp_h = rp.cpu().numpy()
+    new_deg = torch.zeros(n, dtype=torch.int64, device=dev)
+    w_pos, r0 = 0, 0
+    while r0 < n:
+        r1 = int(np.searchsorted(rp_h, rp_h[r0] + chunk, side="right")) - 1
+        r1 = min(max(r1, r0 + 1), n)
+        s0, s1 = int(rp_h[r0]), int(rp_h[r1])
+        if s1 > s0:
+            rows = torch.repeat_interleave(torch.arange(r1 - r0, device=dev, dtype=torch.int64), deg[r0:r1])
+            key = (rows << 32) | (col[s0:s1].to(torch.int64) & 0xFFFFFFFF)
+            del rows
+            key = torch.sort(key).values
+            keep = torch.ones_like(key, dtype=torch.bool)
+            keep[1:] = key[1:] != key[:-1]
+            key = key[keep]
+            del keep
+            new_deg[r0:r1] = torch.bincount(key >> 32, minlength=r1 - r0)
+            col[w_pos:w_pos + key.numel()] = (key & 0xFFFFFFFF).to(torch.int32)
+            w_pos += key.numel()
+            del key
+        r0 = r1
+    col = col[:w_pos].clone()
+    rp = torch.zeros(n + 1, dtype=torch.int64, device=dev)
+    torch.cumsum(new_deg, 0, out=rp[1:])
+    w = None
+    if weighted:
+        w = torch.empty(w_pos, dtype=torch.int32, device=dev)
+        _check(lib.lggen_gpu_weights(rp.data_ptr(), col.data_ptr(), n, seed, w.data_ptr(), st), "weights")
+    return rp, col, w
 
 
 def community(log2n: int = 24, log2block: int = 10, zipf_kmax: int = 1 << 14, zipf_s: float = 2.0,
@@ -153,6 +278,63 @@ def sources(g: Graph, count: int, seed: int) -> np.ndarray:
 def hash4(seed: int, stream: int, i: int, j: int) -> int:
     """The counter-based SplitMix64 draw used by every generator."""
     return int(_lib().lggen_hash(seed, stream, i, j))
+
+
+@dataclass
+class Batch:
+    """Independent graphs concatenated: graph g owns vertices
+    [vptr[g], vptr[g+1]) and arcs [row_ptr[vptr[g]], row_ptr[vptr[g+1]]);
+    col holds LOCAL neighbor IDs (< n_g)."""
+
+    vptr: np.ndarray  # uint64[G+1]
+    row_ptr: np.ndarray  # uint64[V+1], global arc offsets
+    col: np.ndarray  # uint32[arcs], local IDs
+    scales: np.ndarray
+    edge_factors: np.ndarray
+
+    @property
+    def count(self) -> int:
+        return int(self.vptr.shape[0] - 1)
+
+    def graph(self, g: int) -> Graph:
+        v0, v1 = int(self.vptr[g]), int(self.vptr[g + 1])
+        a0 = int(self.row_ptr[v0])
+        rp = (self.row_ptr[v0:v1 + 1] - np.uint64(a0)).astype(np.uint64)
+        return Graph(n=v1 - v0, row_ptr=rp, col=self.col[a0:int(self.row_ptr[v1])], name=f"batch[{g}]")
+
+
+def rmat_batch(count: int = 4096, seed: int = 3, scale_lo: int = 8, scale_hi: int = 16, ef_lo: int = 4,
+               ef_hi: int = 32, threads: int = 0) -> Batch:
+    """`count` independent R-MAT graphs (a, b, c = .57, .19, .19): graph g has
+    scale floor(U), U uniform in [scale_lo, scale_hi + 1) (so n is log-uniform
+    over powers of two) and an edge factor uniform in [ef_lo, ef_hi], both
+    drawn from SplitMix64(seed, stream 7, g); the graph itself uses seed
+    seed * 1000003 + g.  Graphs are built in parallel on the host."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    span = scale_hi - scale_lo + 1
+    scales = np.array([scale_lo + int((hash4(seed, 7, g, 0) >> 11) * span // (1 << 53)) for g in range(count)])
+    efs = np.array([ef_lo + int(hash4(seed, 7, g, 1) % (ef_hi - ef_lo + 1)) for g in range(count)])
+    workers = threads or (os.cpu_count() or 4)
+
+    def one(g):
+        return rmat(int(scales[g]), int(efs[g]), seed=seed * 1000003 + g, threads=1)
+
+    with ThreadPoolExecutor(workers) as ex:
+        graphs = list(ex.map(one, range(count)))
+    ns = np.array([x.n for x in graphs], dtype=np.uint64)
+    vptr = np.zeros(count + 1, dtype=np.uint64)
+    np.cumsum(ns, out=vptr[1:])
+    arcs = np.array([x.arcs for x in graphs], dtype=np.uint64)
+    abase = np.zeros(count + 1, dtype=np.uint64)
+    np.cumsum(arcs, out=abase[1:])
+    row_ptr = np.empty(int(vptr[-1]) + 1, dtype=np.uint64)
+    col = np.empty(int(abase[-1]), dtype=np.uint32)
+    for g, x in enumerate(graphs):
+        row_ptr[int(vptr[g]):int(vptr[g + 1])] = x.row_ptr[:-1] + abase[g]
+        col[int(abase[g]):int(abase[g + 1])] = x.col
+    row_ptr[-1] = abase[-1]
+    return Batch(vptr=vptr, row_ptr=row_ptr, col=col, scales=scales, edge_factors=efs)
 
 
 # --- named workloads (synthetic stand-ins for the paper's Kronecker graphs) ---

@@ -9,8 +9,9 @@
  *
  * Randomness is counter-based: every draw is SplitMix64 (Steele, Lea, Flood,
  * "Fast splittable pseudorandom number generators", OOPSLA 2014) applied to a
- * tuple (seed, stream, i, j), so any subset of edges can be regenerated
- * independently and the result does not depend on the thread count.
+ * tuple (seed, stream, i, j) (R-MAT: to a per-edge key plus the level), so any
+ * subset of edges can be regenerated independently and the result does not
+ * depend on the thread count.
  *
  * Generators:
  *   - R-MAT / Kronecker (Chakrabarti et al. 2004; the Kronecker graphs of the
@@ -95,10 +96,16 @@ typedef struct {
     const uint32_t *perm; /* label permutation or NULL */
 } edge_src;
 
+/* Edge e draws one key h4(seed, RMAT, e, 0) and then one SplitMix64 output per
+   two levels (32 uniform bits per level). */
 static inline void rmat_edge(const edge_src *g, uint64_t e, uint32_t *u, uint32_t *v) {
     uint64_t s = 0, d = 0;
+    const uint64_t key = h4(g->seed, ST_RMAT, e, 0);
+    uint64_t h = 0;
     for (int k = 0; k < g->scale; k++) {
-        double x = u01(h4(g->seed, ST_RMAT, e, (uint64_t)k));
+        if ((k & 1) == 0) h = sm64(key + (uint64_t)k);
+        const uint32_t r32 = (k & 1) ? (uint32_t)h : (uint32_t)(h >> 32);
+        double x = (double)r32 * (1.0 / 4294967296.0);
         uint64_t sb, db;
         if (x < g->a) { sb = 0; db = 0; }
         else if (x < g->ab) { sb = 0; db = 1; }
@@ -323,6 +330,16 @@ int lggen_community(int log2n, int log2block, uint32_t zipf_kmax, double zipf_s,
     free(perm);
     free(dp);
     return rc;
+}
+
+/* The label permutation lggen_rmat applies (for the GPU edge generator). */
+int lggen_rmat_perm(int scale, uint64_t seed, uint32_t *out) {
+    if (scale < 1 || scale > 31 || !out) return LGGEN_EINVAL;
+    uint32_t *p = fisher_yates(1ULL << scale, seed, ST_PERM);
+    if (!p) return LGGEN_ENOMEM;
+    memcpy(out, p, sizeof(uint32_t) << scale);
+    free(p);
+    return LGGEN_OK;
 }
 
 /* Explicit edge list -> symmetric CSR (tests and small fixtures). */

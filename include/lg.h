@@ -100,7 +100,7 @@ typedef struct {
 
 /* Read-only device views of the encoded arrays, for inspection and parity
    checks.  Each stream is u64 words, zero padded to an even count, followed by
-   two zero guard words; `words_*` counts all of them. */
+   four zero guard words; `words_*` counts all of them. */
 typedef struct {
     const uint64_t *A;         uint64_t words_A;
     const uint64_t *O;         uint64_t words_O;         /* packed offsets or CSR row_ptr */

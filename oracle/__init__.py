@@ -48,7 +48,7 @@ def build(force: bool = False) -> str:
     """Compile ``liblgoracle.so`` next to its source (plain C, -O2, no SIMD flags)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-Wall", "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-Wall", "-o", tmp, _SRC])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -76,6 +76,14 @@ def _lib():
             h.orc_bfs.restype = _i32
             h.orc_pagerank.argtypes = [_u64, _p(_u64), _p(_u32), _dbl, _u32, _i64, _p(_dbl)]
             h.orc_pagerank.restype = _i32
+            h.orc_pagerank_threads.argtypes = [_u64, _p(_u64), _p(_u32), _dbl, _u32, _i64, _p(_dbl), _i32]
+            h.orc_pagerank_threads.restype = _i32
+            h.orc_ef_words.argtypes = [_u64, _u64, _u32, _p(_u64), _p(_u64), _p(_u64), _p(_u32)]
+            h.orc_ef_words.restype = None
+            h.orc_ef_build.argtypes = [_u64, _p(_u64), _u32, _p(_u64), _p(_u64), _p(_u64)]
+            h.orc_ef_build.restype = _i32
+            h.orc_global_words.argtypes = [_u64, _p(_u32), _p(_u32), _u32, _u32, _u64, _u64, _p(_u64)]
+            h.orc_global_words.restype = _i32
             _handle = h
     return _handle
 
@@ -192,12 +200,44 @@ def bfs(n, row_ptr, col, src: int) -> np.ndarray:
     return out
 
 
-def pagerank(n, row_ptr, col, damping: float = 0.85, iters: int = 20, personalize: int = -1) -> np.ndarray:
-    """FP64 pull PageRank on the input CSR, exactly ``iters`` iterations."""
+def pagerank(n, row_ptr, col, damping: float = 0.85, iters: int = 20, personalize: int = -1,
+             threads: int = 1) -> np.ndarray:
+    """FP64 pull PageRank on the input CSR, exactly ``iters`` iterations
+    (``threads`` > 1 splits vertices over OpenMP threads; same result)."""
     rp = np.ascontiguousarray(row_ptr, dtype=np.uint64)
     cl = np.ascontiguousarray(col, dtype=np.uint32)
     out = np.zeros(n, dtype=np.float64)
-    rc = _lib().orc_pagerank(n, _ptr(rp, _u64), _ptr(cl, _u32), damping, iters, personalize, _ptr(out, _dbl))
+    rc = _lib().orc_pagerank_threads(n, _ptr(rp, _u64), _ptr(cl, _u32), damping, iters, personalize,
+                                     _ptr(out, _dbl), threads)
     if rc != 0:
         raise OracleError(rc, "orc_pagerank")
     return out
+
+
+def ef_build(x, sample: int = 512):
+    """Elias-Fano arrays (low, high, samples, l) of the offsets x_0..x_{N-1},
+    laid out as :func:`encode` lays them out (Section 4.3)."""
+    xv = np.ascontiguousarray(x, dtype=np.uint64)
+    N = xv.shape[0]
+    lw, hw, sw, l = _u64(), _u64(), _u64(), _u32()
+    _lib().orc_ef_words(N, int(xv[-1]), sample, ctypes.byref(lw), ctypes.byref(hw), ctypes.byref(sw),
+                        ctypes.byref(l))
+    low = np.zeros(lw.value, dtype=np.uint64)
+    high = np.zeros(hw.value, dtype=np.uint64)
+    smp = np.zeros(sw.value, dtype=np.uint64)
+    rc = _lib().orc_ef_build(N, _ptr(xv, _u64), sample, _ptr(low, _u64), _ptr(high, _u64), _ptr(smp, _u64))
+    if rc != 0:
+        raise OracleError(rc, "orc_ef_build")
+    return low, high, smp, int(l.value)
+
+
+def global_words(col, weights, s: int, omega: int, w0: int, w1: int) -> np.ndarray:
+    """Words [w0, w1) of the global-ID A stream of (col, weights) at s + omega
+    bits per record (Sections 3.2.1 and 3.3)."""
+    cl = np.ascontiguousarray(col, dtype=np.uint32)
+    wt = None if weights is None else np.ascontiguousarray(weights, dtype=np.uint32)
+    out = np.zeros(max(w1 - w0, 1), dtype=np.uint64)
+    rc = _lib().orc_global_words(cl.shape[0], _ptr(cl, _u32), _ptr(wt, _u32), s, omega, w0, w1, _ptr(out, _u64))
+    if rc != 0:
+        raise OracleError(rc, "orc_global_words")
+    return out[:w1 - w0]

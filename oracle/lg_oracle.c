@@ -42,7 +42,7 @@
  *   N + (U >> l) + 1 bits with bit (x_i >> l) + i set, select samples
  *   S[k] = position of one number k*sample; DM orders by (degree desc, ID asc).
  *   Every stream is u64 words, zero padded to an even word count, followed by
- *   two zero guard words.
+ *   four zero guard words.
  *
  * Parity unpinned: none -- every function below is pinned by the test suite
  * (closed forms, hand-derived bitstreams, round trips, brute force, linear
@@ -99,11 +99,11 @@ static uint64_t get(const uint64_t *stream, uint64_t p, uint32_t w) {
     return v;
 }
 
-/* data words for `bits` bits, padded to an even count, plus two guard words */
+/* data words for `bits` bits, padded to an even count, plus four zero guard words */
 static uint64_t padded_words(uint64_t bits) {
     uint64_t w = (bits + 63) / 64;
     w += (w & 1);
-    return w + 2;
+    return w + 4;
 }
 
 static uint64_t *zalloc_words(uint64_t words) {
@@ -339,6 +339,57 @@ inval:
 }
 
 /* ------------------------------------------------------------------ */
+/* pieces of the encoder for graphs too large to encode whole          */
+/* ------------------------------------------------------------------ */
+
+/* The Elias-Fano arrays of x_0..x_{N-1} (Section 4.3), laid out exactly as
+   orc_encode lays them out, into caller buffers of orc_ef_words() words. */
+void orc_ef_words(uint64_t N, uint64_t U, uint32_t sample, uint64_t *low_words, uint64_t *high_words,
+                  uint64_t *sample_words, uint32_t *l_out) {
+    uint64_t q = N ? U / N : 0;
+    uint32_t l = q ? orc_bits(q) - 1 : 0;
+    *l_out = l;
+    *low_words = padded_words(N * (uint64_t)l);
+    *high_words = padded_words(N + (U >> l) + 1);
+    *sample_words = padded_words(64 * ((N + sample - 1) / sample));
+}
+
+int orc_ef_build(uint64_t N, const uint64_t *x, uint32_t sample, uint64_t *low, uint64_t *high, uint64_t *samples) {
+    if (N == 0 || sample == 0) return ORC_EINVAL;
+    uint64_t U = x[N - 1], lw, hw, sw;
+    uint32_t l;
+    orc_ef_words(N, U, sample, &lw, &hw, &sw, &l);
+    memset(low, 0, lw * 8); memset(high, 0, hw * 8); memset(samples, 0, sw * 8);
+    uint64_t lowmask = l ? ((1ULL << l) - 1) : 0;
+    for (uint64_t i = 0; i < N; i++) {
+        if (l) put(low, i * l, l, x[i] & lowmask);
+        put(high, (x[i] >> l) + i, 1, 1);
+    }
+    for (uint64_t k = 0; k * sample < N; k++) samples[k] = (x[k * sample] >> l) + k * sample;
+    return ORC_OK;
+}
+
+/* Words [w0, w1) of the global-ID A stream (Sections 3.2.1 and 3.3): record j
+   = [col_j : s][w_j : omega] at bit j (s + omega), one bit at a time. */
+int orc_global_words(uint64_t arcs, const uint32_t *col, const uint32_t *w, uint32_t s, uint32_t omega,
+                     uint64_t w0, uint64_t w1, uint64_t *out) {
+    uint32_t r = s + omega;
+    if (r == 0 || w1 < w0) return ORC_EINVAL;
+    memset(out, 0, (w1 - w0) * 8);
+    uint64_t b0 = w0 * 64, b1 = w1 * 64;
+    uint64_t j0 = b0 / r, j1 = (b1 + r - 1) / r;
+    if (j1 > arcs) j1 = arcs;
+    for (uint64_t j = j0; j < j1; j++) {
+        uint64_t rec = (uint64_t)col[j] | (w ? (uint64_t)w[j] << s : 0);
+        for (uint32_t k = 0; k < r; k++) {
+            uint64_t p = j * r + k;
+            if (p >= b0 && p < b1 && ((rec >> k) & 1ULL)) out[(p - b0) / 64] |= 1ULL << ((p - b0) % 64);
+        }
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
 /* decoder                                                             */
 /* ------------------------------------------------------------------ */
 
@@ -488,8 +539,17 @@ int orc_bfs(uint64_t n, const uint64_t *rp, const uint32_t *col, uint32_t src, u
      global:        r_0 = 1/n,    r_t[v] = (1-d)/n     + d * sum_{u in N_v} r_{t-1}[u] / d_u
      personalized:  r_0 = e_src,  r_t[v] = (1-d)[v=src] + d * sum_{u in N_v} r_{t-1}[u] / d_u
    Vertices of degree 0 contribute nothing (no dangling redistribution). */
+int orc_pagerank_threads(uint64_t n, const uint64_t *rp, const uint32_t *col, double damping, uint32_t iters,
+                         int64_t personalize, double *rank, int threads);
 int orc_pagerank(uint64_t n, const uint64_t *rp, const uint32_t *col, double damping, uint32_t iters,
                  int64_t personalize, double *rank) {
+    return orc_pagerank_threads(n, rp, col, damping, iters, personalize, rank, 1);
+}
+
+/* Same arithmetic; vertices split over `threads` OpenMP threads when built with
+   OpenMP (each vertex's sum keeps its order, so results do not change). */
+int orc_pagerank_threads(uint64_t n, const uint64_t *rp, const uint32_t *col, double damping, uint32_t iters,
+                         int64_t personalize, double *rank, int threads) {
     if (n == 0 || (personalize >= 0 && (uint64_t)personalize >= n)) return ORC_EINVAL;
     double *prev = (double *)malloc(sizeof(double) * n);
     if (!prev) return ORC_ENOMEM;
@@ -497,6 +557,8 @@ int orc_pagerank(uint64_t n, const uint64_t *rp, const uint32_t *col, double dam
         rank[v] = personalize < 0 ? 1.0 / (double)n : (v == (uint64_t)personalize ? 1.0 : 0.0);
     for (uint32_t t = 0; t < iters; t++) {
         memcpy(prev, rank, sizeof(double) * n);
+        (void)threads;
+#pragma omp parallel for schedule(dynamic, 4096) num_threads(threads > 0 ? threads : 1)
         for (uint64_t v = 0; v < n; v++) {
             double sum = 0.0;
             for (uint64_t j = rp[v]; j < rp[v + 1]; j++) {

@@ -7,8 +7,9 @@
 // 32-bit words and use one funnel shift per field.
 //
 // Every stream allocation is padded to an even number of u64 words and
-// followed by two zero guard words, so any read of word i+1, or of the aligned
-// 32-byte sector holding word i, for a data word i stays inside the allocation.
+// followed by four zero guard words (32 bytes), so a read of the word after a
+// data word, or of the aligned 32-byte sector holding it, stays inside the
+// allocation.
 #pragma once
 
 #include <cstdint>
@@ -130,10 +131,15 @@ __device__ __forceinline__ uint4 ldg128_stream(const uint32_t* p, uint64_t pol) 
       : "l"(p), "l"(pol));
   return v;
 }
-// Gathers of per-vertex arrays use the default read-only path: on this GPU a
-// no-allocate L1 hint made 392M random 4-byte gathers 3.5x slower (measured),
-// so L1 allocation is kept for them.
-__device__ __forceinline__ float ldg_gather(const float* p, uint64_t) { return __ldg(p); }
+// Gathers of per-vertex arrays keep the default L1 allocation (on this GPU a
+// no-allocate L1 hint made 392M random 4-byte gathers 3.5x slower, measured)
+// and mark their L2 lines evict-last, so the stream and the freshly written
+// next-iteration array are evicted before them.
+__device__ __forceinline__ float ldg_gather(const float* p, uint64_t pol) {
+  float v;
+  asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+  return v;
+}
 __device__ __forceinline__ uint16_t ldg_gather(const uint16_t* p, uint64_t) { return __ldg(p); }
 __device__ __forceinline__ uint32_t ldg_gather(const uint32_t* p, uint64_t) { return __ldg(p); }
 __device__ __forceinline__ uint64_t ldg_gather(const uint64_t* p, uint64_t) {
@@ -141,18 +147,21 @@ __device__ __forceinline__ uint64_t ldg_gather(const uint64_t* p, uint64_t) {
 }
 
 // ---------------------------------------------------------------------------
-// Sequential bit reader: one thread walks a run of fields.  The stream is
-// fetched in whole 32-byte sectors (two 128-bit loads of one aligned sector)
-// into eight register words, and moved into a 64-bit bit buffer 32 bits at a
-// time, so a warp whose lanes walk different runs issues one sector request
-// per lane per 256 bits consumed.
+// Sequential bit reader: one thread walks a run of fields (w <= 32 bits).  The
+// window lo:hi holds the 64 stream bits starting at word `wnext - 2`; a field
+// at bit offset o (< 32) of lo is one funnel shift and a mask, and advancing
+// past lo shifts the window by one word.  Words come from whole 32-byte
+// sectors (two 128-bit loads of one aligned sector) held in registers, so a
+// warp whose lanes walk different runs issues one sector request per lane per
+// 256 bits.  The window runs one word ahead of the last field read, which the
+// 32-byte zero guard after every stream keeps inside the allocation.
 // ---------------------------------------------------------------------------
 struct BitReader {
   const uint32_t* A;
   uint64_t pol;       // L2 policy of the stream loads
-  uint64_t wnext;     // index of the next 32-bit word to append to buf
-  uint64_t buf;       // unread bits, LSB first
-  uint32_t nb;        // number of valid bits in buf
+  uint64_t wnext;     // index of the next word to enter the window
+  uint32_t lo, hi;    // the window
+  uint32_t o;         // bit offset of the next field in lo, 0..31
   uint4 q0, q1;       // next words of the current sector, q0 first (shifted down)
   uint32_t n0, n1;    // valid words in q0, q1
 
@@ -169,33 +178,35 @@ struct BitReader {
     q1 = b;
     n0 = 4u - skip;
   }
-  __device__ __forceinline__ void push_word() {
+  __device__ __forceinline__ uint32_t next_word() {
     if (n0 == 0) {
       if (n1) { q0 = q1; n0 = n1; n1 = 0; }
       else load_sector();
     }
-    buf |= (uint64_t)q0.x << nb;
-    nb += 32;
+    const uint32_t x = q0.x;
     q0.x = q0.y; q0.y = q0.z; q0.z = q0.w;
     n0--;
     wnext++;
+    return x;
   }
   __device__ __forceinline__ void init(const uint32_t* base, uint64_t bit, uint64_t policy) {
     A = base;
     pol = policy;
     wnext = bit >> 5;
-    buf = 0; nb = 0; n0 = 0; n1 = 0;
-    push_word();
-    const uint32_t sh = (uint32_t)bit & 31u;
-    buf >>= sh;
-    nb -= sh;
+    n0 = 0; n1 = 0;
+    lo = next_word();
+    hi = next_word();
+    o = (uint32_t)bit & 31u;
   }
   // w <= 32
   __device__ __forceinline__ uint32_t get(uint32_t w) {
-    if (nb < w) push_word();
-    const uint32_t v = (uint32_t)buf & mask_lo(w);
-    buf >>= w;
-    nb -= w;
+    const uint32_t v = __funnelshift_r(lo, hi, o) & mask_lo(w);
+    o += w;
+    if (o >= 32) {
+      o -= 32;
+      lo = hi;
+      hi = next_word();
+    }
     return v;
   }
   __device__ __forceinline__ void skip(uint32_t w) { (void)get(w); }
@@ -251,5 +262,34 @@ __device__ __forceinline__ T block_excl_scan(T v, T& total, T* tmp) {
 }
 
 __device__ __forceinline__ void set_err(int* err, int bit) { atomicOr(err, bit); }
+
+// ---------------------------------------------------------------------------
+// Warp-flattened walk over the entries of 32 consecutive rows: lane r holds
+// row r's entry count; lane l then visits flattened entries l, l + 32, ...
+// (entry f of row r with pre[r] <= f < pre[r+1]), so every lane is busy
+// whatever the row lengths and the loads of different rows overlap.
+// `pre` is 33 words of per-warp shared memory.
+// ---------------------------------------------------------------------------
+template <class Body>
+__device__ __forceinline__ void warp_flat(uint64_t* pre, uint64_t my_count, Body body) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t incl = warp_incl_scan<uint64_t>(my_count);
+  pre[lane + 1] = incl;
+  if (lane == 0) pre[0] = 0;
+  __syncwarp();
+  const uint64_t total = __shfl_sync(LG_FULL_MASK, incl, 31);
+#pragma unroll 2
+  for (uint64_t base = 0; base < total; base += 32) {
+    const uint64_t f = base + lane;
+    if (f < total) {
+      int r = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1)
+        if (pre[r + step] <= f) r += step;
+      body(r, f - pre[r]);
+    }
+  }
+  __syncwarp();
+}
 
 }  // namespace lg

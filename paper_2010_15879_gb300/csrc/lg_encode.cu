@@ -109,39 +109,38 @@ cudaError_t scan_excl_u32(const uint32_t* in, uint64_t n, uint64_t* out, uint64_
 // validation (one warp per row; never reads outside the given arrays)
 // =========================================================================
 // One warp takes 32 consecutive rows: lane l loads row l's bounds, then the
-// warp walks the rows with lanes over the entries.
+// warp walks all their entries flattened (every lane busy).
 __global__ void __launch_bounds__(256) k_validate(const uint64_t* __restrict__ rp, const uint32_t* __restrict__ col,
                                                   const uint32_t* __restrict__ w, uint64_t n, uint64_t arcs,
                                                   uint32_t wbits, int* err, unsigned long long* max_deg,
                                                   uint32_t* max_w) {
-  const int lane = threadIdx.x & 31;
+  __shared__ uint64_t pre_s[8][33];
+  __shared__ uint64_t lo_s[8][32];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
   uint32_t wmax = 0, dmax = 0;
   int flags = 0;
-  for (uint64_t v0 = ((uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; v0 < n; v0 += warps * 32) {
+  for (uint64_t v0 = ((uint64_t)blockIdx.x * (blockDim.x >> 5) + wp) * 32; v0 < n; v0 += warps * 32) {
     const uint64_t mv = v0 + lane;
     uint64_t mlo = 0, mhi = 0;
     if (mv < n) { mlo = rp[mv]; mhi = rp[mv + 1]; }
     const bool mbad = mv < n && (mhi < mlo || mhi > arcs || (mv == 0 && mlo != 0) || (mv == n - 1 && mhi != arcs) ||
                                  mhi - mlo > n);
     if (mbad) flags |= DERR_ROWPTR;
-    if (mv < n && !mbad) dmax = max(dmax, (uint32_t)(mhi - mlo));
-    const uint32_t badmask = __ballot_sync(LG_FULL_MASK, mbad);
-    const int rows = (int)min((uint64_t)32, n - v0);
-    for (int r = 0; r < rows; r++) {
-      const uint64_t lo = __shfl_sync(LG_FULL_MASK, mlo, r), hi = __shfl_sync(LG_FULL_MASK, mhi, r);
-      if (badmask >> r & 1u) continue;
-      for (uint64_t j = lo + lane; j < hi; j += 32) {
-        const uint32_t c = col[j];
-        if (c >= n) flags |= DERR_COL_RANGE;
-        if (j > lo && col[j - 1] >= c) flags |= DERR_UNSORTED;
-        if (w) {
-          const uint32_t x = w[j];
-          wmax = max(wmax, x);
-          if (wbits && wbits < 32 && (x >> wbits)) flags |= DERR_WEIGHT;
-        }
+    const uint64_t cnt = (mv < n && !mbad) ? mhi - mlo : 0;
+    dmax = max(dmax, (uint32_t)cnt);
+    lo_s[wp][lane] = mlo;
+    warp_flat(pre_s[wp], cnt, [&](int r, uint64_t k) {
+      const uint64_t j = lo_s[wp][r] + k;
+      const uint32_t c = col[j];
+      if (c >= n) flags |= DERR_COL_RANGE;
+      if (k > 0 && col[j - 1] >= c) flags |= DERR_UNSORTED;
+      if (w) {
+        const uint32_t x = w[j];
+        wmax = max(wmax, x);
+        if (wbits && wbits < 32 && (x >> wbits)) flags |= DERR_WEIGHT;
       }
-    }
+    });
   }
   flags = __reduce_or_sync(LG_FULL_MASK, flags);
   wmax = __reduce_max_sync(LG_FULL_MASK, wmax);
@@ -191,6 +190,8 @@ cudaError_t enc_check_symmetric(const uint64_t* rp, const uint32_t* col, uint64_
 // local widths: w_v = max(1, bits(maxN_v)) (Section 3.2.2) or
 // g_v = max(1, bits(max gap)) (Section 3.6); len_v = bits of the neighborhood
 // =========================================================================
+// one warp takes 32 consecutive rows (bounds loaded one per lane), then the
+// largest difference of each row is reduced over the warp row by row
 __global__ void __launch_bounds__(256) k_local_lengths(const uint64_t* __restrict__ rp,
                                                        const uint32_t* __restrict__ col, uint64_t n, int gap,
                                                        uint32_t s, uint32_t H, uint8_t* __restrict__ wid,
@@ -342,25 +343,46 @@ __global__ void __launch_bounds__(256) k_pack_local(const uint64_t* __restrict__
   // the owner of the next window's first bit
   const uint64_t vb = first[blockIdx.x];
   const uint64_t ve = (blockIdx.x + 1 < gridDim.x) ? (uint64_t)first[blockIdx.x + 1] + 1 : n;
-  const int lane = threadIdx.x & 31, wid_ = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (uint64_t v = vb + wid_; v < ve && v < n; v += nw) {
-    const uint64_t lo = rp[v], d = rp[v + 1] - lo;
-    const uint32_t wv = wid[v];
-    const uint64_t base = x[v];
-    if (lane == 0) {
+  // warps take 32 vertices at a time: lane r owns vertex vb + 32 t + r (header,
+  // first ID, field range inside the window), then the warp packs the fields of
+  // all 32 flattened
+  __shared__ uint64_t pre_s[8][33];
+  __shared__ uint64_t fs_s[8][32], src_s[8][32];
+  __shared__ uint32_t w_s[8][32];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const uint64_t vend = ve < n ? ve : n;
+  for (uint64_t v0 = vb + 32 * (uint64_t)wp; v0 < vend; v0 += 32 * (uint64_t)nw) {
+    const uint64_t v = v0 + lane;
+    uint64_t cnt = 0, fs = 0, src = 0;
+    uint32_t wv = 0;
+    if (v < vend) {
+      const uint64_t lo = rp[v], d = rp[v + 1] - lo;
+      wv = wid[v];
+      const uint64_t base = x[v];
       put_clip(win, v0w, v0c, base, H, wv);
       if (gap && d >= 1) put_clip(win, v0w, v0c, base + H, s, col[lo]);
+      // fields k = 0.. of width wv starting at fs: IDs (local) or differences (gap)
+      fs = base + H + (gap ? s : 0);
+      const uint64_t nf = gap ? (d >= 1 ? d - 1 : 0) : d;
+      if (nf && wv) {
+        const uint64_t klo = b0 > fs ? (b0 - fs) / wv : 0;
+        const uint64_t khi = min(nf, b1 > fs ? (b1 - fs + wv - 1) / wv : 0);
+        if (khi > klo) {
+          cnt = khi - klo;
+          fs += klo * wv;       // bit of the first field inside the window
+          src = lo + klo;       // col index of that field (gap: its left neighbor)
+        }
+      }
     }
-    // fields k = 0.. of width wv starting at fs: IDs (local) or differences (gap)
-    const uint64_t fs = base + H + (gap ? s : 0);
-    const uint64_t nf = gap ? (d >= 1 ? d - 1 : 0) : d;
-    if (nf == 0 || wv == 0) continue;
-    const uint64_t klo = b0 > fs ? (b0 - fs) / wv : 0;
-    const uint64_t khi = min(nf, b1 > fs ? (b1 - fs + wv - 1) / wv : 0);
-    for (uint64_t k = klo + lane; k < khi; k += 32) {
-      const uint32_t val = gap ? col[lo + k + 1] - col[lo + k] : col[lo + k];
-      put_clip(win, v0w, v0c, fs + k * wv, wv, val);
-    }
+    fs_s[wp][lane] = fs;
+    src_s[wp][lane] = src;
+    w_s[wp][lane] = wv;
+    warp_flat(pre_s[wp], cnt, [&](int r, uint64_t k) {
+      const uint64_t j = src_s[wp][r] + k;
+      const uint32_t wr = w_s[wp][r];
+      const uint32_t val = gap ? col[j + 1] - col[j] : col[j];
+      put_clip(win, v0w, v0c, fs_s[wp][r] + k * wr, wr, val);
+    });
   }
   __syncthreads();
   for (uint64_t i = threadIdx.x; i < wcnt; i += blockDim.x)

@@ -31,11 +31,12 @@ struct lg_graph {
 
 namespace lg {
 
-// u64 words for `bits` payload bits: padded to an even count plus two guard words.
+// u64 words for `bits` payload bits: padded to an even count plus four zero
+// guard words (32 bytes).
 inline uint64_t padded_words(uint64_t bits) {
   uint64_t w = (bits + 63) / 64;
   w += (w & 1);
-  return w + 2;
+  return w + 4;
 }
 inline uint32_t host_bits(uint64_t x) {
   uint32_t b = 0;
@@ -73,8 +74,9 @@ cudaError_t radix_sort_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, u
 cudaError_t radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
                            uint64_t n, uint32_t key_bits, void* tmp, cudaStream_t st);
 // Sort each row [off[i], off[i+1]) of keys ascending, moving vals (nullable) along.
+// Rows of <= 32 keys are skipped when `small_done` (their producer sorted them).
 cudaError_t segmented_sort(uint32_t* keys, uint32_t* vals, const uint64_t* off, uint64_t rows,
-                           uint64_t total, uint64_t max_row, cudaStream_t st);
+                           uint64_t total, uint64_t max_row, cudaStream_t st, bool small_done = false);
 
 // ------------------------------------------------------------------ encoder
 cudaError_t enc_validate(const uint64_t* rp, const uint32_t* col, const uint32_t* w, uint64_t n,

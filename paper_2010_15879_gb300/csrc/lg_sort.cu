@@ -321,13 +321,15 @@ static cudaError_t seg_sort_big(uint32_t* keys, uint32_t* vals, const uint64_t* 
 }
 
 cudaError_t segmented_sort(uint32_t* keys, uint32_t* vals, const uint64_t* off, uint64_t rows, uint64_t total,
-                           uint64_t max_row, cudaStream_t st) {
+                           uint64_t max_row, cudaStream_t st, bool small_done) {
   if (rows == 0 || total == 0 || max_row <= 1) return cudaSuccess;
   cudaError_t e;
-  if (vals) k_seg_small<true><<<grid_for(rows, 256, 152 * 16), 256, 0, st>>>(keys, vals, off, rows);
-  else k_seg_small<false><<<grid_for(rows, 256, 152 * 16), 256, 0, st>>>(keys, vals, off, rows);
-  count_launch();
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (!small_done) {
+    if (vals) k_seg_small<true><<<grid_for(rows, 256, 152 * 16), 256, 0, st>>>(keys, vals, off, rows);
+    else k_seg_small<false><<<grid_for(rows, 256, 152 * 16), 256, 0, st>>>(keys, vals, off, rows);
+    count_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   if (max_row <= SEG_SMALL) return cudaSuccess;
   // rows by power-of-two size class
   uint32_t* meta = nullptr;  // cnt[10], base[10], cursor[10]
@@ -384,31 +386,20 @@ __global__ void k_dm_perm(const uint32_t* __restrict__ inv, uint64_t n, uint32_t
     newdeg[i] = (uint32_t)(rp[v + 1] - rp[v]);
   }
 }
-// One warp takes 32 consecutive new rows: lane l loads row l's source and
-// destination bounds, then the warp copies the rows, mapping IDs through perm.
+// one warp per new row: copy the old row mapped through perm (rows are sorted
+// afterwards; one row per warp keeps the most independent rows in flight)
 __global__ void __launch_bounds__(256) k_dm_scatter(const uint64_t* __restrict__ rp, const uint32_t* __restrict__ col,
                                                     const uint32_t* __restrict__ w, const uint32_t* __restrict__ inv,
                                                     const uint32_t* __restrict__ perm, const uint64_t* __restrict__ nrp,
                                                     uint32_t* __restrict__ ncol, uint32_t* __restrict__ nw, uint64_t n) {
   const int lane = threadIdx.x & 31;
   const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-  for (uint64_t i0 = ((uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; i0 < n; i0 += warps * 32) {
-    const uint64_t mi = i0 + lane;
-    uint64_t mlo = 0, md = 0, mo = 0;
-    if (mi < n) {
-      const uint32_t v = inv[mi];
-      mlo = rp[v];
-      md = rp[v + 1] - mlo;
-      mo = nrp[mi];
-    }
-    const int rows = (int)min((uint64_t)32, n - i0);
-    for (int r = 0; r < rows; r++) {
-      const uint64_t lo = __shfl_sync(LG_FULL_MASK, mlo, r), d = __shfl_sync(LG_FULL_MASK, md, r);
-      const uint64_t o = __shfl_sync(LG_FULL_MASK, mo, r);
-      for (uint64_t k = lane; k < d; k += 32) {
-        ncol[o + k] = perm[col[lo + k]];
-        if (w) nw[o + k] = w[lo + k];
-      }
+  for (uint64_t i = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+    const uint32_t v = inv[i];
+    const uint64_t lo = rp[v], d = rp[v + 1] - lo, o = nrp[i];
+    for (uint64_t k = lane; k < d; k += 32) {
+      ncol[o + k] = perm[col[lo + k]];
+      if (w) nw[o + k] = w[lo + k];
     }
   }
 }
@@ -437,7 +428,7 @@ cudaError_t enc_dm_relabel(const uint64_t* rp, const uint32_t* col, const uint32
     e = scan_excl_u32(newdeg, n, nrp, stmp, st);
   }
   if (e == cudaSuccess) {
-    k_dm_scatter<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(rp, col, w, inv_perm, perm, nrp, ncol, nw, n);
+    k_dm_scatter<<<grid_for(n, 8, 152 * 64), 256, 0, st>>>(rp, col, w, inv_perm, perm, nrp, ncol, nw, n);
     count_launch();
     e = cudaGetLastError();
   }

@@ -371,8 +371,8 @@ __global__ void __launch_bounds__(TNT) k_pr_init(GView g, PrArgs a) {
 __device__ __forceinline__ void pr_finish(const GView& g, const PrArgs& a, uint64_t v, uint32_t d, float sum) {
   const float base = a.personal < 0 ? a.base_all : ((int64_t)v == a.personal ? a.base_all : 0.0f);
   const float r = base + a.damp * sum;
-  a.contrib_out[v] = d ? r / (float)d : 0.0f;
-  if (a.last) a.ranks_out[g.inv_perm ? (uint64_t)g.inv_perm[v] : v] = r;
+  __stcs(a.contrib_out + v, d ? r / (float)d : 0.0f);  // streamed: read again only next iteration
+  if (a.last) __stcs(a.ranks_out + (g.inv_perm ? (uint64_t)g.inv_perm[v] : v), r);
 }
 
 // One launch = one iteration.  Blocks [0, HB) take the heavy schedule (a warp

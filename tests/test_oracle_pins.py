@@ -219,3 +219,24 @@ def test_dm_bijection_monotone_isomorphism():
     for v in range(0, g.n, 5):
         want = sorted(int(perm[u]) for u in g.col[g.row_ptr[v]:g.row_ptr[v + 1]])
         assert list(e.decode_raw(int(perm[v]))) == want
+
+
+# ---------------------------------------------------------------- oracle pieces for large graphs
+def test_ef_build_and_global_words_match_full_encode():
+    g = gen.rmat(11, 8, seed=12, weighted=True)
+    e = oracle.encode(g.n, g.row_ptr, g.col, g.weights, id_mode=oracle.ID_GLOBAL, off_mode=oracle.OFF_EF,
+                      sample=64, weight_bits=9)
+    low, high, smp, l = oracle.ef_build(g.row_ptr, sample=64)
+    assert l == e.ef_l
+    assert np.array_equal(low, e.ef_low) and np.array_equal(high, e.ef_high) and np.array_equal(smp, e.samples)
+    used = (e.bits_A + 63) // 64
+    for w0, w1 in [(0, 5), (3, 70), (used - 9, used), (0, used)]:
+        got = oracle.global_words(g.col, g.weights, e.s, e.omega, w0, w1)
+        assert np.array_equal(got, e.A[w0:w1])
+
+
+def test_pagerank_threads_identical():
+    g = gen.rmat(10, 8, seed=13)
+    a = oracle.pagerank(g.n, g.row_ptr, g.col, 0.85, 7)
+    b = oracle.pagerank(g.n, g.row_ptr, g.col, 0.85, 7, threads=4)
+    assert np.array_equal(a, b)
