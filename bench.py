@@ -15,8 +15,13 @@ step (encode included); the JSON also carries kernel-only BFS / PageRank GTEPS,
 the CSR-32 arm, bytes per arc, the roofline of the PageRank kernel and the CPU
 oracle baseline.
 
+The ``batch`` workload times the batching subsystem instead: 4,096 independent
+R-MAT graphs (scales 8..16, edge factors 4..32), one step = one replay of the
+captured persistent launch that encodes every graph with its own widths, runs
+BFS from each graph's vertex 0 and 10 PageRank iterations.
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lg|reference]
-                       [--workload community|rmat16|rmat27]
+                       [--workload community|rmat16|rmat27|batch]
 Under torchrun (N > 1) every rank runs an independent replica ("replicas only":
 one GPU holds the whole graph, no collective on the data path).
 """
@@ -53,7 +58,13 @@ WORKLOADS = {
                "Elias-Fano offsets",
                None,  # built on the device (gen.rmat_gpu)
                dict(id_mode=0, off_mode=1, relabel=False, weight_bits=8), 16, 20),
+    "batch": ("batch of 4,096 independent R-MAT graphs, (a,b,c)=(.57,.19,.19), scale floor(U[8,17)), edge "
+              "factor uniform in [4,32], seeded; per-graph global IDs at bits(n-1) + packed offsets at "
+              "bits(arcs); encode + BFS from vertex 0 + 10 PageRank iterations in one graph-captured "
+              "persistent launch, autotuned lanes per vertex and team tile",
+              None, None, 1, 10),
 }
+BATCH_COUNT, BATCH_SEED = 4096, 3
 
 
 class Workload:
@@ -115,22 +126,25 @@ def peaks():
     return HBM_FALLBACK_GBS, "fallback"
 
 
-def kernel_source_hash():
+def kernel_source_hash(workload="community"):
+    """Hash of the sources of the kernel the roofline reports (k_pr_pull, or
+    k_batch for the batch workload)."""
+    files = ("lg_batch.cu",) if workload == "batch" else ("lg_traverse.cuh", "lg_device.cuh")
     h = hashlib.sha256()
-    for f in ("lg_traverse.cuh", "lg_device.cuh"):
+    for f in files:
         h.update(open(os.path.join(ROOT, "paper_2010_15879_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def ncu_traffic(workload):
-    """DRAM bytes per launch of the PageRank kernel from the committed ncu
+    """DRAM bytes per launch of the reported kernel from the committed ncu
     summary, only if it was taken on the current kernel source."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
     e = d.get(workload)
-    if not e or e.get("source_sha") != kernel_source_hash():
+    if not e or e.get("source_sha") != kernel_source_hash(workload):
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -373,6 +387,171 @@ def run_lg(args, rank, world):
     return out, rank
 
 
+# ------------------------------------------------------------------- batches
+def batch_alg_bytes(V, arcs, bits_total, iters):
+    """Algorithmic bytes of one batch run: encode reads the CSR and writes the
+    streams; BFS decodes every reached neighborhood once, gathers a 4 B depth
+    per arc and initialises / queues 4 B per vertex; PageRank reads the
+    streams, gathers a 4 B contribution per arc and writes 4 B per vertex per
+    iteration, plus the initial contributions and the final ranks."""
+    b = bits_total // 8
+    encode = 8 * (V + 1) + 4 * arcs + b
+    bfs = b + 4 * arcs + 12 * V
+    pr = 4 * V + iters * (b + 4 * arcs + 4 * V) + 4 * V
+    return encode + bfs + pr
+
+
+def batch_teps(rp_d, depths):
+    """Graph500 traversed edges of the per-graph BFS runs (each graph from its vertex 0)."""
+    deg = rp_d[1:] - rp_d[:-1]
+    return int(deg[depths != -1].sum().item()) // 2
+
+
+def run_batch(args, rank, world):
+    import torch
+
+    import paper_2010_15879_gb300 as lg
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    lg.load(auto_build=True)
+    desc, _, _, _, T = WORKLOADS["batch"]
+    t0 = time.time()
+    db = gen.rmat_batch_gpu(count=BATCH_COUNT, seed=BATCH_SEED)
+    V, arcs = db.row_ptr.numel() - 1, db.col.numel()
+    log(f"generated batch of {BATCH_COUNT}: V={V} arcs={arcs} in {time.time() - t0:.1f}s")
+    t0 = time.time()
+    b = lg.lg_batch_create(db.vptr, db.row_ptr, db.col, autotune=True)
+    info = b.info()
+    log(f"created (autotuned) in {time.time() - t0:.1f}s: tile {info['tile_arcs']}, teams {info['teams']} "
+        f"(max {info['max_team']}), lanes {info['graphs_by_lanes']}, grid {info['grid']}x{info['threads']}")
+    stream = torch.cuda.current_stream(dev)
+    depths = torch.empty(V, dtype=torch.int32, device=dev)
+    ranks = torch.empty(V, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    lg.lg_batch_run(b, 0.85, T, depths, ranks)
+    lg.lg_batch_status(b)
+    te_bfs = batch_teps(db.row_ptr, depths)
+    te_step = te_bfs + arcs * T
+    for _ in range(args.warmup):
+        lg.lg_batch_run(b, 0.85, T, depths, ranks)
+    torch.cuda.synchronize(dev)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize(dev)
+    l0 = lg.lg_kernel_launches()
+    with ClockSampler(dev.index) as clk:
+        for e in evs:
+            e[0].record(stream)
+            lg.lg_batch_run(b, 0.85, T, depths, ranks)
+            e[1].record(stream)
+        torch.cuda.synchronize(dev)
+    barrier()
+    launches = lg.lg_kernel_launches() - l0
+    lg.lg_batch_status(b)
+    per = [e[0].elapsed_time(e[1]) for e in evs]
+    step_ms = float(np.sum(per)) / args.steps
+    log(f"[rank {rank}] batch: step {step_ms:.2f} ms (min {min(per):.2f}, max {max(per):.2f})")
+
+    # e2e: the CSR from pinned host memory into the batch's input buffers, the run, results back
+    rp_p = db.row_ptr.cpu().pin_memory()
+    col_p = db.col.cpu().pin_memory()
+    dep_p = torch.empty(V, dtype=torch.int32).pin_memory()
+    rk_p = torch.empty(V, dtype=torch.float32).pin_memory()
+
+    def e2e_step():
+        db.row_ptr.copy_(rp_p, non_blocking=True)
+        db.col.copy_(col_p, non_blocking=True)
+        lg.lg_batch_run(b, 0.85, T, depths, ranks)
+        dep_p.copy_(depths, non_blocking=True)
+        rk_p.copy_(ranks, non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    lg.lg_batch_status(b)
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    h2d = (V + 1) * 8 + arcs * 4
+    d2h = V * 8
+
+    alg = batch_alg_bytes(V, arcs, info["bits_total"], T)
+    peak, peak_kind = peaks()
+    achieved = alg / (step_ms * 1e-3) / 1e9
+    out = {
+        "metric": "GTEPS (batch: per-graph BFS from vertex 0 + 10 PageRank iterations, Log(Graph) encode "
+                  "included, one graph launch)",
+        "value": None, "unit": "GTEPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32 ids / fp32 ranks", "data": "synthetic (seeded generator; no dataset)",
+        "config": {"workload": desc, "graphs": BATCH_COUNT, "V": V, "arcs": arcs, "pr_iters": T,
+                   "damping": 0.85, "l2": "inputs larger than L2 (CSR %.2f GB)" % ((V + 1) * 8 / 1e9 + arcs * 4 / 1e9),
+                   "parallelism": f"replicas x{world}"},
+    }
+    step_ms, e2e_ms, value, e2e_value = combine_replicas(step_ms, e2e_ms, te_step, world, dev)
+    out["ms_per_step"] = step_ms
+    out["value"] = value
+    out["e2e"] = {"value": e2e_value, "unit": "GTEPS", "ms_per_step": e2e_ms,
+                  "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    out["gpu_launches"] = int(launches)
+    out["detail"] = {"bfs_edges": te_bfs, "pr_arcs": arcs * T, "bits_total": info["bits_total"],
+                     "bits_per_arc": info["bits_total"] / arcs, "tile_arcs": info["tile_arcs"],
+                     "teams": info["teams"], "max_team": info["max_team"], "lanes": info["graphs_by_lanes"],
+                     "grid": info["grid"], "threads": info["threads"], "work_items": info["n_items"],
+                     "bytes_vs_csr32": (info["bits_total"] / 8) / (4 * arcs + 8 * (V + 1))}
+    out["roofline"] = {"kernel": "k_batch (persistent: encode + BFS + PageRank, decode fused)", "bound": "hbm",
+                       "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                       "peak_kind": f"{peak_kind} (copy bandwidth)", "algorithmic_bytes_per_launch": alg,
+                       "traffic": ncu_traffic("batch")}
+    out["clocks"] = clk.summary()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        vptr = db.vptr.cpu().numpy().view(np.uint64)
+        out["cpu_baseline"] = cpu_baseline_batch(vptr, rp_p.numpy().view(np.uint64), col_p.numpy().view(np.uint32),
+                                                 T, min_seconds=10.0)
+    b.free()
+    return out, rank
+
+
+def cpu_baseline_batch(vptr, rp, col, iters, min_seconds=10.0, max_graphs=None):
+    """The oracle as it stands (single-threaded C) on a bounded sample of the
+    batch: whole graphs in batch order (BFS from vertex 0 + `iters` PageRank
+    iterations each) until about min_seconds."""
+    import oracle
+
+    te = 0
+    t0 = time.time()
+    k = 0
+    while k < vptr.shape[0] - 1:
+        v0, v1 = int(vptr[k]), int(vptr[k + 1])
+        a0, a1 = int(rp[v0]), int(rp[v1])
+        grp = (rp[v0:v1 + 1] - np.uint64(a0)).astype(np.uint64)
+        gcol = col[a0:a1]
+        d = oracle.bfs(v1 - v0, grp, gcol, 0)
+        te += int(np.diff(grp).astype(np.int64)[d != 0xFFFFFFFF].sum()) // 2
+        oracle.pagerank(v1 - v0, grp, gcol, 0.85, iters)
+        te += (a1 - a0) * iters
+        k += 1
+        el = time.time() - t0
+        if el >= min_seconds or (max_graphs and k >= max_graphs):
+            break
+    el = time.time() - t0
+    return {"value": te / el / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+            "sample": f"the first {k} graph(s) of the batch (BFS from vertex 0 + {iters} PageRank iterations "
+                      f"each), {el:.1f} s"}
+
+
 # ------------------------------------------------------------------ CPU oracle
 def cpu_baseline(n, rp, col, src_h, min_seconds=10.0, max_units=None, bfs_only=False):
     """The oracle as it stands (single-threaded C) on a bounded sample: BFS from
@@ -421,8 +600,47 @@ def profile_pass(args):
         g.free()
 
 
+def profile_batch(args):
+    """Untimed batch runs for profilers: creation (with autotuning), then two
+    replays; pass `-s` to skip the autotuner's launches."""
+    import torch
+
+    import paper_2010_15879_gb300 as lg
+
+    lg.load(auto_build=True)
+    count = args.batch_count or BATCH_COUNT
+    db = gen.rmat_batch_gpu(count=count, seed=BATCH_SEED)
+    b = lg.lg_batch_create(db.vptr, db.row_ptr, db.col, autotune=True)
+    log(f"profile batch: {b.info()['n_items']} work items, {b.info()['launches']} autotune launches")
+    for _ in range(2):
+        lg.lg_batch_run(b, 0.85, args.pr_iters if args.pr_iters is not None else 10)
+    lg.lg_batch_status(b)
+    torch.cuda.synchronize()
+    b.free()
+
+
 def run_reference(args, rank, world):
     import torch
+
+    if args.workload == "batch":
+        desc, _, _, _, T = WORKLOADS["batch"]
+        hb = gen.rmat_batch(count=64, seed=BATCH_SEED)  # the batch's first 64 graphs (seeded per graph)
+        for _ in range(args.warmup):
+            cpu_baseline_batch(hb.vptr, hb.row_ptr, hb.col, T, min_seconds=0.0, max_graphs=1)
+        t0 = time.time()
+        vals = [cpu_baseline_batch(hb.vptr, hb.row_ptr, hb.col, T, min_seconds=2.0)["value"]
+                for _ in range(args.steps)]
+        el = time.time() - t0
+        v = float(np.mean(vals))
+        sample = f"per step: whole graphs from the start of the batch for about 2 s (BFS + {T} PageRank iterations)"
+        return {"impl": "reference", "metric": "GTEPS (batch: per-graph BFS from vertex 0 + 10 PageRank "
+                                               "iterations, Log(Graph) encode included, one graph launch)",
+                "value": v, "unit": "GTEPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64 ranks / u32 depths", "data": "synthetic (seeded generator)",
+                "config": {"workload": desc, "graphs": BATCH_COUNT, "pr_iters": T, "parallelism": "host cores"},
+                "cpu_baseline": {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": sample},
+                "e2e": {"value": v, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}, rank
 
     dev = torch.device("cuda", 0) if (args.workload == "rmat27" and torch.cuda.is_available()) else None
     if args.workload == "rmat27":
@@ -466,6 +684,7 @@ def main():
     ap.add_argument("--profile", choices=["lg", "csr32", "both"], default=None,
                     help="run one untimed pass of the hot path (for ncu) and exit")
     ap.add_argument("--pr-iters", type=int, default=None, help="PageRank iterations in --profile mode")
+    ap.add_argument("--batch-count", type=int, default=None, help="graphs in --profile mode of the batch workload")
     args = ap.parse_args()
     if args.warmup < 3:
         log("warmup raised to 3 (timing rule)")
@@ -479,14 +698,17 @@ def main():
         print(json.dumps(out), flush=True)
         return
     if args.profile:
-        profile_pass(args)
+        if args.workload == "batch":
+            profile_batch(args)
+        else:
+            profile_pass(args)
         return
     if world > 1:
         import torch
         import torch.distributed as dist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         dist.init_process_group("nccl")
-    out, rank = run_lg(args, rank, world)
+    out, rank = (run_batch if args.workload == "batch" else run_lg)(args, rank, world)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

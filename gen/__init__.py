@@ -76,7 +76,10 @@ def _gpu_lib():
             h.lggen_gpu_rmat_count.argtypes = [i32, u64, dbl, dbl, dbl, u64, vp, vp, vp]
             h.lggen_gpu_rmat_scatter.argtypes = [i32, u64, dbl, dbl, dbl, u64, vp, vp, vp, vp]
             h.lggen_gpu_weights.argtypes = [vp, vp, u64, u64, vp, vp]
-            for f in (h.lggen_gpu_rmat_count, h.lggen_gpu_rmat_scatter, h.lggen_gpu_weights):
+            h.lggen_gpu_batch_edges.argtypes = [i32, vp, vp, vp, vp, vp, vp, ctypes.c_uint32, dbl, dbl, dbl, vp,
+                                                vp, vp]
+            for f in (h.lggen_gpu_rmat_count, h.lggen_gpu_rmat_scatter, h.lggen_gpu_weights,
+                      h.lggen_gpu_batch_edges):
                 f.restype = i32
             _gpu_handle = h
     return _gpu_handle
@@ -179,6 +182,39 @@ def rmat(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19, c:
     return _take(out, f"rmat_s{scale}_ef{edge_factor}_seed{seed}")
 
 
+def _sort_dedup_rows(rp, deg, col, n: int, chunk: int):
+    """Sorts every row of a device CSR and drops duplicate arcs, rows taken in
+    chunks of at most ``chunk`` arcs; returns the new (row_ptr, col)."""
+    import torch
+
+    dev = col.device
+    rp_h = rp.cpu().numpy()
+    new_deg = torch.zeros(n, dtype=torch.int64, device=dev)
+    w_pos, r0 = 0, 0
+    while r0 < n:
+        r1 = int(np.searchsorted(rp_h, rp_h[r0] + chunk, side="right")) - 1
+        r1 = min(max(r1, r0 + 1), n)
+        s0, s1 = int(rp_h[r0]), int(rp_h[r1])
+        if s1 > s0:
+            rows = torch.repeat_interleave(torch.arange(r1 - r0, device=dev, dtype=torch.int64), deg[r0:r1])
+            key = (rows << 32) | (col[s0:s1].to(torch.int64) & 0xFFFFFFFF)
+            del rows
+            key = torch.sort(key).values
+            keep = torch.ones_like(key, dtype=torch.bool)
+            keep[1:] = key[1:] != key[:-1]
+            key = key[keep]
+            del keep
+            new_deg[r0:r1] = torch.bincount(key >> 32, minlength=r1 - r0)
+            col[w_pos:w_pos + key.numel()] = (key & 0xFFFFFFFF).to(torch.int32)
+            w_pos += key.numel()
+            del key
+        r0 = r1
+    col = col[:w_pos].clone()
+    rp = torch.zeros(n + 1, dtype=torch.int64, device=dev)
+    torch.cumsum(new_deg, 0, out=rp[1:])
+    return rp, col
+
+
 def rmat_gpu(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19, c: float = 0.19,
              seed: int = 1, weighted: bool = False, permute: bool = True, chunk: int = 1 << 28):
     """The same graph as :func:`rmat`, built on the current CUDA device (for
@@ -209,34 +245,10 @@ def rmat_gpu(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19
     _check(lib.lggen_gpu_rmat_scatter(scale, m, a, a + b, a + b + c, seed, pptr, cursor.data_ptr(),
                                       col.data_ptr(), st), "rmat_scatter")
     del cursor, perm
-    # sort each row and drop duplicate arcs, rows taken in chunks of <= `chunk` arcs
-    rp_h = rp.cpu().numpy()
-    new_deg = torch.zeros(n, dtype=torch.int64, device=dev)
-    w_pos, r0 = 0, 0
-    while r0 < n:
-        r1 = int(np.searchsorted(rp_h, rp_h[r0] + chunk, side="right")) - 1
-        r1 = min(max(r1, r0 + 1), n)
-        s0, s1 = int(rp_h[r0]), int(rp_h[r1])
-        if s1 > s0:
-            rows = torch.repeat_interleave(torch.arange(r1 - r0, device=dev, dtype=torch.int64), deg[r0:r1])
-            key = (rows << 32) | (col[s0:s1].to(torch.int64) & 0xFFFFFFFF)
-            del rows
-            key = torch.sort(key).values
-            keep = torch.ones_like(key, dtype=torch.bool)
-            keep[1:] = key[1:] != key[:-1]
-            key = key[keep]
-            del keep
-            new_deg[r0:r1] = torch.bincount(key >> 32, minlength=r1 - r0)
-            col[w_pos:w_pos + key.numel()] = (key & 0xFFFFFFFF).to(torch.int32)
-            w_pos += key.numel()
-            del key
-        r0 = r1
-    col = col[:w_pos].clone()
-    rp = torch.zeros(n + 1, dtype=torch.int64, device=dev)
-    torch.cumsum(new_deg, 0, out=rp[1:])
+    rp, col = _sort_dedup_rows(rp, deg, col, n, chunk)
     w = None
     if weighted:
-        w = torch.empty(w_pos, dtype=torch.int32, device=dev)
+        w = torch.empty(col.numel(), dtype=torch.int32, device=dev)
         _check(lib.lggen_gpu_weights(rp.data_ptr(), col.data_ptr(), n, seed, w.data_ptr(), st), "weights")
     return rp, col, w
 
@@ -312,9 +324,7 @@ def rmat_batch(count: int = 4096, seed: int = 3, scale_lo: int = 8, scale_hi: in
     seed * 1000003 + g.  Graphs are built in parallel on the host."""
     from concurrent.futures import ThreadPoolExecutor
 
-    span = scale_hi - scale_lo + 1
-    scales = np.array([scale_lo + int((hash4(seed, 7, g, 0) >> 11) * span // (1 << 53)) for g in range(count)])
-    efs = np.array([ef_lo + int(hash4(seed, 7, g, 1) % (ef_hi - ef_lo + 1)) for g in range(count)])
+    scales, efs = _batch_params(count, seed, scale_lo, scale_hi, ef_lo, ef_hi)
     workers = threads or (os.cpu_count() or 4)
 
     def one(g):
@@ -353,3 +363,72 @@ def community_2p24(seed: int = 2, log2n: int = 24) -> Graph:
 def rmat_s27_ef16_weighted(seed: int = 5, scale: int = 27) -> Graph:
     """R-MAT scale 27, edge factor 16, uniform integer weights in [1, 255]."""
     return rmat(scale, 16, seed=seed, weighted=True)
+
+
+def _batch_params(count: int, seed: int, scale_lo: int, scale_hi: int, ef_lo: int, ef_hi: int):
+    span = scale_hi - scale_lo + 1
+    scales = np.array([scale_lo + int((hash4(seed, 7, g, 0) >> 11) * span // (1 << 53)) for g in range(count)])
+    efs = np.array([ef_lo + int(hash4(seed, 7, g, 1) % (ef_hi - ef_lo + 1)) for g in range(count)])
+    return scales, efs
+
+
+@dataclass
+class DeviceBatch:
+    """A batch built on the device: torch tensors vptr int64[G+1], row_ptr
+    int64[V+1] (global arc offsets), col int32[arcs] (local IDs)."""
+
+    vptr: object
+    row_ptr: object
+    col: object
+    scales: np.ndarray
+    edge_factors: np.ndarray
+
+    @property
+    def count(self) -> int:
+        return int(self.scales.shape[0])
+
+
+def rmat_batch_gpu(count: int = 4096, seed: int = 3, scale_lo: int = 8, scale_hi: int = 16, ef_lo: int = 4,
+                   ef_hi: int = 32, a: float = 0.57, b: float = 0.19, c: float = 0.19,
+                   chunk: int = 1 << 28) -> DeviceBatch:
+    """The same batch as :func:`rmat_batch`, built on the current CUDA device:
+    every edge of every graph is drawn by one kernel (graph g with its own
+    seed seed * 1000003 + g, scale and label table), then rows are sorted and
+    deduplicated in chunks."""
+    import torch
+
+    lib = _gpu_lib()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    st = torch.cuda.current_stream().cuda_stream
+    scales, efs = _batch_params(count, seed, scale_lo, scale_hi, ef_lo, ef_hi)
+    ns = (np.ones(count, dtype=np.uint64) << scales.astype(np.uint64))
+    ms = efs.astype(np.uint64) * ns
+    vptr = np.zeros(count + 1, dtype=np.uint64)
+    np.cumsum(ns, out=vptr[1:])
+    ebase = np.zeros(count + 1, dtype=np.uint64)
+    np.cumsum(ms, out=ebase[1:])
+    seeds = np.array([seed * 1000003 + g for g in range(count)], dtype=np.uint64)
+    perms = np.empty(int(vptr[-1]), dtype=np.uint32)
+    p32 = ctypes.POINTER(ctypes.c_uint32)
+    for g in range(count):
+        view = perms[int(vptr[g]):int(vptr[g + 1])]
+        _check(_lib().lggen_rmat_perm(int(scales[g]), int(seeds[g]), view.ctypes.data_as(p32)), "lggen_rmat_perm")
+
+    def up(x, dt):
+        return torch.from_numpy(np.ascontiguousarray(x).view(dt)).to(dev)
+
+    d_ebase, d_vbase, d_seeds = up(ebase, np.int64), up(vptr[:-1], np.int64), up(seeds, np.int64)
+    d_scales, d_perm = up(scales.astype(np.int32), np.int32), up(perms, np.int32)
+    V = int(vptr[-1])
+    deg = torch.zeros(V, dtype=torch.int64, device=dev)
+    args = (d_ebase.data_ptr(), d_vbase.data_ptr(), d_seeds.data_ptr(), d_scales.data_ptr(),
+            d_vbase.data_ptr(), d_perm.data_ptr(), count, a, a + b, a + b + c)
+    _check(lib.lggen_gpu_batch_edges(0, *args, deg.data_ptr(), None, st), "batch_edges(count)")
+    rp = torch.zeros(V + 1, dtype=torch.int64, device=dev)
+    torch.cumsum(deg, 0, out=rp[1:])
+    col = torch.empty(int(rp[-1].item()), dtype=torch.int32, device=dev)
+    cursor = rp[:-1].clone()
+    _check(lib.lggen_gpu_batch_edges(1, *args, cursor.data_ptr(), col.data_ptr(), st), "batch_edges(scatter)")
+    del cursor, d_perm
+    rp, col = _sort_dedup_rows(rp, deg, col, V, chunk)
+    return DeviceBatch(vptr=up(vptr, np.int64), row_ptr=rp, col=col, scales=scales, edge_factors=efs)

@@ -81,7 +81,61 @@ __global__ void k_weights(const uint64_t* rp, const uint32_t* col, uint64_t n, u
   }
 }
 
+// Batches: edge e of the whole batch belongs to graph g with
+// ebase[g] <= e < ebase[g+1]; graph g draws its local edge e - ebase[g] with its
+// own seed, scale and label table, and its vertices sit at vbase[g] onward.
+struct BatchGen {
+  const uint64_t* ebase;  // count+1
+  const uint64_t* vbase;  // count
+  const uint64_t* seeds;  // count
+  const int32_t* scales;  // count
+  const uint64_t* pbase;  // count: first entry of the graph's label table
+  const uint32_t* perms;
+  uint32_t count;
+  double a, ab, abc;
+};
+
+__device__ __forceinline__ uint32_t batch_graph_of(const BatchGen& b, uint64_t e) {
+  uint32_t lo = 0, hi = b.count;  // largest g with ebase[g] <= e
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (b.ebase[mid] <= e) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+template <bool SCATTER>
+__global__ void k_batch_edges(BatchGen b, unsigned long long* deg_or_cursor, uint32_t* col) {
+  const uint64_t M = b.ebase[b.count];
+  for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < M; e += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t g = batch_graph_of(b, e);
+    RmatParams p{b.seeds[g], b.ebase[g + 1] - b.ebase[g], b.scales[g], b.a, b.ab, b.abc, b.perms + b.pbase[g]};
+    uint32_t u, v;
+    rmat_edge(p, e - b.ebase[g], u, v);
+    if (u == v) continue;
+    const uint64_t vb = b.vbase[g];
+    if (SCATTER) {
+      col[atomicAdd(&deg_or_cursor[vb + u], 1ull)] = v;
+      col[atomicAdd(&deg_or_cursor[vb + v], 1ull)] = u;
+    } else {
+      atomicAdd(&deg_or_cursor[vb + u], 1ull);
+      atomicAdd(&deg_or_cursor[vb + v], 1ull);
+    }
+  }
+}
+
 }  // namespace
+
+extern "C" int lggen_gpu_batch_edges(int scatter, const uint64_t* ebase, const uint64_t* vbase,
+                                     const uint64_t* seeds, const int32_t* scales, const uint64_t* pbase,
+                                     const uint32_t* perms, uint32_t count, double a, double ab, double abc,
+                                     unsigned long long* deg_or_cursor, uint32_t* col, void* stream) {
+  BatchGen b{ebase, vbase, seeds, scales, pbase, perms, count, a, ab, abc};
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (scatter) k_batch_edges<true><<<152 * 32, 256, 0, st>>>(b, deg_or_cursor, col);
+  else k_batch_edges<false><<<152 * 32, 256, 0, st>>>(b, deg_or_cursor, col);
+  return (int)cudaGetLastError();
+}
 
 extern "C" int lggen_gpu_rmat_count(int scale, uint64_t m, double a, double ab, double abc, uint64_t seed,
                                     const uint32_t* perm, unsigned long long* deg, void* stream) {

@@ -214,6 +214,113 @@ lg_status lg_pagerank_noalloc(const lg_graph *g, float damping, uint32_t iters,
    caller must make sure no enqueued work still uses g. */
 void lg_free(lg_graph *g);
 
+/* ------------------------------------------------------------------------
+ * Batches: many independent graphs encoded and traversed in one launch.
+ *
+ * Every graph g keeps its own widths, as the paper sizes each structure by
+ * its own n and m (Sections 3.2.1 and 3.4): IDs at s_g = max(1, bits(n_g - 1))
+ * ("LG-g"), offsets packed at w_O = max(1, bits(arcs_g)) ("ptrLogn").  One run
+ * encodes every graph from its CSR, runs BFS from its vertex 0 and `iters`
+ * pull PageRank iterations (Section 7.1.2) on the encoded stream, all in one
+ * persistent kernel captured once as a CUDA graph and replayed.
+ * ------------------------------------------------------------------------ */
+
+typedef struct lg_batch lg_batch; /* opaque; owns its device memory, not the input */
+
+#define LG_BATCH_FLAG_DROP_MEMBER 1u /* failure injection for tests: one member of the
+                                        first multi-CTA team is left out of the work
+                                        queue, so that team's barrier must run out of
+                                        time and lg_batch_status returns LG_ETIMEOUT */
+
+typedef struct {
+    uint32_t autotune;      /* 1: time the candidate decode schedules at creation      */
+    uint32_t lanes;         /* 0: default/autotuned; else lanes per vertex for every
+                               graph, one of 1, 4, 8, 32 (disables autotune)          */
+    uint64_t tile_arcs;     /* arcs per CTA before a graph gets a team of CTAs;
+                               0: 2^19, or autotuned among 2^18 .. 2^21               */
+    uint32_t wait_limit_us; /* time limit of a team barrier; 0 means 2 s              */
+    uint32_t flags;         /* LG_BATCH_FLAG_* bits                                    */
+} lg_batch_opts;
+
+/* One graph of a batch as laid out on the device (64 bytes). */
+typedef struct {
+    uint64_t vbase;    /* first vertex in the batch vertex space        */
+    uint64_t abase;    /* first arc in the batch input arrays           */
+    uint64_t a_word;   /* first u64 word of the graph's A stream        */
+    uint64_t o_word;   /* first u64 word of the graph's packed offsets  */
+    uint32_t n, arcs;
+    uint32_t s, w_O;   /* ID width and offset width                     */
+    uint32_t lanes;    /* decode lanes per vertex                       */
+    uint32_t team;     /* CTAs working on the graph                     */
+    uint32_t pad[2];
+} lg_batch_graph;
+
+typedef struct {
+    uint32_t count;                /* graphs                                      */
+    uint64_t V, arcs;              /* total vertices and arcs                     */
+    const uint64_t *A;             /* all A streams, device, words_A u64 words     */
+    uint64_t words_A;
+    const uint64_t *O;             /* all packed offsets, device                  */
+    uint64_t words_O;
+    const lg_batch_graph *graphs;  /* device, count entries                        */
+    uint32_t n_items;              /* work items (graph, team member) per run     */
+    uint32_t grid, threads;        /* persistent launch shape                     */
+    uint64_t tile_arcs;            /* tile in use                                 */
+    uint32_t teams, max_team;      /* graphs with more than one CTA; largest team */
+    uint64_t bits_total;           /* sum over graphs of arcs*s + (n+1)*w_O       */
+    uint64_t launches;             /* batch kernel launches so far (one per run)  */
+    uint32_t graphs_by_lanes[4];   /* graphs decoded with 1, 4, 8, 32 lanes       */
+} lg_batch_info;
+
+/*
+ * lg_batch_create -- plan a batch of `count` graphs held as one CSR.
+ *   graph_vptr  device, count+1 u64: graph g owns vertices
+ *               [graph_vptr[g], graph_vptr[g+1]) of the batch vertex space;
+ *               graph_vptr[0] = 0, graph_vptr[count] = V
+ *   row_ptr     device, V+1 u64 GLOBAL arc offsets (row_ptr[V] = arcs)
+ *   col         device, arcs u32 LOCAL vertex IDs: a neighbor of a vertex of
+ *               graph g is given relative to graph_vptr[g]; rows strictly
+ *               increasing; every graph undirected (each arc has its reverse)
+ *   opts        host or NULL (all zero)
+ * row_ptr and col are kept BY REFERENCE: every lg_batch_run re-encodes from
+ * them, so they must stay allocated (and may be refilled with new contents of
+ * the same shape) until lg_batch_free.  Widths, stream layout and the work
+ * queue are fixed here; with opts->autotune the candidate schedules are timed
+ * on the device (each candidate run encodes and traverses a sample).  Invalid
+ * input gives LG_EINVAL; a graph needs n_g < 2^32 and arcs_g < 2^32.
+ * Synchronizes `stream`.
+ */
+lg_status lg_batch_create(const uint64_t *graph_vptr, const uint64_t *row_ptr, const uint32_t *col,
+                          uint32_t count, uint64_t V, uint64_t arcs, const lg_batch_opts *opts,
+                          void *stream, lg_batch **out);
+
+/*
+ * lg_batch_run -- encode every graph and traverse it, one graph launch.
+ *   depths  device, V u32: BFS depth from the graph's own vertex 0, by batch
+ *           vertex; UINT32_MAX = unreachable
+ *   ranks   device, V floats: PageRank of each graph over its own n_g (as
+ *           lg_pagerank, global, r_0 = 1/n_g), after `iters` iterations
+ *           (iters = 0 leaves ranks untouched)
+ * Asynchronous.  The first call (and any call with a different damping, iters
+ * or output pointer) captures and instantiates the run graph; later calls only
+ * replay it.  Runs of one batch must not overlap: order them on one stream.
+ * Call lg_batch_status to learn whether a team barrier ran out of time.
+ */
+lg_status lg_batch_run(lg_batch *b, float damping, uint32_t iters, uint32_t *depths, float *ranks,
+                       void *stream);
+
+/* lg_batch_status -- synchronize `stream` and report the last run's device
+   status: LG_OK, or LG_ETIMEOUT if a team barrier gave up (that graph's
+   results are incomplete; the other graphs are unaffected). */
+lg_status lg_batch_status(lg_batch *b, void *stream);
+
+/* lg_batch_info_get -- sizes, schedule and device views.  `out` host.  No GPU work. */
+lg_status lg_batch_info_get(const lg_batch *b, lg_batch_info *out);
+
+/* lg_batch_free -- release the batch's device memory (not the input).  NULL-safe.
+   Synchronizes the device. */
+void lg_batch_free(lg_batch *b);
+
 /* lg_kernel_launches -- number of CUDA kernels this library has launched in
    this process so far (all threads, all devices).  For instrumentation: the
    difference across a region counts the library's launches in it.  No GPU work. */

@@ -29,11 +29,14 @@ __all__ = [
     "LG_ID_GLOBAL", "LG_ID_LOCAL", "LG_ID_LOCAL_GAP", "LG_ID_CSR32", "LG_OFF_PACKED", "LG_OFF_EF",
     "LgError", "LogGraph", "build", "load", "lg_encode", "lg_stats_get", "lg_arrays_get", "lg_neighbors",
     "lg_bfs", "lg_pagerank", "lg_pagerank_noalloc", "lg_free", "lg_last_error", "lg_kernel_launches",
+    "LgBatch", "lg_batch_create", "lg_batch_run", "lg_batch_status", "lg_batch_info_get", "lg_batch_free",
+    "LG_BATCH_FLAG_DROP_MEMBER",
 ]
 
 LG_ID_GLOBAL, LG_ID_LOCAL, LG_ID_LOCAL_GAP, LG_ID_CSR32 = 0, 1, 2, 3
 LG_OFF_PACKED, LG_OFF_EF = 0, 1
 LG_FLAG_CHECK_SYMMETRIC = 1
+LG_BATCH_FLAG_DROP_MEMBER = 1
 STATUS = {0: "LG_OK", 1: "LG_EINVAL", 2: "LG_ENOMEM", 3: "LG_ECUDA", 4: "LG_ERANGE", 5: "LG_ETIMEOUT",
           6: "LG_EUNSUPPORTED"}
 
@@ -58,6 +61,18 @@ class _Arrays(ctypes.Structure):
     _fields_ = [("A", _vp), ("words_A", _u64), ("O", _vp), ("words_O", _u64), ("ef_low", _vp),
                 ("words_ef_low", _u64), ("ef_high", _vp), ("words_ef_high", _u64), ("ef_samples", _vp),
                 ("words_ef_samples", _u64), ("perm", _vp), ("inv_perm", _vp)]
+
+
+class _BatchOpts(ctypes.Structure):
+    _fields_ = [("autotune", _u32), ("lanes", _u32), ("tile_arcs", _u64), ("wait_limit_us", _u32),
+                ("flags", _u32)]
+
+
+class _BatchInfo(ctypes.Structure):
+    _fields_ = [("count", _u32), ("V", _u64), ("arcs", _u64), ("A", _vp), ("words_A", _u64), ("O", _vp),
+                ("words_O", _u64), ("graphs", _vp), ("n_items", _u32), ("grid", _u32), ("threads", _u32),
+                ("tile_arcs", _u64), ("teams", _u32), ("max_team", _u32), ("bits_total", _u64),
+                ("launches", _u64), ("graphs_by_lanes", _u32 * 4)]
 
 
 class LgError(RuntimeError):
@@ -93,8 +108,16 @@ def load(auto_build: bool = False):
         h.lg_last_error.restype = ctypes.c_char_p
         h.lg_kernel_launches.argtypes = []
         h.lg_kernel_launches.restype = _u64
+        h.lg_batch_create.argtypes = [_vp, _vp, _vp, _u32, _u64, _u64, ctypes.POINTER(_BatchOpts), _vp,
+                                      ctypes.POINTER(_vp)]
+        h.lg_batch_run.argtypes = [_vp, _f32, _u32, _vp, _vp, _vp]
+        h.lg_batch_status.argtypes = [_vp, _vp]
+        h.lg_batch_info_get.argtypes = [_vp, ctypes.POINTER(_BatchInfo)]
+        h.lg_batch_free.argtypes = [_vp]
+        h.lg_batch_free.restype = None
         for f in ("lg_encode", "lg_stats_get", "lg_arrays_get", "lg_neighbors", "lg_bfs", "lg_pagerank",
-                  "lg_pagerank_noalloc"):
+                  "lg_pagerank_noalloc", "lg_batch_create", "lg_batch_run", "lg_batch_status",
+                  "lg_batch_info_get"):
             getattr(h, f).restype = _i32
         _lib = h
     return _lib
@@ -277,3 +300,99 @@ def lg_pagerank(g: LogGraph, damping: float = 0.85, iters: int = 20, personalize
     ps = None if personalize is None else ctypes.byref(_u32(personalize))
     _check(lib.lg_pagerank(g.handle, damping, iters, ps, out.data_ptr(), _stream(stream)), "lg_pagerank")
     return out
+
+
+# --- batches -----------------------------------------------------------------
+
+class LgBatch:
+    """Owner of an lg_batch handle and of the input it references."""
+
+    def __init__(self, handle: int, keepalive=()):
+        self._h = _vp(handle)
+        self._keep = keepalive  # row_ptr / col / graph_vptr: lg_batch_run re-encodes from them
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        return lg_batch_info_get(self)
+
+    def free(self):
+        if self._h is not None and self._h.value:
+            load().lg_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def lg_batch_create(graph_vptr, row_ptr, col, *, autotune: bool = True, lanes: int = 0, tile_arcs: int = 0,
+                    wait_limit_us: int = 0, flags: int = 0, stream=None) -> LgBatch:
+    """lg_batch_create: plan a batch of graphs given as one CSR over the batch
+    vertex space (graph_vptr uint64[count+1], row_ptr uint64[V+1] global arc
+    offsets, col uint32[arcs] local IDs).  The device tensors are kept alive
+    by the returned object, since every run re-encodes from them."""
+    lib = load()
+    vp = _dev(graph_vptr, torch.int64, "graph_vptr")
+    rp = _dev(row_ptr, torch.int64, "row_ptr")
+    cl = _dev(col, torch.int32, "col")
+    opts = _BatchOpts(int(bool(autotune)), lanes, tile_arcs, wait_limit_us, flags)
+    h = _vp()
+    _check(lib.lg_batch_create(vp.data_ptr(), rp.data_ptr(), cl.data_ptr() if cl.numel() else None,
+                               vp.numel() - 1, rp.numel() - 1, cl.numel(), ctypes.byref(opts),
+                               _stream(stream), ctypes.byref(h)), "lg_batch_create")
+    return LgBatch(h.value, keepalive=(vp, rp, cl))
+
+
+def lg_batch_run(b: LgBatch, damping: float = 0.85, iters: int = 10, depths: Optional[torch.Tensor] = None,
+                 ranks: Optional[torch.Tensor] = None, stream=None):
+    """lg_batch_run: encode + BFS from each graph's vertex 0 + PageRank, one
+    graph launch.  Returns (depths int32[V] holding uint32, ranks float32[V])."""
+    V = b.info()["V"]
+    if depths is None:
+        depths = torch.empty(V, dtype=torch.int32, device="cuda")
+    if ranks is None:
+        ranks = torch.empty(V, dtype=torch.float32, device="cuda")
+    _check(load().lg_batch_run(b.handle, damping, iters, depths.data_ptr(), ranks.data_ptr(), _stream(stream)),
+           "lg_batch_run")
+    return depths, ranks
+
+
+def lg_batch_status(b: LgBatch, stream=None) -> None:
+    """lg_batch_status: synchronize and raise LgError (LG_ETIMEOUT) if a team
+    barrier of the last run ran out of time."""
+    _check(load().lg_batch_status(b.handle, _stream(stream)), "lg_batch_status")
+
+
+def lg_batch_info_get(b: LgBatch) -> dict:
+    i = _BatchInfo()
+    _check(load().lg_batch_info_get(b.handle, ctypes.byref(i)), "lg_batch_info_get")
+    d = {k: getattr(i, k) for k, _ in _BatchInfo._fields_}
+    d["graphs_by_lanes"] = dict(zip((1, 4, 8, 32), list(i.graphs_by_lanes)))
+    return d
+
+
+def lg_batch_arrays(b: LgBatch) -> dict:
+    """Host copies of the batch's A and O word streams and its graph table
+    (structured numpy array with the fields of lg_batch_graph)."""
+    i = lg_batch_info_get(b)
+    torch.cuda.synchronize()
+    out = {}
+    for name in ("A", "O"):
+        t = torch.as_tensor(_DevView(i[name], i["words_" + name], "<i8"), device="cuda")
+        out[name] = t.cpu().numpy().view(np.uint64).copy()
+    t = torch.as_tensor(_DevView(i["graphs"], i["count"] * 8, "<i8"), device="cuda")
+    raw = t.cpu().numpy().view(np.uint64).reshape(i["count"], 8)
+    dt = np.dtype([("vbase", "<u8"), ("abase", "<u8"), ("a_word", "<u8"), ("o_word", "<u8"), ("n", "<u4"),
+                   ("arcs", "<u4"), ("s", "<u4"), ("w_O", "<u4"), ("lanes", "<u4"), ("team", "<u4"),
+                   ("pad", "<u4", 2)])
+    out["graphs"] = raw.copy().view(dt).reshape(-1)
+    return out
+
+
+def lg_batch_free(b: LgBatch) -> None:
+    b.free()

@@ -28,6 +28,7 @@ SOURCES = [
     "lg_trav_gap.cu",
     "lg_trav_csr32.cu",
     "lg_static.cu",
+    "lg_batch.cu",
 ]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
