@@ -20,8 +20,14 @@ R-MAT graphs (scales 8..16, edge factors 4..32), one step = one replay of the
 captured persistent launch that encodes every graph with its own widths, runs
 BFS from each graph's vertex 0 and 10 PageRank iterations.
 
+The ``serve`` workload measures the serving engine: 3 resident compressed
+R-MAT graphs (scales 20, 22, 24, edge factor 16, global IDs + Elias-Fano
+offsets), 100,000 requests (60 % lookups of 1-256 vertices, 30 % BFS, 10 %
+personalized PageRank of 10 iterations): saturation throughput from a burst,
+then p50 / p99 latency with Poisson arrivals at 0.25, 0.5 and 0.9 of it.
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lg|reference]
-                       [--workload community|rmat16|rmat27|batch]
+                       [--workload community|rmat16|rmat27|batch|serve]
 Under torchrun (N > 1) every rank runs an independent replica ("replicas only":
 one GPU holds the whole graph, no collective on the data path).
 """
@@ -65,6 +71,12 @@ WORKLOADS = {
               None, None, 1, 10),
 }
 BATCH_COUNT, BATCH_SEED = 4096, 3
+WORKLOADS["serve"] = ("serving: 3 resident R-MAT graphs (scales 20, 22, 24, edge factor 16, seed 4), global IDs + "
+                      "Elias-Fano offsets; requests 60% neighborhood lookups of 1-256 uniform vertices, 30% "
+                      "single-source BFS, 10% personalized PageRank (10 iterations, d=0.85), graph uniform, "
+                      "sources uniform over vertices of nonzero degree; Poisson arrivals",
+                      None, None, 1, 10)
+SERVE_SCALES, SERVE_SEED, SERVE_RATES = (20, 22, 24), 4, (0.25, 0.5, 0.9)
 
 
 class Workload:
@@ -524,6 +536,116 @@ def run_batch(args, rank, world):
     return out, rank
 
 
+def latency_summary(lat_ns, kinds):
+    ms = lat_ns.astype(np.float64) / 1e6
+    out = {"p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+           "mean_ms": float(ms.mean())}
+    for k, name in enumerate(("lookup", "bfs", "ppr")):
+        sel = ms[kinds == k]
+        if sel.size:
+            out[name] = {"p50_ms": float(np.percentile(sel, 50)), "p99_ms": float(np.percentile(sel, 99))}
+    return out
+
+
+def run_serve(args, rank, world):
+    """Serving: saturation throughput (burst) and latency at 3 Poisson rates."""
+    import torch
+
+    import paper_2010_15879_gb300 as lg
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    lg.load(auto_build=True)
+    desc = WORKLOADS["serve"][0]
+    t0 = time.time()
+    graphs, rps, sizes = [], [], []
+    for sc in SERVE_SCALES:
+        rp, col, _ = gen.rmat_gpu(sc, 16, seed=SERVE_SEED)
+        g = lg.lg_encode(rp, col, id_mode=0, off_mode=1)
+        st = g.stats()
+        graphs.append(g)
+        rps.append(rp.cpu().numpy().view(np.uint64))
+        sizes.append({"scale": sc, "n": st["n"], "arcs": st["arcs"], "bits_A": st["bits_A"], "bits_O": st["bits_O"]})
+        del rp, col
+    torch.cuda.empty_cache()
+    log(f"3 graphs encoded in {time.time() - t0:.1f}s: " + ", ".join(f"2^{x['scale']}: {x['arcs']} arcs" for x in sizes))
+    nreq = args.serve_requests
+    tr = gen.serve_trace(rps, nreq, seed=SERVE_SEED)
+    h2d = float(np.mean(np.where(tr.kind == 0, np.diff(tr.nbr_off) * 4, 0)) + 32)
+    n_of = np.array([x["n"] for x in sizes], dtype=np.float64)
+    deg_sum = [np.diff(rp) for rp in rps]
+    look = np.zeros(nreq)
+    for i in np.flatnonzero(tr.kind == 0):
+        vs = tr.nbr_vertices[int(tr.nbr_off[i]):int(tr.nbr_off[i + 1])]
+        look[i] = (vs.size + 1) * 8 + 4 * float(deg_sum[int(tr.graph[i])][vs].sum())
+    d2h = float(np.mean(np.where(tr.kind == 0, look, 4 * n_of[tr.graph])))
+    srv = lg.lg_server_create(graphs, device_bytes=48 << 30, host_bytes=8 << 30)
+
+    def replay(trace, label):
+        lat, rs = lg.lg_server_replay(srv, trace.kind, trace.graph, trace.source, trace.nbr_off,
+                                      trace.nbr_vertices, trace.arrival_ns)
+        thr = len(trace) / (rs["makespan_ns"] * 1e-9)
+        log(f"{label}: {len(trace)} requests in {rs['makespan_ns'] / 1e9:.2f}s = {thr:.0f} req/s, "
+            f"p50 {np.percentile(lat, 50) / 1e6:.2f} ms, p99 {np.percentile(lat, 99) / 1e6:.2f} ms")
+        return lat, rs, thr
+
+    # warm-up: a small burst touches every engine
+    warm = gen.serve_trace(rps, 2000, seed=SERVE_SEED + 100)
+    replay(warm, "warm-up")
+    l0 = lg.lg_kernel_launches()
+    with ClockSampler(dev.index) as clk:
+        lat_b, rs_b, sat = replay(tr, "burst (saturation)")
+        per_rate = {}
+        for f in SERVE_RATES:
+            rate = f * sat
+            lat, rs, thr = replay(tr.at_rate(rate, seed=int(f * 100)), f"rate {f:.2f} x saturation")
+            summ = latency_summary(lat, tr.kind)
+            summ.update({"offered_req_per_s": rate, "achieved_req_per_s": thr})
+            per_rate[str(f)] = summ
+    launches = lg.lg_kernel_launches() - l0
+    st = lg.lg_server_stats_get(srv)
+    times = {}
+    for gi, x in enumerate(sizes):
+        for k, name in ((1, "bfs_level"), (2, "ppr_sweep"), (0, "lookup_batch")):
+            o, ns = lg.lg_server_engine_time(srv, gi, k)
+            times[f"2^{x['scale']} {name}"] = {"count": o, "mean_us": ns / 1e3 / max(o, 1)}
+    srv.destroy()
+    # roofline of the PPR sweep on the 2^24 graph: compressed stream + offsets
+    # once, one 32-byte sector of 8 contributions per arc, 32 B written per vertex
+    big = sizes[2]
+    sweep = times[f"2^{big['scale']} ppr_sweep"]
+    alg = (big["bits_A"] + big["bits_O"]) // 8 + 32 * big["arcs"] + 32 * big["n"]
+    peak, peak_kind = peaks()
+    achieved = alg / (sweep["mean_us"] * 1e-6) / 1e9 if sweep["count"] else None
+    for g in graphs:
+        g.free()
+    out = {
+        "metric": "serving throughput at saturation (requests/s; 60% lookups, 30% BFS, 10% PPR over 3 resident "
+                  "compressed R-MAT graphs), with p50/p99 latency at 0.25/0.5/0.9 of it",
+        "value": sat * world, "unit": "req/s", "n_gpus": world, "steps": nreq, "warmup": 2000,
+        "ms_per_step": 1e3 / sat, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32 ids / fp32 ranks", "data": "synthetic (seeded generator and trace; no dataset)",
+        "config": {"workload": desc, "graphs": sizes, "requests": nreq, "rates_of_saturation": list(SERVE_RATES),
+                   "l2": "graphs larger than L2 (2^24: %.2f GB compressed)" % ((big["bits_A"] + big["bits_O"]) / 8e9),
+                   "parallelism": f"replicas x{world}", "step": "one request"},
+        "latency": per_rate,
+        "e2e": {"value": sat * world, "unit": "req/s", "note": "the serving path is end to end: requests from host "
+                "memory, results copied to pinned host memory, timed from scheduled arrival to completion",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "detail": {"burst": {"p50_ms": float(np.percentile(lat_b, 50) / 1e6),
+                             "p99_ms": float(np.percentile(lat_b, 99) / 1e6)},
+                   "server": {k: v for k, v in st.items()}, "engine_device_time": times},
+        "roofline": {"kernel": "k_ppr_pull (8 personalized PageRank slots, 2^24 graph; CUDA events on the engine "
+                               "stream)", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": None if achieved is None else achieved / peak,
+                     "peak_kind": f"{peak_kind} (copy bandwidth)", "algorithmic_bytes_per_launch": alg,
+                     "traffic": ncu_traffic("serve")},
+        "clocks": clk.summary(),
+    }
+    return out, rank
+
+
 def cpu_baseline_batch(vptr, rp, col, iters, min_seconds=10.0, max_graphs=None):
     """The oracle as it stands (single-threaded C) on a bounded sample of the
     batch: whole graphs in batch order (BFS from vertex 0 + `iters` PageRank
@@ -619,9 +741,52 @@ def profile_batch(args):
     b.free()
 
 
+def run_reference_serve(args, rank, world):
+    """The oracle answering the same request trace on the host cores, one
+    request at a time, for a bounded sample (about 2 s per step)."""
+    import oracle
+
+    hs = [gen.rmat(sc, 16, seed=SERVE_SEED) for sc in SERVE_SCALES]
+    tr = gen.serve_trace([h.row_ptr for h in hs], args.serve_requests, seed=SERVE_SEED)
+
+    def answer(i):
+        h = hs[int(tr.graph[i])]
+        k = int(tr.kind[i])
+        if k == 0:
+            vs = tr.nbr_vertices[int(tr.nbr_off[i]):int(tr.nbr_off[i + 1])]
+            return [h.col[h.row_ptr[v]:h.row_ptr[v + 1]].copy() for v in vs]
+        if k == 1:
+            return oracle.bfs(h.n, h.row_ptr, h.col, int(tr.source[i]))
+        return oracle.pagerank(h.n, h.row_ptr, h.col, 0.85, 10, personalize=int(tr.source[i]))
+
+    i = 0
+    for _ in range(args.warmup):
+        answer(i % len(tr)); i += 1
+    done, t0 = 0, time.time()
+    for _ in range(args.steps):
+        ts = time.time()
+        while time.time() - ts < 2.0:
+            answer(i % len(tr)); i += 1; done += 1
+    el = time.time() - t0
+    v = done / el
+    desc = WORKLOADS["serve"][0]
+    return {"impl": "reference", "metric": "serving throughput at saturation (requests/s; 60% lookups, 30% BFS, "
+                                           "10% PPR over 3 resident compressed R-MAT graphs), with p50/p99 latency "
+                                           "at 0.25/0.5/0.9 of it",
+            "value": v, "unit": "req/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 ranks / u32 depths", "data": "synthetic (seeded generator and trace)",
+            "config": {"workload": desc, "requests": args.serve_requests, "parallelism": "host cores"},
+            "cpu_baseline": {"value": v, "unit": "req/s", "cores": 1, "kind": "oracle",
+                             "sample": f"the first {done} requests of the trace, one at a time, {el:.1f} s"},
+            "e2e": {"value": v, "unit": "req/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}, rank
+
+
 def run_reference(args, rank, world):
     import torch
 
+    if args.workload == "serve":
+        return run_reference_serve(args, rank, world)
     if args.workload == "batch":
         desc, _, _, _, T = WORKLOADS["batch"]
         hb = gen.rmat_batch(count=64, seed=BATCH_SEED)  # the batch's first 64 graphs (seeded per graph)
@@ -685,6 +850,7 @@ def main():
                     help="run one untimed pass of the hot path (for ncu) and exit")
     ap.add_argument("--pr-iters", type=int, default=None, help="PageRank iterations in --profile mode")
     ap.add_argument("--batch-count", type=int, default=None, help="graphs in --profile mode of the batch workload")
+    ap.add_argument("--serve-requests", type=int, default=100000, help="requests per rate (serve workload)")
     args = ap.parse_args()
     if args.warmup < 3:
         log("warmup raised to 3 (timing rule)")
@@ -708,7 +874,8 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         dist.init_process_group("nccl")
-    out, rank = (run_batch if args.workload == "batch" else run_lg)(args, rank, world)
+    runner = {"batch": run_batch, "serve": run_serve}.get(args.workload, run_lg)
+    out, rank = runner(args, rank, world)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -432,3 +432,58 @@ def rmat_batch_gpu(count: int = 4096, seed: int = 3, scale_lo: int = 8, scale_hi
     del cursor, d_perm
     rp, col = _sort_dedup_rows(rp, deg, col, V, chunk)
     return DeviceBatch(vptr=up(vptr, np.int64), row_ptr=rp, col=col, scales=scales, edge_factors=efs)
+
+
+# --- serving traces ---------------------------------------------------------
+
+@dataclass
+class Trace:
+    """A request trace for the serving engine, as columns: request i has kind
+    (0 lookup, 1 BFS, 2 personalized PageRank), graph, source, lookup vertices
+    nbr_vertices[nbr_off[i]:nbr_off[i+1]] and arrival time arrival_ns[i]."""
+
+    kind: np.ndarray
+    graph: np.ndarray
+    source: np.ndarray
+    nbr_off: np.ndarray
+    nbr_vertices: np.ndarray
+    arrival_ns: np.ndarray
+
+    def __len__(self) -> int:
+        return int(self.kind.shape[0])
+
+    def at_rate(self, rate_per_s: float, seed: int = 0) -> "Trace":
+        """The same requests with Poisson arrivals at `rate_per_s` (0: all at once)."""
+        if rate_per_s <= 0:
+            arr = np.zeros(len(self), dtype=np.uint64)
+        else:
+            rng = np.random.default_rng(seed + 1)
+            gaps = rng.exponential(1e9 / rate_per_s, size=len(self))
+            arr = np.cumsum(gaps).astype(np.uint64)
+        return Trace(self.kind, self.graph, self.source, self.nbr_off, self.nbr_vertices, arr)
+
+
+def serve_trace(row_ptrs, count: int, seed: int = 4, p_nbr: float = 0.6, p_bfs: float = 0.3,
+                max_lookup: int = 256) -> Trace:
+    """`count` requests over the graphs whose host row_ptr arrays are given:
+    kind drawn with probabilities (p_nbr, p_bfs, rest), graph uniform, lookups
+    of 1..max_lookup vertices uniform in [0, n), BFS / PageRank sources uniform
+    among vertices of nonzero degree.  Arrivals all at 0 (see Trace.at_rate)."""
+    rng = np.random.default_rng(seed)
+    u = rng.random(count)
+    kind = np.where(u < p_nbr, 0, np.where(u < p_nbr + p_bfs, 1, 2)).astype(np.uint32)
+    graph = rng.integers(0, len(row_ptrs), size=count).astype(np.uint32)
+    nonzero = [np.flatnonzero(np.diff(np.asarray(rp, dtype=np.uint64)) > 0).astype(np.uint32) for rp in row_ptrs]
+    ns = [len(rp) - 1 for rp in row_ptrs]
+    source = np.zeros(count, dtype=np.uint32)
+    sizes = np.where(kind == 0, rng.integers(1, max_lookup + 1, size=count), 0).astype(np.uint64)
+    nbr_off = np.zeros(count + 1, dtype=np.uint64)
+    np.cumsum(sizes, out=nbr_off[1:])
+    nbr_vertices = np.zeros(int(nbr_off[-1]), dtype=np.uint32)
+    for i in range(count):
+        g = int(graph[i])
+        if kind[i] == 0:
+            nbr_vertices[int(nbr_off[i]):int(nbr_off[i + 1])] = rng.integers(0, ns[g], size=int(sizes[i]))
+        else:
+            source[i] = nonzero[g][rng.integers(0, len(nonzero[g]))]
+    return Trace(kind, graph, source, nbr_off, nbr_vertices, np.zeros(count, dtype=np.uint64))

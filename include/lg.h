@@ -321,6 +321,130 @@ lg_status lg_batch_info_get(const lg_batch *b, lg_batch_info *out);
    Synchronizes the device. */
 void lg_batch_free(lg_batch *b);
 
+/* ------------------------------------------------------------------------
+ * Serving: resident compressed graphs answering a stream of requests with
+ * continuous batching.  The paper has no serving layer; the requests are its
+ * operations: neighborhood lookups (getNeighbors, Section 3.7.2), BFS and
+ * personalized PageRank (Section 7.1.2), run on graphs encoded by lg_encode.
+ *
+ * Per graph, three engines (host threads with their own CUDA streams) run
+ * concurrently: a 64-slot multi-source BFS sweep that new sources join
+ * between two levels, an 8-slot personalized PageRank sweep that requests join
+ * between two iterations (the 8 rank vectors of a vertex share one 32-byte
+ * sector), and a lookup engine that merges every waiting lookup into one
+ * decode.  A request is admitted when its device state (BFS depth row, PPR
+ * result vector, lookup output) fits a fixed device arena; results are copied
+ * into a pinned host arena and stay there until lg_server_release.
+ * ------------------------------------------------------------------------ */
+
+typedef struct lg_server lg_server; /* opaque; uses the graphs, does not own them */
+
+typedef enum {
+    LG_REQ_NEIGHBORS = 0,   /* N_v of `count` vertices                                  */
+    LG_REQ_BFS = 1,         /* depths from `source`                                     */
+    LG_REQ_PPR = 2          /* personalized PageRank from `source`                       */
+} lg_request_kind;
+
+typedef struct {
+    uint64_t device_bytes;       /* device arena for request state; 0 = 16 GiB          */
+    uint64_t host_bytes;         /* pinned host arena for results; 0 = 4 GiB            */
+    uint32_t bfs_slots;          /* BFS sources per sweep, 1..64; 0 = 64                */
+    uint32_t ppr_slots;          /* PPR requests per sweep, 1..8; 0 = 8                 */
+    uint32_t nbr_batch_vertices; /* most vertices decoded per lookup batch; 0 = 2^20    */
+    uint32_t ppr_iters;          /* PPR iterations when a request gives 0; 0 = 10       */
+} lg_server_opts;
+
+typedef struct {
+    uint32_t kind;              /* lg_request_kind                                      */
+    uint32_t graph;             /* index into the graphs given to lg_server_create      */
+    uint32_t source;            /* BFS / PPR source vertex (< n)                        */
+    uint32_t iters;             /* PPR iterations (0: server default)                   */
+    float damping;              /* PPR damping in (0, 1] (0: 0.85)                      */
+    uint32_t count;             /* lookup: number of vertices, 1 .. 2^20                */
+    const uint32_t *vertices;   /* lookup: host array of `count` vertices (< n), copied */
+    uint64_t user;              /* returned unchanged in the result                     */
+} lg_request;
+
+typedef struct {
+    uint64_t ticket, user;
+    uint32_t kind, graph;
+    int32_t status;             /* LG_OK, LG_ENOMEM or LG_ECUDA                         */
+    const void *data;           /* pinned host memory owned by the server until
+                                   lg_server_release:
+                                   NEIGHBORS: u64 offsets[count+1] (from 0), then u32 IDs
+                                   BFS: u32 depths[n] (UINT32_MAX unreachable)
+                                   PPR: float ranks[n]                                  */
+    uint64_t bytes, count;      /* bytes of data; count = vertices queried, or n        */
+    uint64_t t_submit_ns, t_admit_ns, t_done_ns; /* steady clock                        */
+} lg_result;
+
+typedef struct {
+    uint64_t submitted, completed, failed, by_kind[3];
+    uint64_t bfs_levels;         /* sweep levels run                                    */
+    uint64_t bfs_joins;          /* sources that joined a sweep                         */
+    uint64_t bfs_joins_running;  /* ... while other sources of the sweep were active    */
+    uint64_t bfs_max_active;     /* most sources active in one sweep                    */
+    uint64_t ppr_iterations, ppr_joins, ppr_joins_running, ppr_max_active;
+    uint64_t nbr_batches, nbr_max_batch;
+    uint64_t admission_waits;    /* times a request waited for device memory            */
+    uint64_t device_bytes, device_used, device_peak;
+    uint64_t host_bytes, host_used, host_peak;
+} lg_server_stats;
+
+typedef struct {
+    uint64_t completed, failed;
+    uint64_t makespan_ns;        /* first scheduled arrival to last completion          */
+} lg_replay_stats;
+
+/*
+ * lg_server_create -- start serving `count` graphs (encoded with relabel = 0 on
+ * the current device; relabeled graphs give LG_EUNSUPPORTED).  Allocates the
+ * two arenas and per-graph engine state (BFS masks 24 B and PPR vectors 64 B
+ * per vertex) and starts 3 threads per graph.  The graphs must outlive the
+ * server.
+ */
+lg_status lg_server_create(const lg_graph *const *graphs, uint32_t count, const lg_server_opts *opts,
+                           lg_server **out);
+
+/* lg_server_submit -- enqueue one request (host memory; copied).  Returns at
+   once with a ticket.  Invalid requests give LG_EINVAL; a request whose state
+   could never fit the arenas gives LG_ENOMEM.  Thread-safe. */
+lg_status lg_server_submit(lg_server *s, const lg_request *req, uint64_t *ticket);
+
+/* lg_server_wait -- up to `max` completed results (in completion order), waiting
+   at most timeout_us for the first one; *got = 0 on timeout.  Thread-safe. */
+lg_status lg_server_wait(lg_server *s, lg_result *out, uint32_t max, uint32_t *got, uint32_t timeout_us);
+
+/* lg_server_release -- return a delivered result's host memory to the server. */
+lg_status lg_server_release(lg_server *s, uint64_t ticket);
+
+/* lg_server_stats_get -- counters and arena use.  No GPU work. */
+lg_status lg_server_stats_get(lg_server *s, lg_server_stats *out);
+
+/*
+ * lg_server_replay -- open-loop load generator: request i (columns kind,
+ * graph, source; lookup vertices nbr_vertices[nbr_off[i] .. nbr_off[i+1]])
+ * is submitted by a separate thread at arrival_ns[i] after the start (PPR
+ * with the server's default iterations and damping 0.85).  The calling thread
+ * collects every result: latency_ns[i] = completion - scheduled arrival; if
+ * keep and keep[i] are not NULL the result bytes are copied there (the caller
+ * sizes it: see lg_result.data); every result is released.  All requests are
+ * validated before the clock starts.  Returns LG_ECUDA if a request failed.
+ */
+lg_status lg_server_replay(lg_server *s, uint64_t n, const uint32_t *kind, const uint32_t *graph,
+                           const uint32_t *source, const uint64_t *nbr_off, const uint32_t *nbr_vertices,
+                           const uint64_t *arrival_ns, void *const *keep, uint64_t *latency_ns,
+                           lg_replay_stats *out);
+
+/* lg_server_engine_time -- device time of one engine's kernels, measured with
+   CUDA events on the engine's stream: *ops = BFS levels, PPR sweeps or lookup
+   batches run so far, *gpu_ns = their summed duration.  No GPU work. */
+lg_status lg_server_engine_time(lg_server *s, uint32_t graph, uint32_t kind, uint64_t *ops, uint64_t *gpu_ns);
+
+/* lg_server_destroy -- stop the engines (work in flight finishes, waiting
+   requests are dropped), free the arenas and every undelivered result.  NULL-safe. */
+void lg_server_destroy(lg_server *s);
+
 /* lg_kernel_launches -- number of CUDA kernels this library has launched in
    this process so far (all threads, all devices).  For instrumentation: the
    difference across a region counts the library's launches in it.  No GPU work. */

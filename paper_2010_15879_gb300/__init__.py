@@ -31,12 +31,16 @@ __all__ = [
     "lg_bfs", "lg_pagerank", "lg_pagerank_noalloc", "lg_free", "lg_last_error", "lg_kernel_launches",
     "LgBatch", "lg_batch_create", "lg_batch_run", "lg_batch_status", "lg_batch_info_get", "lg_batch_free",
     "LG_BATCH_FLAG_DROP_MEMBER",
+    "LG_REQ_NEIGHBORS", "LG_REQ_BFS", "LG_REQ_PPR", "LgServer", "lg_server_create", "lg_server_submit",
+    "lg_server_wait", "lg_server_release", "lg_server_stats_get", "lg_server_replay", "lg_server_destroy",
+    "lg_server_engine_time",
 ]
 
 LG_ID_GLOBAL, LG_ID_LOCAL, LG_ID_LOCAL_GAP, LG_ID_CSR32 = 0, 1, 2, 3
 LG_OFF_PACKED, LG_OFF_EF = 0, 1
 LG_FLAG_CHECK_SYMMETRIC = 1
 LG_BATCH_FLAG_DROP_MEMBER = 1
+LG_REQ_NEIGHBORS, LG_REQ_BFS, LG_REQ_PPR = 0, 1, 2
 STATUS = {0: "LG_OK", 1: "LG_EINVAL", 2: "LG_ENOMEM", 3: "LG_ECUDA", 4: "LG_ERANGE", 5: "LG_ETIMEOUT",
           6: "LG_EUNSUPPORTED"}
 
@@ -73,6 +77,34 @@ class _BatchInfo(ctypes.Structure):
                 ("words_O", _u64), ("graphs", _vp), ("n_items", _u32), ("grid", _u32), ("threads", _u32),
                 ("tile_arcs", _u64), ("teams", _u32), ("max_team", _u32), ("bits_total", _u64),
                 ("launches", _u64), ("graphs_by_lanes", _u32 * 4)]
+
+
+class _ServerOpts(ctypes.Structure):
+    _fields_ = [("device_bytes", _u64), ("host_bytes", _u64), ("bfs_slots", _u32), ("ppr_slots", _u32),
+                ("nbr_batch_vertices", _u32), ("ppr_iters", _u32)]
+
+
+class _Request(ctypes.Structure):
+    _fields_ = [("kind", _u32), ("graph", _u32), ("source", _u32), ("iters", _u32), ("damping", _f32),
+                ("count", _u32), ("vertices", _vp), ("user", _u64)]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("ticket", _u64), ("user", _u64), ("kind", _u32), ("graph", _u32), ("status", _i32),
+                ("data", _vp), ("bytes", _u64), ("count", _u64), ("t_submit_ns", _u64), ("t_admit_ns", _u64),
+                ("t_done_ns", _u64)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [(k, _u64) for k in ("submitted", "completed", "failed")] + [("by_kind", _u64 * 3)] + [
+        (k, _u64) for k in ("bfs_levels", "bfs_joins", "bfs_joins_running", "bfs_max_active", "ppr_iterations",
+                            "ppr_joins", "ppr_joins_running", "ppr_max_active", "nbr_batches", "nbr_max_batch",
+                            "admission_waits", "device_bytes", "device_used", "device_peak", "host_bytes",
+                            "host_used", "host_peak")]
+
+
+class _ReplayStats(ctypes.Structure):
+    _fields_ = [("completed", _u64), ("failed", _u64), ("makespan_ns", _u64)]
 
 
 class LgError(RuntimeError):
@@ -115,9 +147,20 @@ def load(auto_build: bool = False):
         h.lg_batch_info_get.argtypes = [_vp, ctypes.POINTER(_BatchInfo)]
         h.lg_batch_free.argtypes = [_vp]
         h.lg_batch_free.restype = None
+        h.lg_server_create.argtypes = [ctypes.POINTER(_vp), _u32, ctypes.POINTER(_ServerOpts), ctypes.POINTER(_vp)]
+        h.lg_server_submit.argtypes = [_vp, ctypes.POINTER(_Request), ctypes.POINTER(_u64)]
+        h.lg_server_wait.argtypes = [_vp, ctypes.POINTER(_Result), _u32, ctypes.POINTER(_u32), _u32]
+        h.lg_server_release.argtypes = [_vp, _u64]
+        h.lg_server_stats_get.argtypes = [_vp, ctypes.POINTER(_ServerStats)]
+        h.lg_server_replay.argtypes = [_vp, _u64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                       ctypes.POINTER(_ReplayStats)]
+        h.lg_server_engine_time.argtypes = [_vp, _u32, _u32, ctypes.POINTER(_u64), ctypes.POINTER(_u64)]
+        h.lg_server_destroy.argtypes = [_vp]
+        h.lg_server_destroy.restype = None
         for f in ("lg_encode", "lg_stats_get", "lg_arrays_get", "lg_neighbors", "lg_bfs", "lg_pagerank",
                   "lg_pagerank_noalloc", "lg_batch_create", "lg_batch_run", "lg_batch_status",
-                  "lg_batch_info_get"):
+                  "lg_batch_info_get", "lg_server_create", "lg_server_submit", "lg_server_wait",
+                  "lg_server_release", "lg_server_stats_get", "lg_server_replay", "lg_server_engine_time"):
             getattr(h, f).restype = _i32
         _lib = h
     return _lib
@@ -396,3 +439,130 @@ def lg_batch_arrays(b: LgBatch) -> dict:
 
 def lg_batch_free(b: LgBatch) -> None:
     b.free()
+
+
+# --- serving -----------------------------------------------------------------
+
+def _result_arrays(r: _Result):
+    """numpy copies of a result's host data."""
+    if not r.data or r.status != 0:
+        return None
+    buf = (ctypes.c_char * r.bytes).from_address(r.data)
+    raw = np.frombuffer(buf, dtype=np.uint8).copy()
+    if r.kind == LG_REQ_NEIGHBORS:
+        off = raw[:(r.count + 1) * 8].view(np.uint64)
+        return off, raw[(r.count + 1) * 8:].view(np.uint32)
+    if r.kind == LG_REQ_BFS:
+        return raw.view(np.uint32)
+    return raw.view(np.float32)
+
+
+class LgServer:
+    """Owner of an lg_server handle (and of references to its graphs)."""
+
+    def __init__(self, handle: int, graphs):
+        self._h = _vp(handle)
+        self.graphs = list(graphs)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def destroy(self):
+        if self._h is not None and self._h.value:
+            load().lg_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def lg_server_create(graphs, device_bytes: int = 0, host_bytes: int = 0, bfs_slots: int = 0, ppr_slots: int = 0,
+                     nbr_batch_vertices: int = 0, ppr_iters: int = 0) -> LgServer:
+    """lg_server_create: serve the given LogGraph objects (kept alive by the server object)."""
+    arr = (_vp * len(graphs))(*[g.handle.value for g in graphs])
+    opts = _ServerOpts(device_bytes, host_bytes, bfs_slots, ppr_slots, nbr_batch_vertices, ppr_iters)
+    h = _vp()
+    _check(load().lg_server_create(arr, len(graphs), ctypes.byref(opts), ctypes.byref(h)), "lg_server_create")
+    return LgServer(h.value, graphs)
+
+
+def lg_server_submit(s: LgServer, kind: int, graph: int, source: int = 0, vertices=None, iters: int = 0,
+                     damping: float = 0.0, user: int = 0) -> int:
+    """lg_server_submit: returns the ticket."""
+    vs = None
+    if vertices is not None:
+        vs = np.ascontiguousarray(vertices, dtype=np.uint32)
+    q = _Request(kind, graph, source, iters, damping, 0 if vs is None else vs.size,
+                 None if vs is None else vs.ctypes.data, user)
+    t = _u64()
+    _check(load().lg_server_submit(s.handle, ctypes.byref(q), ctypes.byref(t)), "lg_server_submit")
+    return t.value
+
+
+def lg_server_wait(s: LgServer, max_results: int = 64, timeout_us: int = 1000000, release: bool = True):
+    """lg_server_wait: list of dicts (ticket, user, kind, graph, status, result
+    arrays, timestamps); results are copied out and released unless
+    ``release`` is False."""
+    buf = (_Result * max_results)()
+    got = _u32()
+    _check(load().lg_server_wait(s.handle, buf, max_results, ctypes.byref(got), timeout_us), "lg_server_wait")
+    out = []
+    for i in range(got.value):
+        r = buf[i]
+        out.append({"ticket": r.ticket, "user": r.user, "kind": r.kind, "graph": r.graph, "status": r.status,
+                    "result": _result_arrays(r), "count": r.count, "t_submit_ns": r.t_submit_ns,
+                    "t_admit_ns": r.t_admit_ns, "t_done_ns": r.t_done_ns})
+        if release:
+            lg_server_release(s, r.ticket)
+    return out
+
+
+def lg_server_release(s: LgServer, ticket: int) -> None:
+    _check(load().lg_server_release(s.handle, ticket), "lg_server_release")
+
+
+def lg_server_stats_get(s: LgServer) -> dict:
+    st = _ServerStats()
+    _check(load().lg_server_stats_get(s.handle, ctypes.byref(st)), "lg_server_stats_get")
+    d = {k: getattr(st, k) for k, _ in _ServerStats._fields_}
+    d["by_kind"] = list(st.by_kind)
+    return d
+
+
+def lg_server_replay(s: LgServer, kind, graph, source, nbr_off, nbr_vertices, arrival_ns, keep=None):
+    """lg_server_replay: open-loop replay of a request trace (numpy columns).
+    ``keep``: optional list of numpy buffers (or None) receiving results.
+    Returns (latency_ns uint64[n], stats dict)."""
+    kind = np.ascontiguousarray(kind, dtype=np.uint32)
+    graph = np.ascontiguousarray(graph, dtype=np.uint32)
+    source = np.ascontiguousarray(source, dtype=np.uint32)
+    nbr_off = np.ascontiguousarray(nbr_off, dtype=np.uint64)
+    nbr_vertices = np.ascontiguousarray(nbr_vertices, dtype=np.uint32)
+    arrival_ns = np.ascontiguousarray(arrival_ns, dtype=np.uint64)
+    n = kind.size
+    lat = np.zeros(n, dtype=np.uint64)
+    keep_arr = None
+    if keep is not None:
+        keep_arr = (_vp * n)(*[None if k is None else k.ctypes.data for k in keep])
+    st = _ReplayStats()
+    rc = load().lg_server_replay(s.handle, n, kind.ctypes.data, graph.ctypes.data, source.ctypes.data,
+                                 nbr_off.ctypes.data, nbr_vertices.ctypes.data if nbr_vertices.size else None,
+                                 arrival_ns.ctypes.data, keep_arr, lat.ctypes.data, ctypes.byref(st))
+    _check(rc, "lg_server_replay")
+    return lat, {"completed": st.completed, "failed": st.failed, "makespan_ns": st.makespan_ns}
+
+
+def lg_server_engine_time(s: LgServer, graph: int, kind: int):
+    """(operations run, device nanoseconds) of one engine (CUDA events on its stream)."""
+    ops, ns = _u64(), _u64()
+    _check(load().lg_server_engine_time(s.handle, graph, kind, ctypes.byref(ops), ctypes.byref(ns)),
+           "lg_server_engine_time")
+    return ops.value, ns.value
+
+
+def lg_server_destroy(s: LgServer) -> None:
+    s.destroy()

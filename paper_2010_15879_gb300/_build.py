@@ -29,6 +29,7 @@ SOURCES = [
     "lg_trav_csr32.cu",
     "lg_static.cu",
     "lg_batch.cu",
+    "lg_serve.cu",
 ]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]

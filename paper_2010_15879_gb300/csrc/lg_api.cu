@@ -158,6 +158,25 @@ cudaError_t pr_finish_multi(const GView& g, const PrArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+__global__ void k_ppr_finish_multi(GView g, PprArgs a) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.n_multi; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t first = g.multi[i];
+    const HeavyItem h = g.items[first];
+    float s[PPR_K];
+    for (int k = 0; k < PPR_K; k++) s[k] = 0.f;
+    for (uint32_t j = 0; j < h.nitems; j++)
+      for (int k = 0; k < PPR_K; k++) s[k] += a.part[(uint64_t)(first + j) * PPR_K + k];
+    ppr_finish(a, h.v, h.deg, s);
+  }
+}
+
+cudaError_t ppr_finish_multi(const GView& g, const PprArgs& a, cudaStream_t st) {
+  if (g.n_multi == 0) return cudaSuccess;
+  k_ppr_finish_multi<<<grid_for(g.n_multi, 256, 4096), 256, 0, st>>>(g, a);
+  count_launch();
+  return cudaGetLastError();
+}
+
 template <typename M>
 __global__ void k_bfs_finish_multi(GView g, BfsArgs a) {
   M* hacc = reinterpret_cast<M*>(a.hacc);

@@ -140,6 +140,14 @@ __device__ __forceinline__ float ldg_gather(const float* p, uint64_t pol) {
   asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
   return v;
 }
+// four consecutive floats (16-byte aligned), same policy
+__device__ __forceinline__ float4 ldg_gather4(const float* p, uint64_t pol) {
+  float4 v;
+  asm("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+      : "l"(p), "l"(pol));
+  return v;
+}
 __device__ __forceinline__ uint16_t ldg_gather(const uint16_t* p, uint64_t) { return __ldg(p); }
 __device__ __forceinline__ uint32_t ldg_gather(const uint32_t* p, uint64_t) { return __ldg(p); }
 __device__ __forceinline__ uint64_t ldg_gather(const uint64_t* p, uint64_t) {

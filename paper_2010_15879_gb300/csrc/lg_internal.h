@@ -128,6 +128,8 @@ struct BfsArgs {
   const void* front_in;      // frontier masks of this level [n]
   void* front_out;           // frontier masks of the next level [n] (zero before a push level)
   uint32_t* depth;           // S x n depths in stored labels
+  uint32_t* const* rows;     // or, if not null, one depth row per source (device array of S pointers)
+  const uint32_t* row_base;  // with rows: level at which each source joined (depth = level - base)
   uint64_t all_mask;         // bits of the active sources
   uint32_t S;
   uint32_t level;            // depth of the current frontier
@@ -137,6 +139,21 @@ struct BfsArgs {
   uint32_t* counters;        // [0] next queue length, [1] new (vertex, source) pairs
   void* hacc;                // per split vertex: OR of its items' frontier masks
   int* err;
+};
+
+// Personalized PageRank for up to PPR_K requests at once (the serving
+// engine): contributions are PPR_K floats per vertex, slot k of vertex v at
+// [v * PPR_K + k], so one 32-byte sector gather serves every slot.
+constexpr int PPR_K = 8;
+struct PprArgs {
+  const float* cin;          // [n][PPR_K] r_{t-1}[u] / d_u per slot
+  float* cout;               // [n][PPR_K]; slots not in `active` are written 0
+  float* part;               // [n_items][PPR_K] partial sums of split vertices
+  uint32_t active;           // slots iterating in this launch
+  uint32_t last;             // slots whose final ranks are written to result[k]
+  uint32_t src[PPR_K];       // personalization vertex of each slot (stored label)
+  float damp[PPR_K];
+  float* result[PPR_K];      // n floats each (slots in `last`)
 };
 
 struct NbrArgs {
@@ -158,11 +175,14 @@ struct TravOps {
   cudaError_t (*plan_count)(const GView&, const PlanArgs&, cudaStream_t);
   cudaError_t (*plan_fill)(const GView&, const PlanArgs&, cudaStream_t);
   cudaError_t (*plan_carry)(const GView&, const PlanArgs&, cudaStream_t);
+  cudaError_t (*ppr_pull)(const GView&, const PprArgs&, cudaStream_t);
+  cudaError_t (*ppr_join)(const GView&, float* cin, uint32_t slot, uint32_t src, cudaStream_t);
 };
 
 // finishing kernels for vertices split into several heavy items (lg_api.cu)
 cudaError_t pr_finish_multi(const GView& g, const PrArgs& a, cudaStream_t st);
 cudaError_t bfs_finish_multi(const GView& g, const BfsArgs& a, int mask_bytes, cudaStream_t st);
+cudaError_t ppr_finish_multi(const GView& g, const PprArgs& a, cudaStream_t st);
 cudaError_t plan_carry_scan(HeavyItem* items, const uint32_t* multi, uint64_t n_multi, const uint32_t* segsum,
                             cudaStream_t st);
 

@@ -54,13 +54,17 @@ template <> __device__ __forceinline__ uint64_t atomic_or_mask<uint64_t>(uint64_
   return (uint64_t)atomicOr(reinterpret_cast<unsigned long long*>(p), (unsigned long long)m);
 }
 
+// depth of v for every source in bitsv: row s of the S x n array, or row
+// rows[s] when the caller keeps one separate row per source (a source that
+// joined a running sweep at level row_base[s] counts depths from there)
 template <typename M>
-__device__ __forceinline__ void write_depths(uint32_t* depth, uint64_t n, uint64_t v, M bitsv, uint32_t d) {
+__device__ __forceinline__ void write_depths(const BfsArgs& a, uint64_t n, uint64_t v, M bitsv, uint32_t d) {
   uint64_t b = (uint64_t)bitsv;
   while (b) {
     const int s = __ffsll((long long)b) - 1;
     b &= b - 1;
-    depth[(uint64_t)s * n + v] = d;
+    if (a.rows) a.rows[s][v] = d - a.row_base[s];
+    else a.depth[(uint64_t)s * n + v] = d;
   }
 }
 
@@ -378,7 +382,7 @@ __device__ __forceinline__ void pr_finish(const GView& g, const PrArgs& a, uint6
 // One launch = one iteration.  Blocks [0, HB) take the heavy schedule (a warp
 // per item); the other blocks take one tile of 512 vertices each.
 template <int IDM, int OFF>
-__global__ void __launch_bounds__(TNT, 6) k_pr_pull(GView g, PrArgs a) {
+__global__ void __launch_bounds__(TNT, (IDM == ID_LOCAL || IDM == ID_CSR32) ? 5 : 6) k_pr_pull(GView g, PrArgs a) {
   __shared__ TileSmem sm;
   const float* __restrict__ c = a.contrib_in;
   const unsigned hb = heavy_blocks(g.n_items);
@@ -422,26 +426,316 @@ __global__ void __launch_bounds__(TNT, 6) k_pr_pull(GView g, PrArgs a) {
   for (int i = threadIdx.x; i < cnt; i += TNT)
     if (sm.deg[i] == 0) pr_finish(g, a, v0 + i, 0, 0.0f);
 
-  // light vertices: sequential decode of contiguous runs, 4 gathers in flight
-  uint32_t jb, je;
-  light_range(sm, jb, je);
-  for (uint32_t j = jb; j < je; j++) {
-    const int i = sm.clist[j];
-    const uint32_t d = sm.deg[i];
-    SeqDec<IDM> dec;
-    dec.init(g, sm.st[i], sm.wid[i], pstream);
-    float s0 = 0.f, s1 = 0.f;
-    uint32_t k = 0;
-    for (; k + 4 <= d; k += 4) {  // four gathers in flight
-      const uint32_t u0 = dec.next(), u1 = dec.next(), u2 = dec.next(), u3 = dec.next();
-      const float f0 = ldg_gather(c + u0, pkeep), f1 = ldg_gather(c + u1, pkeep);
-      const float f2 = ldg_gather(c + u2, pkeep), f3 = ldg_gather(c + u3, pkeep);
-      s0 += f0 + f1;
-      s1 += f2 + f3;
+  if (IDM == ID_LOCAL_GAP) {
+    // gap-coded IDs cannot start mid-neighborhood: runs of whole vertices,
+    // sequential decode, 4 gathers in flight
+    uint32_t jb, je;
+    light_range(sm, jb, je);
+    for (uint32_t j = jb; j < je; j++) {
+      const int i = sm.clist[j];
+      const uint32_t d = sm.deg[i];
+      SeqDec<IDM> dec;
+      dec.init(g, sm.st[i], sm.wid[i], pstream);
+      float s0 = 0.f, s1 = 0.f;
+      uint32_t k = 0;
+      for (; k + 4 <= d; k += 4) {
+        const uint32_t u0 = dec.next(), u1 = dec.next(), u2 = dec.next(), u3 = dec.next();
+        const float f0 = ldg_gather(c + u0, pkeep), f1 = ldg_gather(c + u1, pkeep);
+        const float f2 = ldg_gather(c + u2, pkeep), f3 = ldg_gather(c + u3, pkeep);
+        s0 += f0 + f1;
+        s1 += f2 + f3;
+      }
+      for (; k < d; k++) s0 += ldg_gather(c + dec.next(), pkeep);
+      pr_finish(g, a, v0 + i, d, s0 + s1);
     }
-    for (; k < d; k++) s0 += ldg_gather(c + dec.next(), pkeep);
-    pr_finish(g, a, v0 + i, d, s0 + s1);
+    return;
   }
+  // Fields-balanced light phase (as in k_ppr_pull): thread t decodes fields
+  // [F*t/TNT, F*(t+1)/TNT) of the tile's light fields, entering its first
+  // vertex mid-neighborhood if need be; per-vertex sums go to vsum, the
+  // partial sum of a vertex entered mid-way to carry[t]; a uniform phase adds
+  // them per vertex in thread order and finishes the vertex.
+  __shared__ float vsum[TV];
+  __shared__ float carry[TNT];
+  float* ps = nullptr;
+  const uint32_t F = sm.nfields, nl = sm.nlight;
+  const uint32_t flo = (uint32_t)((uint64_t)F * threadIdx.x / TNT);
+  const uint32_t fhi = (uint32_t)((uint64_t)F * (threadIdx.x + 1) / TNT);
+  carry[threadIdx.x] = 0.f;
+  if (flo < fhi) {
+    uint32_t lo = 0, hi = nl - 1;  // the vertex holding field flo: last j with fpre[j] <= flo
+    while (lo < hi) {
+      const uint32_t m = (lo + hi + 1) >> 1;
+      if (sm.fpre[m] <= flo) lo = m; else hi = m - 1;
+    }
+    uint32_t j = lo, f = flo;
+    ps = sm.fpre[j] < flo ? &carry[threadIdx.x] : &vsum[j];
+    while (f < fhi) {
+      const int i = sm.clist[j];
+      const uint32_t vend = min(sm.fpre[j + 1], fhi);
+      const uint32_t fw = IDM == ID_GLOBAL ? g.r : (IDM == ID_CSR32 ? 32u : (uint32_t)sm.wid[i]);
+      SeqDec<IDM> dec;
+      dec.init(g, sm.st[i] + (uint64_t)(f - sm.fpre[j]) * fw, sm.wid[i], pstream);
+      const uint32_t d = vend - f;
+      float s0 = 0.f, s1 = 0.f;
+      uint32_t k = 0;
+      for (; k + 4 <= d; k += 4) {  // four gathers in flight
+        const uint32_t u0 = dec.next(), u1 = dec.next(), u2 = dec.next(), u3 = dec.next();
+        const float f0 = ldg_gather(c + u0, pkeep), f1 = ldg_gather(c + u1, pkeep);
+        const float f2 = ldg_gather(c + u2, pkeep), f3 = ldg_gather(c + u3, pkeep);
+        s0 += f0 + f1;
+        s1 += f2 + f3;
+      }
+      for (; k < d; k++) s0 += ldg_gather(c + dec.next(), pkeep);
+      *ps = s0 + s1;
+      f = vend;
+      j++;
+      ps = &vsum[j];
+    }
+  }
+  __syncthreads();
+  for (uint32_t j = threadIdx.x; j < nl; j += TNT) {
+    const uint32_t fs = sm.fpre[j], fe = sm.fpre[j + 1];
+    float sum = vsum[j];
+    uint32_t q = (uint32_t)((uint64_t)fs * TNT / (F ? F : 1));  // the thread holding the first field
+    while (q + 1 < TNT && (uint32_t)((uint64_t)F * (q + 1) / TNT) <= fs) q++;
+    while (q > 0 && (uint32_t)((uint64_t)F * q / TNT) > fs) q--;
+    for (q = q + 1; q < TNT && (uint32_t)((uint64_t)F * q / TNT) < fe; q++) sum += carry[q];
+    const int i = sm.clist[j];
+    pr_finish(g, a, v0 + i, sm.deg[i], sum);
+  }
+}
+
+// ===========================================================================
+// Personalized PageRank, PPR_K requests per sweep (serving engine).  Slot k
+// iterates r_t[v] = (1-d_k)[v == s_k] + d_k * sum_{u in N_v} r_{t-1}[u] / d_u;
+// the same tile / heavy-item structure as k_pr_pull, with PPR_K sums per
+// vertex and one 32-byte gather per arc for all slots.
+// ===========================================================================
+__device__ __forceinline__ void ppr_finish(const PprArgs& a, uint64_t v, uint32_t d, const float (&sum)[PPR_K]) {
+  float out[PPR_K];
+#pragma unroll
+  for (int k = 0; k < PPR_K; k++) {
+    const bool act = (a.active >> k) & 1u;
+    const float r = ((uint64_t)a.src[k] == v ? 1.0f - a.damp[k] : 0.0f) + a.damp[k] * sum[k];
+    out[k] = (act && d) ? r / (float)d : 0.0f;
+    if (act && ((a.last >> k) & 1u)) a.result[k][v] = r;
+  }
+  float4* o = reinterpret_cast<float4*>(a.cout + v * PPR_K);
+  __stcs(o, make_float4(out[0], out[1], out[2], out[3]));
+  __stcs(o + 1, make_float4(out[4], out[5], out[6], out[7]));
+}
+
+// half h of the slots (4 of them) for vertex v, written by one lane of a pair
+__device__ __forceinline__ void ppr_finish_half(const PprArgs& a, uint64_t v, uint32_t d, const float4& sum, int h) {
+  const float sv[4] = {sum.x, sum.y, sum.z, sum.w};
+  float out[4];
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    const int k = h * 4 + q;
+    const bool act = (a.active >> k) & 1u;
+    const float r = ((uint64_t)a.src[k] == v ? 1.0f - a.damp[k] : 0.0f) + a.damp[k] * sv[q];
+    out[q] = (act && d) ? r / (float)d : 0.0f;
+    if (act && ((a.last >> k) & 1u)) a.result[k][v] = r;
+  }
+  __stcs(reinterpret_cast<float4*>(a.cout + v * PPR_K + h * 4), make_float4(out[0], out[1], out[2], out[3]));
+}
+
+__device__ __forceinline__ void add4(float4& s, const float4& x) {
+  s.x += x.x; s.y += x.y; s.z += x.z; s.w += x.w;
+}
+
+// range of compacted light vertices owned by lane pair `p` of `np` pairs
+__device__ __forceinline__ void light_range_of(const TileSmem& sm, uint32_t p, uint32_t np, uint32_t& jb,
+                                               uint32_t& je) {
+  const uint64_t F = sm.nfields;
+  const uint32_t flo = (uint32_t)((F * p) / np);
+  const uint32_t fhi = (uint32_t)((F * (p + 1)) / np);
+  const uint32_t nl = sm.nlight;
+  uint32_t lo = 0, hi = nl;
+  while (lo < hi) { const uint32_t m = (lo + hi) >> 1; if (sm.fpre[m] < flo) lo = m + 1; else hi = m; }
+  jb = lo;
+  hi = nl;
+  while (lo < hi) { const uint32_t m = (lo + hi) >> 1; if (sm.fpre[m] < fhi) lo = m + 1; else hi = m; }
+  je = lo;
+}
+
+// Light vertices are decoded by lane PAIRS: both lanes of a pair walk the
+// same run of neighborhoods, lane h gathering the 16-byte half h of each
+// neighbor's 32-byte slot row, so a pair's two loads of one arc coalesce into
+// one sector and every thread keeps four arcs in flight.
+template <int IDM, int OFF>
+__global__ void __launch_bounds__(TNT, 4) k_ppr_pull(GView g, PprArgs a) {
+  __shared__ TileSmem sm;
+  const float* __restrict__ c = a.cin;
+  const unsigned hb = heavy_blocks(g.n_items);
+  const int lane = threadIdx.x & 31;
+  const uint64_t pstream = policy_stream(), pkeep = policy_keep();
+  if (blockIdx.x < hb) {
+    // heavy item: lane pairs again -- the pair (2i, 2i+1) gathers both halves
+    // of field i of each 16-field round; Kahan-compensated lane sums
+    const uint64_t it = (uint64_t)blockIdx.x * (TNT / 32) + (threadIdx.x >> 5);
+    if (it >= g.n_items) return;
+    const HeavyItem hv = g.items[it];
+    const uint32_t f1 = hv.f0 + hv.nf;
+    const int h = lane & 1;
+    const float* ch = c + h * 4;
+    uint32_t carry = hv.carry;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f), comp = acc;
+    for (uint32_t base = hv.f0; base < f1; base += 64) {
+      uint32_t id[2];
+      warp_ids<IDM, 2>(g, hv.bit, hv.w, base, f1, carry, id);
+      float4 x[4];
+#pragma unroll
+      for (int u = 0; u < 2; u++) {
+#pragma unroll
+        for (int r = 0; r < 2; r++) {
+          const uint32_t from = (uint32_t)(r * 16 + (lane >> 1));
+          const uint32_t fid = __shfl_sync(LG_FULL_MASK, id[u], from);
+          x[u * 2 + r] = (base + 32u * u + from < f1) ? ldg_gather4(ch + (uint64_t)fid * PPR_K, pkeep)
+                                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        float* ap = &acc.x;
+        float* cp = &comp.x;
+        const float* xp = &x[q].x;
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+          const float y = xp[e] - cp[e];
+          const float t = ap[e] + y;
+          cp[e] = (t - ap[e]) - y;
+          ap[e] = t;
+        }
+      }
+    }
+    // sum the 16 lanes of each parity (offsets 16, 8, 4, 2 keep the parity)
+#pragma unroll
+    for (int o = 16; o >= 2; o >>= 1) {
+      acc.x += __shfl_xor_sync(LG_FULL_MASK, acc.x, o);
+      acc.y += __shfl_xor_sync(LG_FULL_MASK, acc.y, o);
+      acc.z += __shfl_xor_sync(LG_FULL_MASK, acc.z, o);
+      acc.w += __shfl_xor_sync(LG_FULL_MASK, acc.w, o);
+    }
+    if (lane < 2) {
+      if (hv.nitems == 1) {
+        ppr_finish_half(a, hv.v, hv.deg, acc, h);
+      } else {
+        float* pp = a.part + it * PPR_K + h * 4;
+        pp[0] = acc.x; pp[1] = acc.y; pp[2] = acc.z; pp[3] = acc.w;
+      }
+    }
+    return;
+  }
+  const uint64_t v0 = (uint64_t)(blockIdx.x - hb) * TV;
+  const int cnt = (int)min((uint64_t)TV, g.n - v0);
+  tile_offsets<OFF>(g, v0, cnt, sm.xs, sm.ts);
+  __syncthreads();
+  tile_classify<IDM>(g, sm, cnt, [](int) { return true; });
+  const float zero[PPR_K] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int i = threadIdx.x; i < cnt; i += TNT)
+    if (sm.deg[i] == 0) ppr_finish(a, v0 + i, 0, zero);
+  const int h = threadIdx.x & 1;
+  const float* ch = c + h * 4;
+  if (IDM == ID_LOCAL_GAP) {
+    // gap-coded IDs cannot start mid-neighborhood: runs of whole vertices
+    uint32_t jb, je;
+    light_range_of(sm, threadIdx.x >> 1, TNT / 2, jb, je);
+    for (uint32_t j = jb; j < je; j++) {
+      const int i = sm.clist[j];
+      const uint32_t d = sm.deg[i];
+      SeqDec<IDM> dec;
+      dec.init(g, sm.st[i], sm.wid[i], pstream);
+      float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0;
+      uint32_t k = 0;
+      for (; k + 4 <= d; k += 4) {
+        const uint32_t u0 = dec.next(), u1 = dec.next(), u2 = dec.next(), u3 = dec.next();
+        const float4 x0 = ldg_gather4(ch + (uint64_t)u0 * PPR_K, pkeep);
+        const float4 x1 = ldg_gather4(ch + (uint64_t)u1 * PPR_K, pkeep);
+        const float4 x2 = ldg_gather4(ch + (uint64_t)u2 * PPR_K, pkeep);
+        const float4 x3 = ldg_gather4(ch + (uint64_t)u3 * PPR_K, pkeep);
+        add4(s0, x0); add4(s1, x1); add4(s0, x2); add4(s1, x3);
+      }
+      for (; k < d; k++) add4(s0, ldg_gather4(ch + (uint64_t)dec.next() * PPR_K, pkeep));
+      add4(s0, s1);
+      ppr_finish_half(a, v0 + i, d, s0, h);
+    }
+    return;
+  }
+  // Fields-balanced light phase: pair w takes fields [F*w/NW, F*(w+1)/NW) of
+  // the tile's compacted light fields, starting mid-neighborhood if need be.
+  // A vertex's sum over the range that contains its first field goes to
+  // vsum[j]; a pair that entered its first vertex mid-way leaves that partial
+  // in carry[w].  A uniform phase then adds, per vertex, vsum and the carries
+  // of the following pairs in pair order (deterministic) and finishes it.
+  __shared__ float4 vsum[TV][2];
+  __shared__ float4 carry[TNT / 2][2];
+  constexpr uint32_t NW = TNT / 2;
+  const uint32_t w = threadIdx.x >> 1;
+  const uint32_t F = sm.nfields, nl = sm.nlight;
+  const uint32_t flo = (uint32_t)((uint64_t)F * w / NW), fhi = (uint32_t)((uint64_t)F * (w + 1) / NW);
+  carry[w][h] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (flo < fhi) {
+    uint32_t lo = 0, hi = nl - 1;  // the vertex holding field flo: last j with fpre[j] <= flo
+    while (lo < hi) {
+      const uint32_t m = (lo + hi + 1) >> 1;
+      if (sm.fpre[m] <= flo) lo = m; else hi = m - 1;
+    }
+    uint32_t j = lo, f = flo;
+    bool head = sm.fpre[j] < flo;
+    while (f < fhi) {
+      const int i = sm.clist[j];
+      const uint32_t vend = min(sm.fpre[j + 1], fhi);
+      const uint32_t off = f - sm.fpre[j];
+      const uint32_t fw = IDM == ID_GLOBAL ? g.r : (IDM == ID_CSR32 ? 32u : (uint32_t)sm.wid[i]);
+      SeqDec<IDM> dec;
+      dec.init(g, sm.st[i] + (uint64_t)off * fw, sm.wid[i], pstream);
+      float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0;
+      const uint32_t d = vend - f;
+      uint32_t k = 0;
+      for (; k + 4 <= d; k += 4) {  // four arcs in flight
+        const uint32_t u0 = dec.next(), u1 = dec.next(), u2 = dec.next(), u3 = dec.next();
+        const float4 x0 = ldg_gather4(ch + (uint64_t)u0 * PPR_K, pkeep);
+        const float4 x1 = ldg_gather4(ch + (uint64_t)u1 * PPR_K, pkeep);
+        const float4 x2 = ldg_gather4(ch + (uint64_t)u2 * PPR_K, pkeep);
+        const float4 x3 = ldg_gather4(ch + (uint64_t)u3 * PPR_K, pkeep);
+        add4(s0, x0); add4(s1, x1); add4(s0, x2); add4(s1, x3);
+      }
+      for (; k < d; k++) add4(s0, ldg_gather4(ch + (uint64_t)dec.next() * PPR_K, pkeep));
+      add4(s0, s1);
+      if (head) carry[w][h] = s0;
+      else vsum[j][h] = s0;
+      head = false;
+      f = vend;
+      j++;
+    }
+  }
+  __syncthreads();
+  for (uint32_t t = threadIdx.x; t < nl * 2; t += TNT) {
+    const uint32_t j = t >> 1;
+    const int hh = (int)(t & 1);
+    const uint32_t fs = sm.fpre[j], fe = sm.fpre[j + 1];
+    float4 sum = vsum[j][hh];
+    // pairs after the owner whose ranges start inside this vertex
+    uint32_t q = (uint32_t)((uint64_t)fs * NW / (F ? F : 1));
+    while (q + 1 < NW && (uint32_t)((uint64_t)F * (q + 1) / NW) <= fs) q++;
+    while (q > 0 && (uint32_t)((uint64_t)F * q / NW) > fs) q--;
+    for (q = q + 1; q < NW && (uint32_t)((uint64_t)F * q / NW) < fe; q++) add4(sum, carry[q][hh]);
+    const int i = sm.clist[j];
+    ppr_finish_half(a, v0 + i, sm.deg[i], sum, hh);
+  }
+}
+
+// a slot joins: its column of `cin` is all zero (the slot was idle for a
+// whole sweep, or the array is fresh); r_0 = e_src gives cin[src] = 1 / d_src
+template <int IDM, int OFF>
+__global__ void __launch_bounds__(32) k_ppr_join(GView g, float* cin, uint32_t slot, uint32_t src) {
+  uint64_t x0, x1, start;
+  uint32_t d, w;
+  offset_pair<OFF>(g, src, x0, x1);
+  vgeo<IDM>(g, x0, x1, start, d, w);
+  if (threadIdx.x == 0) cin[(uint64_t)src * PPR_K + slot] = d ? 1.0f / (float)d : 0.0f;
 }
 
 // ===========================================================================
@@ -456,7 +750,7 @@ __device__ __forceinline__ void bfs_finish(const GView& g, const BfsArgs& a, uin
   fout[v] = nb;
   if (nb) {
     vis[v] = (M)(vis[v] | nb);
-    write_depths<M>(a.depth, g.n, v, nb, a.level + 1);
+    write_depths<M>(a, g.n, v, nb, a.level + 1);
     if (qbuf) {
       qbuf[atomicAdd(qn, 1u)] = (uint32_t)v;
       atomicAdd(pairs, (uint32_t)__popcll((unsigned long long)nb));
@@ -468,7 +762,7 @@ __device__ __forceinline__ void bfs_finish(const GView& g, const BfsArgs& a, uin
 }
 
 template <int IDM, int OFF, typename M>
-__global__ void __launch_bounds__(TNT, 6) k_bfs_pull(GView g, BfsArgs a) {
+__global__ void __launch_bounds__(TNT, IDM == ID_LOCAL_GAP ? 6 : 5) k_bfs_pull(GView g, BfsArgs a) {
   __shared__ TileSmem sm;
   __shared__ M need_sm[TV];
   __shared__ uint32_t qbuf[TV];
@@ -520,25 +814,80 @@ __global__ void __launch_bounds__(TNT, 6) k_bfs_pull(GView g, BfsArgs a) {
   for (int i = threadIdx.x; i < cnt; i += TNT)
     if (sm.deg[i] == 0 || (sm.deg[i] <= g.heavy_min && need_sm[i] == 0)) fout[v0 + i] = 0;
 
-  uint32_t jb, je;
-  light_range(sm, jb, je);
-  for (uint32_t j = jb; j < je; j++) {
-    const int i = sm.clist[j];
-    const uint32_t d = sm.deg[i];
-    const M need = need_sm[i];
-    SeqDec<IDM> dec;
-    dec.init(g, sm.st[i], sm.wid[i], pstream);
-    M acc = 0;
-    uint32_t k = 0;
-    for (; k + 4 <= d; k += 4) {  // early exit once every unvisited source is found
-      const uint32_t u0 = dec.next(), u1 = dec.next(), u2 = dec.next(), u3 = dec.next();
-      acc |= (M)(ldg_gather(fin + u0, pkeep) | ldg_gather(fin + u1, pkeep) | ldg_gather(fin + u2, pkeep) |
-                 ldg_gather(fin + u3, pkeep));
-      if ((M)(acc & need) == need) break;
+  if (IDM == ID_LOCAL_GAP) {
+    // gap-coded IDs: runs of whole vertices (no mid-neighborhood start)
+    uint32_t jb, je;
+    light_range(sm, jb, je);
+    for (uint32_t j = jb; j < je; j++) {
+      const int i = sm.clist[j];
+      const uint32_t d = sm.deg[i];
+      const M need = need_sm[i];
+      SeqDec<IDM> dec;
+      dec.init(g, sm.st[i], sm.wid[i], pstream);
+      M acc = 0;
+      uint32_t k = 0;
+      for (; k + 4 <= d; k += 4) {  // early exit once every unvisited source is found
+        const uint32_t u0 = dec.next(), u1 = dec.next(), u2 = dec.next(), u3 = dec.next();
+        acc |= (M)(ldg_gather(fin + u0, pkeep) | ldg_gather(fin + u1, pkeep) | ldg_gather(fin + u2, pkeep) |
+                   ldg_gather(fin + u3, pkeep));
+        if ((M)(acc & need) == need) break;
+      }
+      if ((M)(acc & need) != need)
+        for (; k < d; k++) acc |= ldg_gather(fin + dec.next(), pkeep);
+      bfs_finish<M>(g, a, v0 + i, need, acc, qbuf, &qn, &newpairs);
     }
-    if ((M)(acc & need) != need)
-      for (; k < d; k++) acc |= ldg_gather(fin + dec.next(), pkeep);
-    bfs_finish<M>(g, a, v0 + i, need, acc, qbuf, &qn, &newpairs);
+  } else {
+    // fields-balanced (as in k_pr_pull): partial ORs of a vertex split over
+    // threads are combined exactly in a uniform phase
+    __shared__ M vor[TV];
+    __shared__ M carry[TNT];
+    const uint32_t F = sm.nfields, nl = sm.nlight;
+    const uint32_t flo = (uint32_t)((uint64_t)F * threadIdx.x / TNT);
+    const uint32_t fhi = (uint32_t)((uint64_t)F * (threadIdx.x + 1) / TNT);
+    carry[threadIdx.x] = 0;
+    if (flo < fhi) {
+      uint32_t lo = 0, hi = nl - 1;
+      while (lo < hi) {
+        const uint32_t m = (lo + hi + 1) >> 1;
+        if (sm.fpre[m] <= flo) lo = m; else hi = m - 1;
+      }
+      uint32_t j = lo, f = flo;
+      M* ps = sm.fpre[j] < flo ? &carry[threadIdx.x] : &vor[j];
+      while (f < fhi) {
+        const int i = sm.clist[j];
+        const M need = need_sm[i];
+        const uint32_t vend = min(sm.fpre[j + 1], fhi);
+        const uint32_t fw = IDM == ID_GLOBAL ? g.r : (IDM == ID_CSR32 ? 32u : (uint32_t)sm.wid[i]);
+        SeqDec<IDM> dec;
+        dec.init(g, sm.st[i] + (uint64_t)(f - sm.fpre[j]) * fw, sm.wid[i], pstream);
+        const uint32_t d = vend - f;
+        M acc = 0;
+        uint32_t k = 0;
+        for (; k + 4 <= d; k += 4) {
+          const uint32_t u0 = dec.next(), u1 = dec.next(), u2 = dec.next(), u3 = dec.next();
+          acc |= (M)(ldg_gather(fin + u0, pkeep) | ldg_gather(fin + u1, pkeep) | ldg_gather(fin + u2, pkeep) |
+                     ldg_gather(fin + u3, pkeep));
+          if ((M)(acc & need) == need) break;
+        }
+        if ((M)(acc & need) != need)
+          for (; k < d; k++) acc |= ldg_gather(fin + dec.next(), pkeep);
+        *ps = acc;
+        f = vend;
+        j++;
+        ps = &vor[j];
+      }
+    }
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < nl; j += TNT) {
+      const uint32_t fs = sm.fpre[j], fe = sm.fpre[j + 1];
+      M acc = vor[j];
+      uint32_t q = (uint32_t)((uint64_t)fs * TNT / (F ? F : 1));
+      while (q + 1 < TNT && (uint32_t)((uint64_t)F * (q + 1) / TNT) <= fs) q++;
+      while (q > 0 && (uint32_t)((uint64_t)F * q / TNT) > fs) q--;
+      for (q = q + 1; q < TNT && (uint32_t)((uint64_t)F * q / TNT) < fe; q++) acc |= carry[q];
+      const int i = sm.clist[j];
+      bfs_finish<M>(g, a, v0 + i, need_sm[i], acc, qbuf, &qn, &newpairs);
+    }
   }
 
   __syncthreads();
@@ -585,7 +934,7 @@ __global__ void __launch_bounds__(256) k_bfs_push(GView g, BfsArgs a) {
           if (nb) {
             const M oldf = atomic_or_mask<M>(fout + u_id, nb);
             app = (oldf == 0);
-            write_depths<M>(a.depth, g.n, u_id, nb, nd);
+            write_depths<M>(a, g.n, u_id, nb, nd);
             pairs += __popcll((unsigned long long)nb);
           }
         }
@@ -820,11 +1169,25 @@ cudaError_t launch_plan_carry(const GView& g, const PlanArgs& p, cudaStream_t st
 }
 
 template <int IDM, int OFF>
+cudaError_t launch_ppr_pull(const GView& g, const PprArgs& a, cudaStream_t st) {
+  k_ppr_pull<IDM, OFF><<<heavy_blocks(g.n_items) + tiles_of(g.n), TNT, 0, st>>>(g, a);
+  count_launch();
+  return cudaGetLastError();
+}
+template <int IDM, int OFF>
+cudaError_t launch_ppr_join(const GView& g, float* cin, uint32_t slot, uint32_t src, cudaStream_t st) {
+  k_ppr_join<IDM, OFF><<<1, 32, 0, st>>>(g, cin, slot, src);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <int IDM, int OFF>
 const TravOps* make_ops() {
   static const TravOps ops = {
       &launch_pr_init<IDM, OFF>,    &launch_pr_pull<IDM, OFF>,     &launch_bfs_pull<IDM, OFF>,
       &launch_bfs_push<IDM, OFF>,   &launch_nbr_degrees<IDM, OFF>, &launch_nbr_decode<IDM, OFF>,
       &launch_plan_count<IDM, OFF>, &launch_plan_fill<IDM, OFF>,   &launch_plan_carry<IDM, OFF>,
+      &launch_ppr_pull<IDM, OFF>,   &launch_ppr_join<IDM, OFF>,
   };
   return &ops;
 }

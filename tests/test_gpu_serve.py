@@ -1,0 +1,247 @@
+"""Serving engine: resident compressed graphs (global IDs + Elias-Fano
+offsets) answering lookups, BFS and personalized PageRank with continuous
+batching.
+
+Every result is checked against the oracle (lookups equal the CSR rows, BFS
+depths equal a FIFO BFS, PageRank within 1e-4 relative of the FP64 oracle's
+personalized PageRank after 10 iterations), and each result of a mixed burst
+is the same as the result of the request run alone.  The mix must really be
+batched: sources join running BFS sweeps and PageRank sweeps, lookups merge.
+Admission by device memory is checked with an arena that holds only a few
+requests at a time.
+"""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+import paper_2010_15879_gb300 as lg
+
+pytestmark = pytest.mark.gpu
+
+PR_RTOL = 1e-4
+ITERS = 10
+SCALES = (10, 12, 14)
+
+
+@pytest.fixture(scope="module")
+def graphs():
+    lg.load(auto_build=True)
+    hs = [gen.rmat(sc, 16, seed=40 + sc) for sc in SCALES]
+    enc = [lg.lg_encode(h.row_ptr, h.col, id_mode=lg.LG_ID_GLOBAL, off_mode=lg.LG_OFF_EF) for h in hs]
+    return hs, enc
+
+
+def check_result(h, kind, source, vertices, res):
+    if kind == lg.LG_REQ_NEIGHBORS:
+        off, ids = res
+        assert off.size == len(vertices) + 1
+        for i, v in enumerate(vertices):
+            assert np.array_equal(ids[off[i]:off[i + 1]], h.col[h.row_ptr[v]:h.row_ptr[v + 1]])
+    elif kind == lg.LG_REQ_BFS:
+        assert np.array_equal(res, oracle.bfs(h.n, h.row_ptr, h.col, int(source)))
+    else:
+        want = oracle.pagerank(h.n, h.row_ptr, h.col, 0.85, ITERS, personalize=int(source))
+        got = res.astype(np.float64)
+        nz = want > 0
+        assert np.all(got[~nz] == 0)
+        rel = np.abs(got[nz] - want[nz]) / want[nz]
+        assert rel.max() <= PR_RTOL, f"PPR max rel err {rel.max():.3e}"
+
+
+def result_bytes(h, kind, count):
+    if kind == lg.LG_REQ_NEIGHBORS:
+        return None  # sized per request below
+    return h.n * 4
+
+
+def test_serve_single_requests(graphs):
+    hs, enc = graphs
+    s = lg.lg_server_create(enc, device_bytes=1 << 30, host_bytes=1 << 29)
+    rng = np.random.default_rng(3)
+    for gi, h in enumerate(hs):
+        deg = np.diff(h.row_ptr)
+        srcs = [int(np.argmax(deg)), int(np.flatnonzero(deg)[rng.integers(0, (deg > 0).sum())])]
+        isolated = np.flatnonzero(deg == 0)
+        if isolated.size:
+            srcs.append(int(isolated[0]))
+        for src in srcs:
+            for kind in (lg.LG_REQ_BFS, lg.LG_REQ_PPR):
+                lg.lg_server_submit(s, kind, gi, source=src)
+                (r,) = lg.lg_server_wait(s, 1, 10_000_000)
+                assert r["status"] == 0 and r["kind"] == kind
+                check_result(h, kind, src, None, r["result"])
+        vs = rng.integers(0, h.n, size=200).astype(np.uint32)
+        vs[0] = np.argmax(deg)
+        lg.lg_server_submit(s, lg.LG_REQ_NEIGHBORS, gi, vertices=vs)
+        (r,) = lg.lg_server_wait(s, 1, 10_000_000)
+        check_result(h, lg.LG_REQ_NEIGHBORS, None, vs, r["result"])
+    st = lg.lg_server_stats_get(s)
+    assert st["failed"] == 0 and st["completed"] == st["submitted"]
+    s.destroy()
+
+
+def run_alone(s, tr, i):
+    k = int(tr.kind[i])
+    vs = tr.nbr_vertices[int(tr.nbr_off[i]):int(tr.nbr_off[i + 1])] if k == 0 else None
+    lg.lg_server_submit(s, k, int(tr.graph[i]), source=int(tr.source[i]), vertices=vs)
+    (r,) = lg.lg_server_wait(s, 1, 30_000_000)
+    assert r["status"] == 0
+    return r["result"]
+
+
+def keep_buffers(hs, tr):
+    """Result buffers for lg_server_replay, sized as lg_result.data."""
+    keep = []
+    for i in range(len(tr)):
+        k, g = int(tr.kind[i]), int(tr.graph[i])
+        if k == 0:
+            vs = tr.nbr_vertices[int(tr.nbr_off[i]):int(tr.nbr_off[i + 1])]
+            deg = np.diff(hs[g].row_ptr)
+            total = int(deg[vs].sum())
+            keep.append(np.zeros((vs.size + 1) * 8 + total * 4, dtype=np.uint8))
+        else:
+            keep.append(np.zeros(hs[g].n * 4, dtype=np.uint8))
+    return keep
+
+
+def parse_kept(buf, kind, count):
+    if kind == 0:
+        off = buf[:(count + 1) * 8].view(np.uint64)
+        return off, buf[(count + 1) * 8:].view(np.uint32)
+    return buf.view(np.uint32) if kind == 1 else buf.view(np.float32)
+
+
+def test_serve_mix_equals_alone(graphs):
+    """A burst of 1,200 mixed requests (60 % lookups, 30 % BFS, 10 % PPR over
+    the three graphs): every result equals the same request run alone, and the
+    engines really batched them."""
+    hs, enc = graphs
+    tr = gen.serve_trace([h.row_ptr for h in hs], 1200, seed=11)
+    s = lg.lg_server_create(enc, device_bytes=2 << 30, host_bytes=1 << 30)
+    alone = [run_alone(s, tr, i) for i in range(len(tr))]
+    s.destroy()
+    s = lg.lg_server_create(enc, device_bytes=2 << 30, host_bytes=1 << 30)
+    keep = keep_buffers(hs, tr)
+    lat, rs = lg.lg_server_replay(s, tr.kind, tr.graph, tr.source, tr.nbr_off, tr.nbr_vertices, tr.arrival_ns,
+                                  keep=keep)
+    st = lg.lg_server_stats_get(s)
+    s.destroy()
+    assert rs["completed"] == len(tr) and rs["failed"] == 0
+    assert np.all(lat > 0)
+    exact_ppr = 0
+    for i in range(len(tr)):
+        k = int(tr.kind[i])
+        count = int(tr.nbr_off[i + 1] - tr.nbr_off[i]) if k == 0 else 0
+        mix = parse_kept(keep[i], k, count)
+        if k == 0:
+            assert np.array_equal(mix[0], alone[i][0]) and np.array_equal(mix[1], alone[i][1]), f"lookup {i}"
+        elif k == 1:
+            assert np.array_equal(mix, alone[i]), f"BFS {i}"
+        else:
+            a = alone[i].astype(np.float64)
+            m = mix.astype(np.float64)
+            nz = a > 0
+            assert np.all(m[~nz] == 0)
+            assert (np.abs(m[nz] - a[nz]) / a[nz]).max() <= PR_RTOL, f"PPR {i}"
+            exact_ppr += int(np.array_equal(mix, alone[i]))
+    # a sample against the oracle
+    for i in range(0, len(tr), 37):
+        k = int(tr.kind[i])
+        vs = tr.nbr_vertices[int(tr.nbr_off[i]):int(tr.nbr_off[i + 1])]
+        check_result(hs[int(tr.graph[i])], k, tr.source[i], vs, alone[i])
+    # continuous batching really happened
+    assert st["bfs_joins_running"] > 0 and st["bfs_max_active"] > 1, st
+    assert st["ppr_joins_running"] > 0 and st["ppr_max_active"] > 1, st
+    assert st["nbr_max_batch"] > 1, st
+    assert exact_ppr == int((tr.kind == 2).sum())  # slots are independent: bit-identical
+
+
+def test_serve_admission_by_device_memory(graphs):
+    """An arena of 256 KiB holds at most four 64 KiB request states of the
+    2^14-vertex graph: every request still completes, correctly, and the arena
+    never overflows."""
+    hs, enc = graphs
+    h = hs[2]
+    s = lg.lg_server_create([enc[2]], device_bytes=256 << 10, host_bytes=256 << 20)
+    deg = np.diff(h.row_ptr)
+    srcs = np.flatnonzero(deg)[:: max(1, (deg > 0).sum() // 40)][:40]
+    tickets = {}
+    for j, src in enumerate(srcs):
+        kind = lg.LG_REQ_BFS if j % 2 == 0 else lg.LG_REQ_PPR
+        tickets[lg.lg_server_submit(s, kind, 0, source=int(src))] = (kind, int(src))
+    got = []
+    while len(got) < len(tickets):
+        got += lg.lg_server_wait(s, 64, 30_000_000)
+    st = lg.lg_server_stats_get(s)
+    s.destroy()
+    for r in got:
+        kind, src = tickets[r["ticket"]]
+        assert r["status"] == 0
+        check_result(h, kind, src, None, r["result"])
+    assert st["device_peak"] <= 256 << 10
+    assert st["admission_waits"] > 0
+    assert st["bfs_max_active"] <= 4 and st["ppr_max_active"] <= 4
+
+
+def test_serve_invalid_requests(graphs):
+    hs, enc = graphs
+    s = lg.lg_server_create(enc[:1], device_bytes=1 << 20, host_bytes=1 << 24)
+    n = hs[0].n
+    bad = [dict(kind=1, graph=1, source=0), dict(kind=1, graph=0, source=n), dict(kind=2, graph=0, source=n + 5),
+           dict(kind=0, graph=0, vertices=np.array([0, n], dtype=np.uint32)), dict(kind=7, graph=0, source=0),
+           dict(kind=2, graph=0, source=0, damping=1.5)]
+    for b in bad:
+        with pytest.raises(lg.LgError) as ei:
+            lg.lg_server_submit(s, **b)
+        assert ei.value.status == 1, b
+    with pytest.raises(lg.LgError) as ei:  # an empty lookup
+        lg.lg_server_submit(s, 0, 0, vertices=np.zeros(0, dtype=np.uint32))
+    assert ei.value.status == 1
+    s.destroy()
+    tiny = lg.lg_server_create(enc[2:], device_bytes=4096, host_bytes=1 << 24)
+    with pytest.raises(lg.LgError) as ei:  # a 64 KiB depth row can never fit a 4 KiB arena
+        lg.lg_server_submit(tiny, 1, 0, source=1)
+    assert ei.value.status == 2
+    tiny.destroy()
+
+
+def test_serve_poisson_trace(graphs):
+    """Open-loop arrivals at a moderate rate: every request completes, latency
+    is positive and the server drains."""
+    hs, enc = graphs
+    tr = gen.serve_trace([h.row_ptr for h in hs], 2000, seed=5).at_rate(4000.0, seed=5)
+    s = lg.lg_server_create(enc, device_bytes=2 << 30, host_bytes=1 << 30)
+    lat, rs = lg.lg_server_replay(s, tr.kind, tr.graph, tr.source, tr.nbr_off, tr.nbr_vertices, tr.arrival_ns)
+    st = lg.lg_server_stats_get(s)
+    s.destroy()
+    assert rs["completed"] == 2000 and rs["failed"] == 0
+    assert np.all(lat > 0) and st["host_used"] == 0
+    assert rs["makespan_ns"] >= int(tr.arrival_ns[-1])
+
+
+@pytest.mark.parametrize("id_mode,off_mode", [(lg.LG_ID_GLOBAL, lg.LG_OFF_PACKED), (lg.LG_ID_LOCAL, lg.LG_OFF_EF),
+                                              (lg.LG_ID_LOCAL_GAP, lg.LG_OFF_EF), (lg.LG_ID_CSR32, 0)])
+def test_serve_all_modes(graphs, id_mode, off_mode):
+    """The serving kernels in every ID / offset mode: 16 BFS and 16 PPR
+    requests (two PPR sweeps of 8 slots), hubs and low-degree sources."""
+    hs, _ = graphs
+    h = hs[2]
+    g = lg.lg_encode(h.row_ptr, h.col, id_mode=id_mode, off_mode=off_mode)
+    s = lg.lg_server_create([g], device_bytes=1 << 30, host_bytes=1 << 29)
+    deg = np.diff(h.row_ptr)
+    order = np.argsort(-deg)
+    srcs = np.concatenate([order[:6], np.flatnonzero(deg)[::997][:10]]).astype(np.uint32)
+    tickets = {}
+    for src in srcs:
+        for kind in (lg.LG_REQ_BFS, lg.LG_REQ_PPR):
+            tickets[lg.lg_server_submit(s, kind, 0, source=int(src))] = (kind, int(src))
+    got = []
+    while len(got) < len(tickets):
+        got += lg.lg_server_wait(s, 64, 30_000_000)
+    s.destroy()
+    g.free()
+    for r in got:
+        kind, src = tickets[r["ticket"]]
+        assert r["status"] == 0
+        check_result(h, kind, src, None, r["result"])
