@@ -782,6 +782,35 @@ def run_reference_serve(args, rank, world):
             "e2e": {"value": v, "unit": "req/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}, rank
 
 
+def profile_serve(args):
+    """Untimed serving pass for profilers: the 2^24 graph of the serve
+    workload alone, 16 personalized PageRank requests (two full 8-slot sweeps
+    of 10 iterations), then 64 BFS and 64 lookups."""
+    import paper_2010_15879_gb300 as lg
+
+    lg.load(auto_build=True)
+    rp, col, _ = gen.rmat_gpu(SERVE_SCALES[-1], 16, seed=SERVE_SEED)
+    g = lg.lg_encode(rp, col, id_mode=0, off_mode=1)
+    rph = rp.cpu().numpy().view(np.uint64)
+    del rp, col
+    srv = lg.lg_server_create([g], device_bytes=8 << 30, host_bytes=4 << 30)
+    nz = np.flatnonzero(np.diff(rph) > 0)
+    rng = np.random.default_rng(SERVE_SEED)
+    for kind, count in ((2, 16), (1, 64), (0, 64)):
+        for _ in range(count):
+            if kind == 0:
+                lg.lg_server_submit(srv, 0, 0, vertices=rng.integers(0, len(rph) - 1, 128).astype(np.uint32))
+            else:
+                lg.lg_server_submit(srv, kind, 0, source=int(nz[rng.integers(0, nz.size)]))
+        got = 0
+        while got < count:
+            got += len(lg.lg_server_wait(srv, 64, 30_000_000))
+    ops, ns = lg.lg_server_engine_time(srv, 0, 2)
+    log(f"profile serve: {ops} PageRank sweeps, {ns / 1e3 / max(ops, 1):.0f} us each")
+    srv.destroy()
+    g.free()
+
+
 def run_reference(args, rank, world):
     import torch
 
@@ -866,6 +895,8 @@ def main():
     if args.profile:
         if args.workload == "batch":
             profile_batch(args)
+        elif args.workload == "serve":
+            profile_serve(args)
         else:
             profile_pass(args)
         return

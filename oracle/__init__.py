@@ -74,6 +74,8 @@ def _lib():
                 getattr(h, f).restype = _u64
             h.orc_bfs.argtypes = [_u64, _p(_u64), _p(_u32), _u32, _p(_u32)]
             h.orc_bfs.restype = _i32
+            h.orc_sssp.argtypes = [_u64, _p(_u64), _p(_u32), _p(_u32), _u32, _p(_u64)]
+            h.orc_sssp.restype = _i32
             h.orc_pagerank.argtypes = [_u64, _p(_u64), _p(_u32), _dbl, _u32, _i64, _p(_dbl)]
             h.orc_pagerank.restype = _i32
             h.orc_pagerank_threads.argtypes = [_u64, _p(_u64), _p(_u32), _dbl, _u32, _i64, _p(_dbl), _i32]
@@ -197,6 +199,19 @@ def bfs(n, row_ptr, col, src: int) -> np.ndarray:
     rc = _lib().orc_bfs(n, _ptr(rp, _u64), _ptr(cl, _u32), src, _ptr(out, _u32))
     if rc != 0:
         raise OracleError(rc, "orc_bfs")
+    return out
+
+
+def sssp(n, row_ptr, col, weights, src: int) -> np.ndarray:
+    """Shortest-path distances (uint64, UINT64_MAX = unreachable) from src on the
+    weighted input CSR, by Dijkstra's algorithm."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.uint64)
+    cl = np.ascontiguousarray(col, dtype=np.uint32)
+    wt = np.ascontiguousarray(weights, dtype=np.uint32)
+    out = np.zeros(n, dtype=np.uint64)
+    rc = _lib().orc_sssp(n, _ptr(rp, _u64), _ptr(cl, _u32), _ptr(wt, _u32), src, _ptr(out, _u64))
+    if rc != 0:
+        raise OracleError(rc, "orc_sssp")
     return out
 
 

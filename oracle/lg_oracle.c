@@ -25,7 +25,8 @@
  *     vector stored with Elias-Fano (Elias 1974, Fano 1971; Okanohara-Sadakane
  *     2007), select(j) = the j-th one = the start of A_j (Section 4.1).
  *   - Section 5.6 (DM permuter): a higher degree gives a smaller label.
- *   - Section 7.1.2: BFS (depth per vertex) and PageRank without atomics.
+ *   - Section 7.1.2: BFS (depth per vertex), PageRank without atomics, and
+ *     SSSP (shortest-path distances; computed here by Dijkstra).
  *
  * Readings of silent or ambiguous points (the CUDA path follows the same ones):
  *   IDs are 0-based; bits(x) = 0 for x = 0, else floor(log2 x) + 1, so
@@ -531,6 +532,64 @@ int orc_bfs(uint64_t n, const uint64_t *rp, const uint32_t *col, uint32_t src, u
         }
     }
     free(queue);
+    return ORC_OK;
+}
+
+/* Single-source shortest paths on the weighted INPUT csr (Section 7.1.2
+   "SSSP"; the paper runs GAPBS's delta-stepping, whose result is the plain
+   shortest-path distance): dist[v] = minimum over paths src -> v of the sum of
+   the arc weights, UINT64_MAX if unreachable.  Dijkstra's algorithm with a
+   binary heap of (distance, vertex) entries and lazy deletion; weights >= 0. */
+typedef struct { uint64_t d; uint32_t v; } orc_heap_entry;
+
+static void heap_push(orc_heap_entry *h, uint64_t *len, uint64_t d, uint32_t v) {
+    uint64_t i = (*len)++;
+    while (i > 0) {
+        uint64_t p = (i - 1) / 2;
+        if (h[p].d <= d) break;
+        h[i] = h[p];
+        i = p;
+    }
+    h[i].d = d;
+    h[i].v = v;
+}
+
+static orc_heap_entry heap_pop(orc_heap_entry *h, uint64_t *len) {
+    orc_heap_entry top = h[0], last = h[--(*len)];
+    uint64_t i = 0;
+    for (;;) {
+        uint64_t c = 2 * i + 1;
+        if (c >= *len) break;
+        if (c + 1 < *len && h[c + 1].d < h[c].d) c++;
+        if (h[c].d >= last.d) break;
+        h[i] = h[c];
+        i = c;
+    }
+    if (*len) h[i] = last;
+    return top;
+}
+
+int orc_sssp(uint64_t n, const uint64_t *rp, const uint32_t *col, const uint32_t *w, uint32_t src, uint64_t *dist) {
+    if (src >= n || !w) return ORC_EINVAL;
+    const uint64_t arcs = rp[n];
+    orc_heap_entry *h = (orc_heap_entry *)malloc(sizeof(orc_heap_entry) * (arcs + 1));
+    if (!h) return ORC_ENOMEM;
+    for (uint64_t v = 0; v < n; v++) dist[v] = UINT64_MAX;
+    uint64_t len = 0;
+    dist[src] = 0;
+    heap_push(h, &len, 0, src);
+    while (len) {
+        orc_heap_entry e = heap_pop(h, &len);
+        if (e.d != dist[e.v]) continue; /* stale entry */
+        for (uint64_t j = rp[e.v]; j < rp[e.v + 1]; j++) {
+            uint64_t nd = e.d + w[j];
+            if (nd < dist[col[j]]) {
+                dist[col[j]] = nd;
+                heap_push(h, &len, nd, col[j]);
+            }
+        }
+    }
+    free(h);
     return ORC_OK;
 }
 
