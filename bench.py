@@ -77,6 +77,10 @@ WORKLOADS["serve"] = ("serving: 3 resident R-MAT graphs (scales 20, 22, 24, edge
                       "sources uniform over vertices of nonzero degree; Poisson arrivals",
                       None, None, 1, 10)
 SERVE_SCALES, SERVE_SEED, SERVE_RATES = (20, 22, 24), 4, (0.25, 0.5, 0.9)
+WORKLOADS["sssp"] = ("SSSP (delta-stepping, delta 32) from 4 sources on R-MAT scale 27, edge factor 16, weights in "
+                     "[1,255] at 8 bits; global 27-bit IDs + Elias-Fano offsets; CSR-32 with 32-bit weights beside it",
+                     None, dict(id_mode=0, off_mode=1, relabel=False, weight_bits=8), 4, 0)
+SSSP_DELTA = 32
 
 
 class Workload:
@@ -646,6 +650,120 @@ def run_serve(args, rank, world):
     return out, rank
 
 
+def sssp_teps(deg_d, dist):
+    """Graph500 counting: (sum of the degrees of the reached vertices) / 2."""
+    return int(deg_d[dist != -1].sum().item()) // 2
+
+
+def run_sssp(args, rank, world):
+    import torch
+
+    import paper_2010_15879_gb300 as lg
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    lg.load(auto_build=True)
+    desc, _, opts, S, _ = WORKLOADS["sssp"]
+    t0 = time.time()
+    rp, col, w = gen.rmat_gpu(27, 16, seed=5, weighted=True)
+    n, arcs = rp.numel() - 1, col.numel()
+    deg_d = rp[1:] - rp[:-1]
+    class _G:
+        pass
+    _G.n, _G.row_ptr = n, rp.cpu().numpy().view(np.uint64)
+    src = gen.sources(_G, S, seed=7)
+    log(f"generated rmat_s27_ef16_seed5 weighted: n={n} arcs={arcs} in {time.time() - t0:.1f}s")
+    stream = torch.cuda.current_stream(dev)
+    arms = {}
+    for name, o in (("log(graph)", opts), ("csr32", dict(id_mode=3))):
+        g = lg.lg_encode(rp, col, w, **o)
+        st = g.stats()
+        dist = torch.empty(n, dtype=torch.int64, device=dev)
+        te = 0
+        for s_ in src:  # TEPS accounting, untimed
+            lg.lg_sssp(g, int(s_), SSSP_DELTA, out=dist)
+            te += sssp_teps(deg_d, dist)
+        for _ in range(args.warmup):
+            lg.lg_sssp(g, int(src[0]), SSSP_DELTA, out=dist)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = lg.lg_kernel_launches()
+        with ClockSampler(dev.index) as clk:
+            e0.record(stream)
+            for _ in range(args.steps):
+                for s_ in src:
+                    lg.lg_sssp(g, int(s_), SSSP_DELTA, out=dist)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / args.steps
+        arms[name] = dict(ms=ms, te=te, stats=st, launches=lg.lg_kernel_launches() - l0, clocks=clk.summary())
+        log(f"[rank {rank}] {name}: {S} SSSP in {ms:.1f} ms = {te / (ms * 1e-3) / 1e9:.2f} GTEPS")
+        g.free()
+    lgarm, csr = arms["log(graph)"], arms["csr32"]
+    # e2e: weighted CSR from pinned host memory, encode, the 4 SSSP, distances back
+    rp_p, col_p, w_p = rp.cpu().pin_memory(), col.cpu().pin_memory(), w.cpu().pin_memory()
+    out_p = torch.empty(S * n, dtype=torch.int64).pin_memory()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rp.copy_(rp_p, non_blocking=True)
+    col.copy_(col_p, non_blocking=True)
+    w.copy_(w_p, non_blocking=True)
+    g = lg.lg_encode(rp, col, w, **opts)
+    dist = torch.empty(n, dtype=torch.int64, device=dev)
+    for i, s_ in enumerate(src):
+        lg.lg_sssp(g, int(s_), SSSP_DELTA, out=dist)
+        out_p[i * n:(i + 1) * n].copy_(dist, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = e0.elapsed_time(e1)
+    g.free()
+    st = lgarm["stats"]
+    step_ms, e2e_ms, value, e2e_value = combine_replicas(lgarm["ms"], e2e_ms, lgarm["te"], world, dev)
+    alg = S * ((st["bits_A"] + st["bits_O"]) // 8 + 8 * arcs + 8 * n)
+    peak, peak_kind = peaks()
+    achieved = alg / (step_ms * 1e-3) / 1e9
+    out = {
+        "metric": "GTEPS (SSSP delta-stepping from 4 sources, Log(Graph) compressed weighted graph, Graph500 counting)",
+        "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64 distances, 8-bit weights", "data": "synthetic (seeded generator; no dataset)",
+        "config": {"workload": desc, "n": n, "arcs": arcs, "sources": S, "delta": SSSP_DELTA,
+                   "l2": "inputs larger than L2 (weighted CSR %.1f GB)" % ((n + 1) * 8 / 1e9 + arcs * 8 / 1e9),
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": e2e_value, "unit": "GTEPS", "ms_per_step": e2e_ms, "note": "includes the encode",
+                "h2d_bytes_per_step": (n + 1) * 8 + arcs * 8, "d2h_bytes_per_step": S * n * 8},
+        "gpu_launches": int(lgarm["launches"] // max(args.steps, 1)),
+        "detail": {"csr32": {"ms": csr["ms"], "gteps": csr["te"] / (csr["ms"] * 1e-3) / 1e9},
+                   "speedup_vs_csr32": csr["ms"] / lgarm["ms"], "bits_per_arc": st["bits_per_arc"],
+                   "bytes_vs_weighted_csr32": ((st["bits_A"] + st["bits_O"]) / 8) / (8 * arcs + 8 * (n + 1))},
+        "roofline": {"kernel": "k_sssp_relax (delta-stepping relaxation, decode fused)", "bound": "hbm",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": f"{peak_kind} (copy bandwidth)",
+                     "algorithmic_bytes_per_launch": alg, "note": "per step (4 SSSP): stream + offsets once and "
+                     "one 8-byte distance per arc and vertex per source", "traffic": None},
+        "clocks": lgarm["clocks"],
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_sssp()
+    return out, rank
+
+
+def cpu_baseline_sssp(scale=22):
+    """The oracle's Dijkstra on the same generator at scale 22 (1/32 of the
+    graph), one source: a bounded sample of the SSSP workload."""
+    import oracle
+
+    h = gen.rmat(scale, 16, seed=5, weighted=True)
+    s = int(gen.sources(h, 1, seed=7)[0])
+    t0 = time.time()
+    d = oracle.sssp(h.n, h.row_ptr, h.col, h.weights, s)
+    el = time.time() - t0
+    te = int(h.degrees()[d != np.iinfo(np.uint64).max].sum()) // 2
+    return {"value": te / el / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+            "sample": f"one Dijkstra on R-MAT scale {scale} (same generator, weights, edge factor), {el:.1f} s"}
+
+
 def cpu_baseline_batch(vptr, rp, col, iters, min_seconds=10.0, max_graphs=None):
     """The oracle as it stands (single-threaded C) on a bounded sample of the
     batch: whole graphs in batch order (BFS from vertex 0 + `iters` PageRank
@@ -816,6 +934,18 @@ def run_reference(args, rank, world):
 
     if args.workload == "serve":
         return run_reference_serve(args, rank, world)
+    if args.workload == "sssp":
+        desc = WORKLOADS["sssp"][0]
+        vals = [cpu_baseline_sssp() for _ in range(max(1, args.steps))]
+        v = float(np.mean([x["value"] for x in vals]))
+        return {"impl": "reference", "metric": "GTEPS (SSSP delta-stepping from 4 sources, Log(Graph) compressed "
+                                               "weighted graph, Graph500 counting)",
+                "value": v, "unit": "GTEPS", "n_gpus": world, "steps": args.steps, "warmup": 0,
+                "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "u64 distances", "data": "synthetic (seeded generator)",
+                "config": {"workload": desc, "parallelism": "host cores"},
+                "cpu_baseline": {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": vals[0]["sample"]},
+                "e2e": {"value": v, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}, rank
     if args.workload == "batch":
         desc, _, _, _, T = WORKLOADS["batch"]
         hb = gen.rmat_batch(count=64, seed=BATCH_SEED)  # the batch's first 64 graphs (seeded per graph)
@@ -905,7 +1035,7 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         dist.init_process_group("nccl")
-    runner = {"batch": run_batch, "serve": run_serve}.get(args.workload, run_lg)
+    runner = {"batch": run_batch, "serve": run_serve, "sssp": run_sssp}.get(args.workload, run_lg)
     out, rank = runner(args, rank, world)
     if rank == 0:
         print(json.dumps(out), flush=True)

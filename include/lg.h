@@ -173,6 +173,20 @@ lg_status lg_bfs(const lg_graph *g, const uint32_t *sources, uint32_t S, uint32_
                  void *stream);
 
 /*
+ * lg_sssp -- single-source shortest paths (Section 7.1.2 "SSSP", delta-
+ * stepping) on a weighted graph (weights stored after each ID, Section 3.3),
+ * neighborhoods and weights decoded inside the relaxation kernel.
+ *   source  original ID (< n)
+ *   delta   bucket width (0 = 32); any value gives the same distances
+ *   dist    device, n u64 indexed by original ID: the minimum over paths from
+ *           source of the sum of arc weights, UINT64_MAX if unreachable
+ * Needs a weighted graph in LG_ID_GLOBAL or LG_ID_CSR32 (else
+ * LG_EUNSUPPORTED).  Synchronizes `stream` once per relaxation round (queue
+ * sizes steer the buckets).
+ */
+lg_status lg_sssp(const lg_graph *g, uint32_t source, uint64_t delta, uint64_t *dist, void *stream);
+
+/*
  * lg_pagerank -- pull PageRank without atomics (Section 7.1.2), FP32, exactly
  * `iters` iterations, neighborhoods decoded inside the kernel:
  *   global:        r_0 = 1/n,    r_t[v] = (1-d)/n      + d * sum_{u in N_v} r_{t-1}[u] / d_u

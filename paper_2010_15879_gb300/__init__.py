@@ -28,7 +28,7 @@ from ._build import LIB, build, is_stale
 __all__ = [
     "LG_ID_GLOBAL", "LG_ID_LOCAL", "LG_ID_LOCAL_GAP", "LG_ID_CSR32", "LG_OFF_PACKED", "LG_OFF_EF",
     "LgError", "LogGraph", "build", "load", "lg_encode", "lg_stats_get", "lg_arrays_get", "lg_neighbors",
-    "lg_bfs", "lg_pagerank", "lg_pagerank_noalloc", "lg_free", "lg_last_error", "lg_kernel_launches",
+    "lg_bfs", "lg_sssp", "lg_pagerank", "lg_pagerank_noalloc", "lg_free", "lg_last_error", "lg_kernel_launches",
     "LgBatch", "lg_batch_create", "lg_batch_run", "lg_batch_status", "lg_batch_info_get", "lg_batch_free",
     "LG_BATCH_FLAG_DROP_MEMBER",
     "LG_REQ_NEIGHBORS", "LG_REQ_BFS", "LG_REQ_PPR", "LgServer", "lg_server_create", "lg_server_submit",
@@ -133,6 +133,7 @@ def load(auto_build: bool = False):
         h.lg_arrays_get.argtypes = [_vp, ctypes.POINTER(_Arrays)]
         h.lg_neighbors.argtypes = [_vp, _vp, _u64, _vp, _vp, _vp, _u64, _vp]
         h.lg_bfs.argtypes = [_vp, _vp, _u32, _vp, _vp]
+        h.lg_sssp.argtypes = [_vp, _u32, _u64, _vp, _vp]
         h.lg_pagerank.argtypes = [_vp, _f32, _u32, ctypes.POINTER(_u32), _vp, _vp]
         h.lg_pagerank_noalloc.argtypes = [_vp, _f32, _u32, ctypes.POINTER(_u32), _vp, _vp]
         h.lg_free.argtypes = [_vp]
@@ -158,7 +159,7 @@ def load(auto_build: bool = False):
         h.lg_server_destroy.argtypes = [_vp]
         h.lg_server_destroy.restype = None
         for f in ("lg_encode", "lg_stats_get", "lg_arrays_get", "lg_neighbors", "lg_bfs", "lg_pagerank",
-                  "lg_pagerank_noalloc", "lg_batch_create", "lg_batch_run", "lg_batch_status",
+                  "lg_pagerank_noalloc", "lg_sssp", "lg_batch_create", "lg_batch_run", "lg_batch_status",
                   "lg_batch_info_get", "lg_server_create", "lg_server_submit", "lg_server_wait",
                   "lg_server_release", "lg_server_stats_get", "lg_server_replay", "lg_server_engine_time"):
             getattr(h, f).restype = _i32
@@ -319,6 +320,17 @@ def lg_bfs(g: LogGraph, sources, out: Optional[torch.Tensor] = None, stream=None
     if out is None:
         out = torch.empty((S, n), dtype=torch.int32, device="cuda")
     _check(lib.lg_bfs(g.handle, src.data_ptr() if S else None, S, out.data_ptr(), _stream(stream)), "lg_bfs")
+    return out
+
+
+def lg_sssp(g: LogGraph, source: int, delta: int = 0, out: Optional[torch.Tensor] = None,
+            stream=None) -> torch.Tensor:
+    """lg_sssp: shortest-path distances (n,) as int64 holding uint64 values
+    (UINT64_MAX = -1: unreachable) from `source` on a weighted graph."""
+    n = lg_stats_get(g)["n"]
+    if out is None:
+        out = torch.empty(n, dtype=torch.int64, device="cuda")
+    _check(load().lg_sssp(g.handle, source, delta, out.data_ptr(), _stream(stream)), "lg_sssp")
     return out
 
 

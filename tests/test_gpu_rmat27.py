@@ -9,8 +9,9 @@ The oracle cannot re-encode 1.5e11 bits one at a time within a test, so it is
 compared on what it can compute piece by piece: the whole Elias-Fano offset
 structure, 200 windows of the A stream (first, last and random), 4,000 sampled
 neighborhoods with weights, two of the 16 BFS sources in full (all 16 checked
-for the properties every BFS depth array has), and PageRank after 3
-iterations in full (after 20, the sum rule).
+for the properties every BFS depth array has), PageRank after 3 iterations in
+full (after 20, the sum rule), and SSSP over the 8-bit weights from one source
+in full (Dijkstra) and from three more by the defining properties.
 """
 import numpy as np
 import pytest
@@ -109,3 +110,29 @@ def test_rmat27_pagerank(rmat27):
     isolated = int((np.diff(rp) == 0).sum())
     assert abs(r20.sum() - (1.0 - isolated * 0.85 / n)) < 1e-3
     assert r20.min() >= (1 - 0.85) / n * (1 - 1e-5)
+
+
+def test_rmat27_sssp(rmat27):
+    g, (rp, col, w) = rmat27
+    n = rp.shape[0] - 1
+    deg = np.diff(rp)
+    nz = np.flatnonzero(deg)
+    srcs = [int(nz[12345]), int(np.argmax(deg)), int(nz[-7]), int(nz[len(nz) // 2])]
+    d0 = lg.lg_sssp(g, srcs[0]).cpu().numpy().view(np.uint64)
+    assert np.array_equal(d0, oracle.sssp(n, rp, col, w, srcs[0]))
+    rng = np.random.default_rng(2)
+    arcs_s = rng.integers(0, col.shape[0], size=3_000_000)
+    us = np.searchsorted(rp, arcs_s, side="right") - 1
+    vs = col[arcs_s]
+    ws = w[arcs_s].astype(np.uint64)
+    INF64 = np.iinfo(np.uint64).max
+    for s in srcs[1:]:
+        d = lg.lg_sssp(g, s).cpu().numpy().view(np.uint64)
+        assert d[s] == 0
+        du, dv = d[us], d[vs]
+        reach = du != INF64
+        assert np.all((du == INF64) == (dv == INF64))
+        assert np.all(dv[reach] <= du[reach] + ws[reach])  # no arc shortens a distance
+        depth = oracle.bfs(n, rp, col, s) if s == srcs[1] else None
+        if depth is not None:
+            assert np.array_equal(d != INF64, depth != INF)
