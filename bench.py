@@ -565,7 +565,7 @@ def run_serve(args, rank, world):
     graphs, rps, sizes = [], [], []
     for sc in SERVE_SCALES:
         rp, col, _ = gen.rmat_gpu(sc, 16, seed=SERVE_SEED)
-        g = lg.lg_encode(rp, col, id_mode=0, off_mode=1)
+        g = lg.lg_encode(rp, col, id_mode=0, off_mode=1, relabel=args.serve_relabel)
         st = g.stats()
         graphs.append(g)
         rps.append(rp.cpu().numpy().view(np.uint64))
@@ -629,7 +629,8 @@ def run_serve(args, rank, world):
         "value": sat * world, "unit": "req/s", "n_gpus": world, "steps": nreq, "warmup": 2000,
         "ms_per_step": 1e3 / sat, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u32 ids / fp32 ranks", "data": "synthetic (seeded generator and trace; no dataset)",
-        "config": {"workload": desc, "graphs": sizes, "requests": nreq, "rates_of_saturation": list(SERVE_RATES),
+        "config": {"workload": desc + ("; DM relabel" if args.serve_relabel else "; no relabel"), "graphs": sizes,
+                   "requests": nreq, "rates_of_saturation": list(SERVE_RATES),
                    "l2": "graphs larger than L2 (2^24: %.2f GB compressed)" % ((big["bits_A"] + big["bits_O"]) / 8e9),
                    "parallelism": f"replicas x{world}", "step": "one request"},
         "latency": per_rate,
@@ -908,7 +909,7 @@ def profile_serve(args):
 
     lg.load(auto_build=True)
     rp, col, _ = gen.rmat_gpu(SERVE_SCALES[-1], 16, seed=SERVE_SEED)
-    g = lg.lg_encode(rp, col, id_mode=0, off_mode=1)
+    g = lg.lg_encode(rp, col, id_mode=0, off_mode=1, relabel=args.serve_relabel)
     rph = rp.cpu().numpy().view(np.uint64)
     del rp, col
     srv = lg.lg_server_create([g], device_bytes=8 << 30, host_bytes=4 << 30)
@@ -1010,6 +1011,9 @@ def main():
     ap.add_argument("--pr-iters", type=int, default=None, help="PageRank iterations in --profile mode")
     ap.add_argument("--batch-count", type=int, default=None, help="graphs in --profile mode of the batch workload")
     ap.add_argument("--serve-requests", type=int, default=100000, help="requests per rate (serve workload)")
+    ap.add_argument("--serve-no-relabel", dest="serve_relabel", action="store_false",
+                    help="serve workload: keep the generator's labels (default: DM relabel, Section 5.6, "
+                         "which puts the hubs first for gather locality)")
     args = ap.parse_args()
     if args.warmup < 3:
         log("warmup raised to 3 (timing rule)")

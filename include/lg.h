@@ -411,11 +411,12 @@ typedef struct {
 } lg_replay_stats;
 
 /*
- * lg_server_create -- start serving `count` graphs (encoded with relabel = 0 on
- * the current device; relabeled graphs give LG_EUNSUPPORTED).  Allocates the
- * two arenas and per-graph engine state (BFS masks 24 B and PPR vectors 64 B
- * per vertex) and starts 3 threads per graph.  The graphs must outlive the
- * server.
+ * lg_server_create -- start serving `count` graphs encoded on the current
+ * device.  Requests and results use original IDs; for a DM-relabeled graph
+ * the server keeps a host copy of its permutation and the PageRank sweep keeps
+ * the hubs' rows in L2.  Allocates the two arenas and per-graph engine state
+ * (BFS masks 24 B and PPR vectors 64 B per vertex) and starts 3 threads per
+ * graph.  The graphs must outlive the server.
  */
 lg_status lg_server_create(const lg_graph *const *graphs, uint32_t count, const lg_server_opts *opts,
                            lg_server **out);

@@ -130,6 +130,7 @@ struct BfsArgs {
   uint32_t* depth;           // S x n depths in stored labels
   uint32_t* const* rows;     // or, if not null, one depth row per source (device array of S pointers)
   const uint32_t* row_base;  // with rows: level at which each source joined (depth = level - base)
+  const uint32_t* row_perm;  // with rows: row index of stored vertex v (inv_perm), or null = v
   uint64_t all_mask;         // bits of the active sources
   uint32_t S;
   uint32_t level;            // depth of the current frontier
@@ -154,6 +155,8 @@ struct PprArgs {
   uint32_t src[PPR_K];       // personalization vertex of each slot (stored label)
   float damp[PPR_K];
   float* result[PPR_K];      // n floats each (slots in `last`)
+  const uint32_t* result_perm;  // result index of stored vertex v (inv_perm), or null = v
+  uint32_t hot;              // gathers of rows u < hot are kept in L2 (evict-last), the others evict-first
 };
 
 struct NbrArgs {

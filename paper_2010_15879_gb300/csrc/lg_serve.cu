@@ -46,7 +46,8 @@ constexpr int BFS_SLOTS = 64;
 // ---------------------------------------------------------------- kernels
 // new sources enter the current frontier (one thread: duplicates merge)
 struct JoinItem {
-  uint32_t src, slot;
+  uint32_t src, slot;  // stored label of the source, slot
+  uint32_t orig, pad;  // the source's original ID (its index in the depth row)
 };
 __global__ void k_bfs_join(uint64_t* vis, uint64_t* cur, uint32_t* const* rows, uint32_t* row_base,
                            const JoinItem* joins, uint32_t J, uint32_t level, uint32_t* queue, uint32_t* qlen) {
@@ -58,7 +59,7 @@ __global__ void k_bfs_join(uint64_t* vis, uint64_t* cur, uint32_t* const* rows, 
     if (cur[s] == 0) queue[q++] = s;
     cur[s] |= bit;
     vis[s] |= bit;
-    rows[joins[j].slot][s] = 0;
+    rows[joins[j].slot][joins[j].orig] = 0;
     row_base[joins[j].slot] = level;  // later depths are written as level + 1 - base
   }
   *qlen = q;
@@ -113,6 +114,7 @@ struct Engine;
 struct lg_server {
   int device = 0;
   std::vector<const lg_graph*> graphs;
+  std::vector<std::vector<uint32_t>> perms;  // host copies of relabeled graphs' perm
   lg_server_opts opts{};
   // arenas
   std::mutex mem_mu;
@@ -214,10 +216,14 @@ struct Engine {
     if (t1) cudaEventDestroy(t1);
   }
 
+  const std::vector<uint32_t>* perm_h = nullptr;  // original -> stored label (relabeled graphs)
+
   Engine(lg_server* s, uint32_t i) : srv(s), gi(i), g(s->graphs[i]) {
     view = make_view(g);
     ops = trav_ops((int)g->id_mode, (int)g->off_mode);
+    if (g->perm) perm_h = &s->perms[i];
   }
+  uint32_t stored(uint32_t v) const { return perm_h ? (*perm_h)[v] : v; }
   virtual ~Engine() = default;
   virtual lg_status setup() = 0;
   virtual void loop() = 0;
@@ -378,7 +384,7 @@ struct BfsEngine : Engine {
       slots[s].r = r;
       slots[s].row = row;
       slots[s].join_level = level;
-      joins_h[J++] = JoinItem{r->source, (uint32_t)s};
+      joins_h[J++] = JoinItem{stored(r->source), (uint32_t)s, r->source, 0};
     }
     return J;
   }
@@ -417,6 +423,7 @@ struct BfsEngine : Engine {
     a.front_out = nxt;
     a.rows = rows_dev;
     a.row_base = base_dev;
+    a.row_perm = g->inv_perm;  // rows are indexed by original ID
     a.all_mask = active;
     a.S = BFS_SLOTS;
     a.level = level;
@@ -530,8 +537,13 @@ struct PprEngine : Engine {
   std::deque<std::pair<cudaEvent_t, cudaEvent_t>> markers;  // (start, end) of each queued sweep
   std::vector<cudaEvent_t> free_events, free_timed;
 
+  uint32_t hot;  // rows below this stored label are gathered with evict-last
+
   PprEngine(lg_server* s, uint32_t i) : Engine(s, i), n(g->n) {
     nslots = std::min<uint32_t>(PPR_K, s->opts.ppr_slots ? s->opts.ppr_slots : PPR_K);
+    // DM relabeling puts the hubs first: keep their rows (up to 64 MB) in L2
+    // and stream the others; without relabeling every row is kept
+    hot = g->relabel ? (uint32_t)std::min<uint64_t>(n, (64ull << 20) / (PPR_K * 4)) : (uint32_t)n;
   }
 
   lg_status setup() override {
@@ -660,7 +672,7 @@ struct PprEngine : Engine {
         if (act) srv->ppr_joins_running += joins.size();
         srv->ppr_joins += joins.size();
         for (uint32_t k : joins)
-          if (ops->ppr_join(view, ca, k, slots[k].r->source, st) != cudaSuccess) ok = false;
+          if (ops->ppr_join(view, ca, k, stored(slots[k].r->source), st) != cudaSuccess) ok = false;
       }
       act = active_mask();
       srv->bump_max(srv->ppr_max_active, (uint64_t)__builtin_popcount(act));
@@ -670,12 +682,14 @@ struct PprEngine : Engine {
       a.cout = cb;
       a.part = part;
       a.active = act;
+      a.result_perm = g->inv_perm;  // results indexed by original ID
+      a.hot = hot;
       std::vector<uint32_t> retiring;
       bool was_dirty[PPR_K];
       for (uint32_t k = 0; k < PPR_K; k++) {
         was_dirty[k] = k < nslots && slots[k].state == FREE_DIRTY;
         if (k < nslots && slots[k].state == ACTIVE) {
-          a.src[k] = slots[k].r->source;
+          a.src[k] = stored(slots[k].r->source);
           a.damp[k] = slots[k].r->damping;
           a.result[k] = slots[k].res;
           if (slots[k].t + 1 == slots[k].r->iters) {
@@ -999,12 +1013,17 @@ extern "C" lg_status lg_server_create(const lg_graph* const* graphs, uint32_t co
       set_error_message("lg_server_create: every graph must live on the current device");
       return LG_EINVAL;
     }
-    if (graphs[i]->relabel) {
-      delete s;
-      set_error_message("lg_server_create: relabeled graphs are not served (encode with relabel = 0)");
-      return LG_EUNSUPPORTED;
-    }
     s->graphs.push_back(graphs[i]);
+  }
+  s->perms.resize(count);
+  for (uint32_t i = 0; i < count; i++) {
+    if (!graphs[i]->perm) continue;
+    s->perms[i].resize(graphs[i]->n);
+    if (cudaMemcpy(s->perms[i].data(), graphs[i]->perm, graphs[i]->n * 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
+      delete s;
+      set_error_message("lg_server_create: reading a permutation failed");
+      return LG_ECUDA;
+    }
   }
   const uint64_t dev_bytes = s->opts.device_bytes ? s->opts.device_bytes : (16ull << 30);
   const uint64_t host_bytes = s->opts.host_bytes ? s->opts.host_bytes : (4ull << 30);

@@ -63,7 +63,7 @@ __device__ __forceinline__ void write_depths(const BfsArgs& a, uint64_t n, uint6
   while (b) {
     const int s = __ffsll((long long)b) - 1;
     b &= b - 1;
-    if (a.rows) a.rows[s][v] = d - a.row_base[s];
+    if (a.rows) a.rows[s][a.row_perm ? (uint64_t)a.row_perm[v] : v] = d - a.row_base[s];
     else a.depth[(uint64_t)s * n + v] = d;
   }
 }
@@ -519,7 +519,7 @@ __device__ __forceinline__ void ppr_finish(const PprArgs& a, uint64_t v, uint32_
     const bool act = (a.active >> k) & 1u;
     const float r = ((uint64_t)a.src[k] == v ? 1.0f - a.damp[k] : 0.0f) + a.damp[k] * sum[k];
     out[k] = (act && d) ? r / (float)d : 0.0f;
-    if (act && ((a.last >> k) & 1u)) a.result[k][v] = r;
+    if (act && ((a.last >> k) & 1u)) a.result[k][a.result_perm ? (uint64_t)a.result_perm[v] : v] = r;
   }
   float4* o = reinterpret_cast<float4*>(a.cout + v * PPR_K);
   __stcs(o, make_float4(out[0], out[1], out[2], out[3]));
@@ -536,9 +536,15 @@ __device__ __forceinline__ void ppr_finish_half(const PprArgs& a, uint64_t v, ui
     const bool act = (a.active >> k) & 1u;
     const float r = ((uint64_t)a.src[k] == v ? 1.0f - a.damp[k] : 0.0f) + a.damp[k] * sv[q];
     out[q] = (act && d) ? r / (float)d : 0.0f;
-    if (act && ((a.last >> k) & 1u)) a.result[k][v] = r;
+    if (act && ((a.last >> k) & 1u)) a.result[k][a.result_perm ? (uint64_t)a.result_perm[v] : v] = r;
   }
   __stcs(reinterpret_cast<float4*>(a.cout + v * PPR_K + h * 4), make_float4(out[0], out[1], out[2], out[3]));
+}
+
+// one 16-byte half row of slot contributions; rows of the first `hot`
+// vertices (the hubs, after DM relabeling) stay in L2, the rest stream through
+__device__ __forceinline__ float4 gather_row(const float* ch, uint32_t u, uint32_t hot, uint64_t keep, uint64_t stream) {
+  return ldg_gather4(ch + (uint64_t)u * PPR_K, u < hot ? keep : stream);
 }
 
 __device__ __forceinline__ void add4(float4& s, const float4& x) {
@@ -592,7 +598,7 @@ __global__ void __launch_bounds__(TNT, 4) k_ppr_pull(GView g, PprArgs a) {
         for (int r = 0; r < 2; r++) {
           const uint32_t from = (uint32_t)(r * 16 + (lane >> 1));
           const uint32_t fid = __shfl_sync(LG_FULL_MASK, id[u], from);
-          x[u * 2 + r] = (base + 32u * u + from < f1) ? ldg_gather4(ch + (uint64_t)fid * PPR_K, pkeep)
+          x[u * 2 + r] = (base + 32u * u + from < f1) ? gather_row(ch, fid, a.hot, pkeep, pstream)
                                                       : make_float4(0.f, 0.f, 0.f, 0.f);
         }
       }
@@ -651,13 +657,13 @@ __global__ void __launch_bounds__(TNT, 4) k_ppr_pull(GView g, PprArgs a) {
       uint32_t k = 0;
       for (; k + 4 <= d; k += 4) {
         const uint32_t u0 = dec.next(), u1 = dec.next(), u2 = dec.next(), u3 = dec.next();
-        const float4 x0 = ldg_gather4(ch + (uint64_t)u0 * PPR_K, pkeep);
-        const float4 x1 = ldg_gather4(ch + (uint64_t)u1 * PPR_K, pkeep);
-        const float4 x2 = ldg_gather4(ch + (uint64_t)u2 * PPR_K, pkeep);
-        const float4 x3 = ldg_gather4(ch + (uint64_t)u3 * PPR_K, pkeep);
+        const float4 x0 = ldg_gather4(ch + (uint64_t)u0 * PPR_K, u0 < a.hot ? pkeep : pstream);
+        const float4 x1 = ldg_gather4(ch + (uint64_t)u1 * PPR_K, u1 < a.hot ? pkeep : pstream);
+        const float4 x2 = ldg_gather4(ch + (uint64_t)u2 * PPR_K, u2 < a.hot ? pkeep : pstream);
+        const float4 x3 = ldg_gather4(ch + (uint64_t)u3 * PPR_K, u3 < a.hot ? pkeep : pstream);
         add4(s0, x0); add4(s1, x1); add4(s0, x2); add4(s1, x3);
       }
-      for (; k < d; k++) add4(s0, ldg_gather4(ch + (uint64_t)dec.next() * PPR_K, pkeep));
+      for (; k < d; k++) add4(s0, gather_row(ch, dec.next(), a.hot, pkeep, pstream));
       add4(s0, s1);
       ppr_finish_half(a, v0 + i, d, s0, h);
     }
@@ -696,13 +702,13 @@ __global__ void __launch_bounds__(TNT, 4) k_ppr_pull(GView g, PprArgs a) {
       uint32_t k = 0;
       for (; k + 4 <= d; k += 4) {  // four arcs in flight
         const uint32_t u0 = dec.next(), u1 = dec.next(), u2 = dec.next(), u3 = dec.next();
-        const float4 x0 = ldg_gather4(ch + (uint64_t)u0 * PPR_K, pkeep);
-        const float4 x1 = ldg_gather4(ch + (uint64_t)u1 * PPR_K, pkeep);
-        const float4 x2 = ldg_gather4(ch + (uint64_t)u2 * PPR_K, pkeep);
-        const float4 x3 = ldg_gather4(ch + (uint64_t)u3 * PPR_K, pkeep);
+        const float4 x0 = ldg_gather4(ch + (uint64_t)u0 * PPR_K, u0 < a.hot ? pkeep : pstream);
+        const float4 x1 = ldg_gather4(ch + (uint64_t)u1 * PPR_K, u1 < a.hot ? pkeep : pstream);
+        const float4 x2 = ldg_gather4(ch + (uint64_t)u2 * PPR_K, u2 < a.hot ? pkeep : pstream);
+        const float4 x3 = ldg_gather4(ch + (uint64_t)u3 * PPR_K, u3 < a.hot ? pkeep : pstream);
         add4(s0, x0); add4(s1, x1); add4(s0, x2); add4(s1, x3);
       }
-      for (; k < d; k++) add4(s0, ldg_gather4(ch + (uint64_t)dec.next() * PPR_K, pkeep));
+      for (; k < d; k++) add4(s0, gather_row(ch, dec.next(), a.hot, pkeep, pstream));
       add4(s0, s1);
       if (head) carry[w][h] = s0;
       else vsum[j][h] = s0;

@@ -220,28 +220,37 @@ def test_serve_poisson_trace(graphs):
     assert rs["makespan_ns"] >= int(tr.arrival_ns[-1])
 
 
-@pytest.mark.parametrize("id_mode,off_mode", [(lg.LG_ID_GLOBAL, lg.LG_OFF_PACKED), (lg.LG_ID_LOCAL, lg.LG_OFF_EF),
-                                              (lg.LG_ID_LOCAL_GAP, lg.LG_OFF_EF), (lg.LG_ID_CSR32, 0)])
-def test_serve_all_modes(graphs, id_mode, off_mode):
-    """The serving kernels in every ID / offset mode: 16 BFS and 16 PPR
-    requests (two PPR sweeps of 8 slots), hubs and low-degree sources."""
+@pytest.mark.parametrize("id_mode,off_mode,relabel", [(lg.LG_ID_GLOBAL, lg.LG_OFF_PACKED, False),
+                                                      (lg.LG_ID_LOCAL, lg.LG_OFF_EF, False),
+                                                      (lg.LG_ID_LOCAL_GAP, lg.LG_OFF_EF, False),
+                                                      (lg.LG_ID_CSR32, 0, False),
+                                                      (lg.LG_ID_GLOBAL, lg.LG_OFF_EF, True),
+                                                      (lg.LG_ID_LOCAL_GAP, lg.LG_OFF_EF, True)])
+def test_serve_all_modes(graphs, id_mode, off_mode, relabel):
+    """The serving kernels in every ID / offset mode, with and without DM
+    relabeling (requests and results in original IDs): 16 BFS, 16 PPR
+    (two PPR sweeps of 8 slots) and 16 lookups, hubs and low-degree sources."""
     hs, _ = graphs
     h = hs[2]
-    g = lg.lg_encode(h.row_ptr, h.col, id_mode=id_mode, off_mode=off_mode)
+    g = lg.lg_encode(h.row_ptr, h.col, id_mode=id_mode, off_mode=off_mode, relabel=relabel)
     s = lg.lg_server_create([g], device_bytes=1 << 30, host_bytes=1 << 29)
     deg = np.diff(h.row_ptr)
     order = np.argsort(-deg)
     srcs = np.concatenate([order[:6], np.flatnonzero(deg)[::997][:10]]).astype(np.uint32)
     tickets = {}
+    rng = np.random.default_rng(int(id_mode) * 2 + int(relabel))
     for src in srcs:
         for kind in (lg.LG_REQ_BFS, lg.LG_REQ_PPR):
-            tickets[lg.lg_server_submit(s, kind, 0, source=int(src))] = (kind, int(src))
+            tickets[lg.lg_server_submit(s, kind, 0, source=int(src))] = (kind, int(src), None)
+        vs = rng.integers(0, h.n, size=64).astype(np.uint32)
+        vs[0] = src
+        tickets[lg.lg_server_submit(s, lg.LG_REQ_NEIGHBORS, 0, vertices=vs)] = (lg.LG_REQ_NEIGHBORS, None, vs)
     got = []
     while len(got) < len(tickets):
         got += lg.lg_server_wait(s, 64, 30_000_000)
     s.destroy()
     g.free()
     for r in got:
-        kind, src = tickets[r["ticket"]]
+        kind, src, vs = tickets[r["ticket"]]
         assert r["status"] == 0
-        check_result(h, kind, src, None, r["result"])
+        check_result(h, kind, src, vs, r["result"])
