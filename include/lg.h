@@ -68,8 +68,12 @@ typedef enum {
 typedef struct {
     uint32_t id_mode;       /* lg_id_mode                                                   */
     uint32_t off_mode;      /* lg_off_mode (ignored for LG_ID_CSR32)                        */
-    uint32_t relabel;       /* 0 = keep IDs, 1 = DM permuter (Section 5.6): higher degree
-                               gets a smaller label, ties by original ID                    */
+    uint32_t relabel;       /* 0 = keep IDs; 1 = DM permuter (Section 5.6): higher degree
+                               gets a smaller label, ties by original ID; 2 = the greedy
+                               heuristic for local IDs (Section 3.2.2, Listing 1): vertices
+                               by increasing degree (ties by ID) give the next free labels
+                               to their unlabeled neighbors, unreached vertices follow in
+                               ID order                                                      */
     uint32_t select_sample; /* EF select sample rate, a power of two in [64, 65536];
                                0 means 512                                                  */
     uint32_t weight_bits;   /* 0 = bits(max weight); else the fixed weight width (<= 32)    */

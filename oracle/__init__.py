@@ -23,6 +23,7 @@ _lock = threading.Lock()
 _handle = None
 
 ID_GLOBAL, ID_LOCAL, ID_LOCAL_GAP = 0, 1, 2
+RELABEL_NONE, RELABEL_DM, RELABEL_GREEDY = 0, 1, 2
 OFF_PACKED, OFF_EF = 0, 1
 
 _u64, _u32, _i32, _i64, _dbl = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_int64, ctypes.c_double
@@ -185,7 +186,7 @@ def encode(n, row_ptr, col, weights=None, id_mode=ID_GLOBAL, off_mode=OFF_PACKED
     wt = None if weights is None else np.ascontiguousarray(weights, dtype=np.uint32)
     h = ctypes.c_void_p()
     rc = _lib().orc_encode(n, cl.shape[0], _ptr(rp, _u64), _ptr(cl, _u32), _ptr(wt, _u32), id_mode, off_mode,
-                           int(bool(relabel)), sample, weight_bits, ctypes.byref(h))
+                           int(relabel), sample, weight_bits, ctypes.byref(h))
     if rc != 0:
         raise OracleError(rc, "orc_encode")
     return Encoded(h.value)

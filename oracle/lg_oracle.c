@@ -25,6 +25,8 @@
  *     vector stored with Elias-Fano (Elias 1974, Fano 1971; Okanohara-Sadakane
  *     2007), select(j) = the j-th one = the start of A_j (Section 4.1).
  *   - Section 5.6 (DM permuter): a higher degree gives a smaller label.
+ *   - Section 3.2.2, Listing 1 (greedy relabeling for local IDs): vertices by
+ *     increasing degree hand out the smallest free labels to their neighbors.
  *   - Section 7.1.2: BFS (depth per vertex), PageRank without atomics, and
  *     SSSP (shortest-path distances; computed here by Dijkstra).
  *
@@ -131,15 +133,55 @@ static int cmp_idw(const void *a, const void *b) {
     return (u > v) - (u < v);
 }
 
-/* Builds the relabeled CSR: row P(v) = sorted { P(u) : u in N_v }. */
-static int dm_relabel(uint64_t n, const uint64_t *rp, const uint32_t *col, const uint32_t *w,
+/* Greedy relabeling heuristic for local IDs (Listing 1, Section 3.2.2):
+   vertices taken by increasing degree (ties by ID), each giving the next new
+   labels to those of its neighbors (in row order) that have none yet; the
+   vertices never reached get the remaining labels in ID order.  Labels start
+   at 0 and every vertex of the sorted order is visited (the listing's loops
+   start at 1 and its last loop names the wrong variable; read as intended). */
+static int cmp_deg_asc(const void *a, const void *b) {
+    uint32_t u = *(const uint32_t *)a, v = *(const uint32_t *)b;
+    uint64_t du = g_deg_for_cmp[u], dv = g_deg_for_cmp[v];
+    if (du != dv) return du < dv ? -1 : 1;
+    return (u > v) - (u < v);
+}
+
+static void greedy_perm(uint64_t n, const uint64_t *rp, const uint32_t *col, const uint64_t *deg,
+                        uint32_t *perm, uint32_t *inv, unsigned char *visit) {
+    uint32_t *id = inv; /* the sorted order, overwritten by the inverse at the end */
+    for (uint64_t v = 0; v < n; v++) { id[v] = (uint32_t)v; visit[v] = 0; }
+    g_deg_for_cmp = deg;
+    qsort(id, n, sizeof(uint32_t), cmp_deg_asc);
+    uint32_t nl = 0;
+    for (uint64_t i = 0; i < n; i++) {
+        uint32_t v = id[i];
+        for (uint64_t j = rp[v]; j < rp[v + 1]; j++) {
+            uint32_t u = col[j];
+            if (!visit[u]) { perm[u] = nl++; visit[u] = 1; }
+        }
+    }
+    for (uint64_t v = 0; v < n; v++)
+        if (!visit[v]) { perm[v] = nl++; visit[v] = 1; }
+    for (uint64_t v = 0; v < n; v++) inv[perm[v]] = (uint32_t)v;
+}
+
+/* Builds the relabeled CSR: row P(v) = sorted { P(u) : u in N_v }, with P
+   the DM order (relabel = 1) or the greedy heuristic (relabel = 2). */
+static int dm_relabel(uint64_t n, const uint64_t *rp, const uint32_t *col, const uint32_t *w, uint32_t relabel,
                       uint32_t *perm, uint32_t *inv, uint64_t *nrp, uint32_t *ncol, uint32_t *nw) {
     uint64_t *deg = (uint64_t *)malloc(sizeof(uint64_t) * (n ? n : 1));
     if (!deg) return ORC_ENOMEM;
     for (uint64_t v = 0; v < n; v++) { deg[v] = rp[v + 1] - rp[v]; inv[v] = (uint32_t)v; }
-    g_deg_for_cmp = deg;
-    qsort(inv, n, sizeof(uint32_t), cmp_dm);
-    for (uint64_t i = 0; i < n; i++) perm[inv[i]] = (uint32_t)i;
+    if (relabel == 2) {
+        unsigned char *visit = (unsigned char *)malloc(n ? n : 1);
+        if (!visit) { free(deg); return ORC_ENOMEM; }
+        greedy_perm(n, rp, col, deg, perm, inv, visit);
+        free(visit);
+    } else {
+        g_deg_for_cmp = deg;
+        qsort(inv, n, sizeof(uint32_t), cmp_dm);
+        for (uint64_t i = 0; i < n; i++) perm[inv[i]] = (uint32_t)i;
+    }
     nrp[0] = 0;
     for (uint64_t i = 0; i < n; i++) nrp[i + 1] = nrp[i] + deg[inv[i]];
     idw *tmp = NULL;
@@ -200,7 +242,8 @@ int orc_encode(uint64_t n, uint64_t arcs, const uint64_t *row_ptr, const uint32_
     orc_graph *g = (orc_graph *)calloc(1, sizeof(orc_graph));
     if (!g) return ORC_ENOMEM;
     g->n = n; g->arcs = arcs; g->id_mode = id_mode; g->off_mode = off_mode;
-    g->relabel = relabel ? 1 : 0; g->sample = sample; g->weighted = weights ? 1 : 0;
+    if (relabel > 2) { free(g); return ORC_EINVAL; }
+    g->relabel = relabel; g->sample = sample; g->weighted = weights ? 1 : 0;
 
     /* optional DM relabel */
     const uint64_t *rp = row_ptr;
@@ -213,7 +256,7 @@ int orc_encode(uint64_t n, uint64_t arcs, const uint64_t *row_ptr, const uint32_
         ncol = (uint32_t *)malloc(sizeof(uint32_t) * (arcs ? arcs : 1));
         if (weights) nw = (uint32_t *)malloc(sizeof(uint32_t) * (arcs ? arcs : 1));
         if (!g->perm || !g->inv_perm || !nrp || !ncol || (weights && !nw)) goto nomem;
-        if (dm_relabel(n, row_ptr, col, weights, g->perm, g->inv_perm, nrp, ncol, nw) != ORC_OK) goto nomem;
+        if (dm_relabel(n, row_ptr, col, weights, relabel, g->perm, g->inv_perm, nrp, ncol, nw) != ORC_OK) goto nomem;
         rp = nrp; cl = ncol; wt = nw;
     }
 

@@ -27,6 +27,7 @@ from ._build import LIB, build, is_stale
 
 __all__ = [
     "LG_ID_GLOBAL", "LG_ID_LOCAL", "LG_ID_LOCAL_GAP", "LG_ID_CSR32", "LG_OFF_PACKED", "LG_OFF_EF",
+    "LG_RELABEL_NONE", "LG_RELABEL_DM", "LG_RELABEL_GREEDY",
     "LgError", "LogGraph", "build", "load", "lg_encode", "lg_stats_get", "lg_arrays_get", "lg_neighbors",
     "lg_bfs", "lg_sssp", "lg_pagerank", "lg_pagerank_noalloc", "lg_free", "lg_last_error", "lg_kernel_launches",
     "LgBatch", "lg_batch_create", "lg_batch_run", "lg_batch_status", "lg_batch_info_get", "lg_batch_free",
@@ -38,6 +39,7 @@ __all__ = [
 
 LG_ID_GLOBAL, LG_ID_LOCAL, LG_ID_LOCAL_GAP, LG_ID_CSR32 = 0, 1, 2, 3
 LG_OFF_PACKED, LG_OFF_EF = 0, 1
+LG_RELABEL_NONE, LG_RELABEL_DM, LG_RELABEL_GREEDY = 0, 1, 2
 LG_FLAG_CHECK_SYMMETRIC = 1
 LG_BATCH_FLAG_DROP_MEMBER = 1
 LG_REQ_NEIGHBORS, LG_REQ_BFS, LG_REQ_PPR = 0, 1, 2
@@ -226,7 +228,7 @@ class LogGraph:
 
 
 def lg_encode(row_ptr, col, weights=None, *, id_mode: int = LG_ID_GLOBAL, off_mode: int = LG_OFF_PACKED,
-              relabel: bool = False, select_sample: int = 512, weight_bits: int = 0,
+              relabel: int = 0, select_sample: int = 512, weight_bits: int = 0,
               check_symmetric: bool = False, stream=None) -> LogGraph:
     """lg_encode: build the logarithmized graph from a CSR (row_ptr uint64[n+1],
     col uint32[arcs], optional weights uint32[arcs]; int64/int32 tensors are
@@ -236,7 +238,7 @@ def lg_encode(row_ptr, col, weights=None, *, id_mode: int = LG_ID_GLOBAL, off_mo
     cl = _dev(col, torch.int32, "col")
     wt = None if weights is None else _dev(weights, torch.int32, "weights")
     n = rp.numel() - 1
-    opts = _Opts(id_mode, off_mode, int(bool(relabel)), select_sample, weight_bits,
+    opts = _Opts(id_mode, off_mode, int(relabel), select_sample, weight_bits,
                  LG_FLAG_CHECK_SYMMETRIC if check_symmetric else 0)
     h = _vp()
     st = _stream(stream)

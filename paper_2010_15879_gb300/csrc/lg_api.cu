@@ -440,7 +440,7 @@ static lg_status encode_impl(lg_graph* g, const uint64_t* row_ptr, const uint32_
   }
   g->r = g->s + g->omega;
 
-  // ---- optional DM relabel (Section 5.6)
+  // ---- optional relabel: DM (Section 5.6) or the greedy heuristic (Listing 1)
   const uint64_t* rp = row_ptr;
   const uint32_t* cl = col;
   const uint32_t* wt = weights;
@@ -451,7 +451,8 @@ static lg_status encode_impl(lg_graph* g, const uint64_t* row_ptr, const uint32_
     LG_TRY(t_nrp.alloc((n + 1) * sizeof(uint64_t)));
     LG_TRY(t_ncol.alloc(arcs * sizeof(uint32_t)));
     if (weights) LG_TRY(t_nw.alloc(arcs * sizeof(uint32_t)));
-    LG_TRY(enc_dm_relabel(row_ptr, col, weights, n, arcs, g->max_degree, g->perm, g->inv_perm, t_nrp.as<uint64_t>(),
+    LG_TRY(enc_dm_relabel(row_ptr, col, weights, n, arcs, g->max_degree, g->relabel, g->perm, g->inv_perm,
+                          t_nrp.as<uint64_t>(),
                           t_ncol.as<uint32_t>(), weights ? t_nw.as<uint32_t>() : nullptr, st));
     rp = t_nrp.as<uint64_t>();
     cl = t_ncol.as<uint32_t>();
@@ -551,7 +552,7 @@ extern "C" lg_status lg_encode(const uint64_t* row_ptr, const uint32_t* col, con
     return LG_EINVAL;
   }
   if (o.weight_bits > 32) { set_errf("lg_encode: weight_bits must be <= 32"); return LG_EINVAL; }
-  if (o.relabel > 1) { set_errf("lg_encode: relabel must be 0 or 1"); return LG_EINVAL; }
+  if (o.relabel > 2) { set_errf("lg_encode: relabel must be 0, 1 (DM) or 2 (greedy)"); return LG_EINVAL; }
   if (weights && (o.id_mode == LG_ID_LOCAL || o.id_mode == LG_ID_LOCAL_GAP)) {
     set_errf("lg_encode: weights are supported with LG_ID_GLOBAL and LG_ID_CSR32 only");
     return LG_EUNSUPPORTED;

@@ -84,8 +84,9 @@ cudaError_t enc_validate(const uint64_t* rp, const uint32_t* col, const uint32_t
                          uint32_t* max_w, cudaStream_t st);
 cudaError_t enc_check_symmetric(const uint64_t* rp, const uint32_t* col, uint64_t n, int* err,
                                 cudaStream_t st);
+// relabeled CSR for permuter `mode`: 1 = DM (Section 5.6), 2 = greedy (Listing 1)
 cudaError_t enc_dm_relabel(const uint64_t* rp, const uint32_t* col, const uint32_t* w, uint64_t n,
-                           uint64_t arcs, uint64_t max_deg, uint32_t* perm, uint32_t* inv_perm,
+                           uint64_t arcs, uint64_t max_deg, uint32_t mode, uint32_t* perm, uint32_t* inv_perm,
                            uint64_t* nrp, uint32_t* ncol, uint32_t* nw, cudaStream_t st);
 cudaError_t enc_local_lengths(const uint64_t* rp, const uint32_t* col, uint64_t n, int gap, uint32_t s,
                               uint32_t H, uint8_t* wid, uint64_t* len, cudaStream_t st);

@@ -404,9 +404,51 @@ __global__ void __launch_bounds__(256) k_dm_scatter(const uint64_t* __restrict__
   }
 }
 
+// =========================================================================
+// Greedy permuter for local IDs (Listing 1, Section 3.2.2).  The listing walks
+// the vertices by increasing degree (ties by ID) and hands the next free label
+// to each neighbor that has none; so a vertex's label is the rank of its FIRST
+// appearance in the neighbor lists concatenated in that order, and vertices
+// that never appear follow in ID order.  That rank is computed in parallel:
+// every arc offers its position in the concatenation to its target with
+// atomicMin, then one sort by (first position, ID) gives the labels.
+// =========================================================================
+__global__ void k_gr_keys(const uint64_t* __restrict__ rp, uint64_t n, uint32_t* __restrict__ keys,
+                          uint32_t* __restrict__ vals) {
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x) {
+    keys[v] = (uint32_t)(rp[v + 1] - rp[v]);
+    vals[v] = (uint32_t)v;
+  }
+}
+__global__ void k_gr_degs(const uint64_t* __restrict__ rp, const uint32_t* __restrict__ order, uint64_t n,
+                          uint32_t* __restrict__ sdeg, uint64_t* __restrict__ first, uint64_t none,
+                          uint32_t* __restrict__ ids) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t v = order[i];
+    sdeg[i] = (uint32_t)(rp[v + 1] - rp[v]);
+    first[i] = none;
+    ids[i] = (uint32_t)i;
+  }
+}
+// one warp per vertex of the sorted order: its arcs offer positions pos0[i] + j
+__global__ void __launch_bounds__(256) k_gr_first(const uint64_t* __restrict__ rp, const uint32_t* __restrict__ col,
+                                                  const uint32_t* __restrict__ order, const uint64_t* __restrict__ pos0,
+                                                  uint64_t n, unsigned long long* __restrict__ first) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t i = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+    const uint32_t v = order[i];
+    const uint64_t lo = rp[v], d = rp[v + 1] - lo, p = pos0[i];
+    for (uint64_t k = lane; k < d; k += 32) {
+      const uint32_t u = col[lo + k];
+      if ((unsigned long long)(p + k) < first[u]) atomicMin(first + u, (unsigned long long)(p + k));
+    }
+  }
+}
+
 cudaError_t enc_dm_relabel(const uint64_t* rp, const uint32_t* col, const uint32_t* w, uint64_t n, uint64_t arcs,
-                           uint64_t max_deg, uint32_t* perm, uint32_t* inv_perm, uint64_t* nrp, uint32_t* ncol,
-                           uint32_t* nw, cudaStream_t st) {
+                           uint64_t max_deg, uint32_t mode, uint32_t* perm, uint32_t* inv_perm, uint64_t* nrp,
+                           uint32_t* ncol, uint32_t* nw, cudaStream_t st) {
   cudaError_t e;
   uint32_t *keys = nullptr, *k2 = nullptr, *v2 = nullptr, *newdeg = nullptr;
   uint64_t* stmp = nullptr;
@@ -417,7 +459,39 @@ cudaError_t enc_dm_relabel(const uint64_t* rp, const uint32_t* col, const uint32
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&newdeg, n * sizeof(uint32_t), st);
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&stmp, scan_tmp_words(n) * sizeof(uint64_t), st);
   if (e == cudaSuccess) e = cudaMallocAsync(&rtmp, radix_tmp_bytes(n), st);
-  if (e == cudaSuccess) {
+  if (e == cudaSuccess && mode == 2) {
+    // greedy: order by (degree asc, ID asc), first appearances, sort by them
+    uint64_t *pos0 = nullptr, *first = nullptr, *first2 = nullptr;
+    e = cudaMallocAsync((void**)&pos0, (n + 1) * sizeof(uint64_t), st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&first, n * sizeof(uint64_t), st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&first2, n * sizeof(uint64_t), st);
+    if (e == cudaSuccess) {
+      k_gr_keys<<<grid_for(n, 256, 152 * 32), 256, 0, st>>>(rp, n, keys, inv_perm);  // inv_perm: the order
+      count_launch();
+      e = radix_sort_u32(keys, inv_perm, k2, v2, n, host_bits(max_deg), rtmp, st);
+    }
+    if (e == cudaSuccess) {
+      // first[] indexed by vertex; keys reused as the sorted degrees, v2 as vertex IDs
+      k_gr_degs<<<grid_for(n, 256, 152 * 32), 256, 0, st>>>(rp, inv_perm, n, keys, first, arcs, v2);
+      count_launch();
+      e = scan_excl_u32(keys, n, pos0, stmp, st);
+    }
+    if (e == cudaSuccess) {
+      k_gr_first<<<grid_for(n, 8, 152 * 64), 256, 0, st>>>(rp, col, inv_perm, pos0, n,
+                                                           reinterpret_cast<unsigned long long*>(first));
+      count_launch();
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+      // new label i goes to the vertex with the i-th smallest (first, ID): v2
+      // holds 0..n-1, the radix sort is stable, never-seen vertices share key arcs
+      e = radix_sort_u64(first, v2, first2, k2, n, host_bits(arcs), rtmp, st);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(inv_perm, v2, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st);
+    cudaFreeAsync(pos0, st);
+    cudaFreeAsync(first, st);
+    cudaFreeAsync(first2, st);
+  } else if (e == cudaSuccess) {
     k_dm_keys<<<grid_for(n, 256, 152 * 32), 256, 0, st>>>(rp, n, max_deg, keys, inv_perm);
     count_launch();
     e = radix_sort_u32(keys, inv_perm, k2, v2, n, host_bits(max_deg), rtmp, st);
