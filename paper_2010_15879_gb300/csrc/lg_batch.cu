@@ -14,8 +14,10 @@
 // BFS levels and PageRank iterations.  A team waits only for slots that
 // running CTAs take next, so the queue makes progress as long as p <= grid;
 // each wait also has a time limit after which the CTA records a timeout and
-// abandons the graph.  Data written inside the launch (streams, queues,
-// contributions, depths) is read with L2-coherent loads (ld.global.cg).
+// abandons the graph.  Streams are read with ordinary loads after the encode
+// barrier (see sfield); per-vertex data that other CTAs of a team rewrite
+// between sweeps or levels (contributions, depths, queues) is read with
+// L2-coherent loads (ld.global.cg).
 //
 // Each graph decodes its neighborhoods with T lanes per vertex (T = 1, 4, 8
 // or 32); T per average-degree class and the team tile are chosen by a timing
@@ -77,17 +79,24 @@ struct BatchArgs {
   uint64_t wait_ns;         // team barrier time limit
 };
 
-__device__ __forceinline__ uint64_t ldcg64(const uint64_t* p) {
-  return __ldcg(reinterpret_cast<const unsigned long long*>(p));
-}
-
-// field of w <= 32 bits at bit p of a stream written in this launch
-__device__ __forceinline__ uint32_t cfield(const uint64_t* S, uint64_t p, uint32_t w) {
+// field of w <= 32 bits at bit p of a graph's stream.  Every graph's streams
+// start on a 128-byte line and are written before the barrier that ends the
+// encode phase; a CTA never reads a line of them before it is written (no
+// line is shared with another graph, and stores do not allocate in L1), so
+// after that barrier ordinary L1-cached loads see the written words.
+__device__ __forceinline__ uint32_t sfield(const uint64_t* S, uint64_t p, uint32_t w) {
   const uint64_t wi = p >> 6;
   const uint32_t sh = (uint32_t)p & 63u;
-  uint64_t v = ldcg64(S + wi) >> sh;
-  if (sh + w > 64) v |= ldcg64(S + wi + 1) << (64u - sh);
+  uint64_t v = S[wi] >> sh;
+  if (sh + w > 64) v |= S[wi + 1] << (64u - sh);
   return (uint32_t)(v & ((1ull << w) - 1ull));
+}
+
+// per-vertex arrays rewritten by other CTAs of a team between sweeps / levels
+// are read through L2 (ld.global.cg); a single-CTA graph reads them plainly
+template <bool TEAM>
+__device__ __forceinline__ float cget(const float* p) {
+  return TEAM ? __ldcg(p) : *p;
 }
 
 __device__ __forceinline__ uint64_t globaltimer_ns() {
@@ -133,8 +142,9 @@ __device__ __forceinline__ float group_sum(float x) {
   return x;
 }
 
-// Pull PageRank over vertices [v0, v1) of one graph, T lanes per vertex.
-template <int T>
+// Pull PageRank over vertices [v0, v1) of one graph, T lanes per vertex; each
+// lane keeps four fields (and their four gathers) in flight.
+template <int T, bool TEAM>
 __device__ void pr_sweep(const BatchArgs& a, const BatchGraph& G, uint32_t v0, uint32_t v1, const float* cin,
                          float* cout, bool last) {
   const uint64_t* A = a.A + G.a_word;
@@ -142,16 +152,27 @@ __device__ void pr_sweep(const BatchArgs& a, const BatchGraph& G, uint32_t v0, u
   constexpr uint32_t groups = BNT / T;
   const uint32_t gid = threadIdx.x / T, lane = threadIdx.x % T;
   const float base = (1.0f - a.damp) / (float)G.n;
+  const uint32_t s = G.s;
   // every group runs the same number of rounds so the shuffles stay converged
   for (uint32_t vb = v0; vb < v1; vb += groups) {
     const uint32_t v = vb + gid;
-    float sum = 0.f;
+    float sum = 0.f, sum2 = 0.f;
     uint32_t x0 = 0, x1 = 0;
     if (v < v1) {
-      x0 = cfield(O, (uint64_t)v * G.w_O, G.w_O);
-      x1 = cfield(O, (uint64_t)(v + 1) * G.w_O, G.w_O);
-      for (uint32_t j = x0 + lane; j < x1; j += T) sum += __ldcg(cin + cfield(A, (uint64_t)j * G.s, G.s));
+      x0 = sfield(O, (uint64_t)v * G.w_O, G.w_O);
+      x1 = sfield(O, (uint64_t)(v + 1) * G.w_O, G.w_O);
+      uint32_t j = x0 + lane;
+      for (; j + 3 * T < x1; j += 4 * T) {
+        const uint32_t u0 = sfield(A, (uint64_t)j * s, s), u1 = sfield(A, (uint64_t)(j + T) * s, s);
+        const uint32_t u2 = sfield(A, (uint64_t)(j + 2 * T) * s, s), u3 = sfield(A, (uint64_t)(j + 3 * T) * s, s);
+        const float f0 = cget<TEAM>(cin + u0), f1 = cget<TEAM>(cin + u1);
+        const float f2 = cget<TEAM>(cin + u2), f3 = cget<TEAM>(cin + u3);
+        sum += f0 + f1;
+        sum2 += f2 + f3;
+      }
+      for (; j < x1; j += T) sum += cget<TEAM>(cin + sfield(A, (uint64_t)j * s, s));
     }
+    sum += sum2;
     if (T > 1) sum = group_sum<T>(sum);
     if (v < v1 && lane == 0) {
       const uint32_t d = x1 - x0;
@@ -173,10 +194,10 @@ __device__ void bfs_level(const BatchArgs& a, const BatchGraph& G, uint32_t memb
   const uint32_t gid = threadIdx.x / T, lane = threadIdx.x % T;
   for (uint32_t q = member * groups + gid; q < qlen; q += p * groups) {
     const uint32_t v = __ldcg(qin + q);
-    const uint32_t x0 = cfield(O, (uint64_t)v * G.w_O, G.w_O);
-    const uint32_t x1 = cfield(O, (uint64_t)(v + 1) * G.w_O, G.w_O);
+    const uint32_t x0 = sfield(O, (uint64_t)v * G.w_O, G.w_O);
+    const uint32_t x1 = sfield(O, (uint64_t)(v + 1) * G.w_O, G.w_O);
     for (uint32_t j = x0 + lane; j < x1; j += T) {
-      const uint32_t u = cfield(A, (uint64_t)j * G.s, G.s);
+      const uint32_t u = sfield(A, (uint64_t)j * G.s, G.s);
       if (__ldcg(depth + u) == INF32 && atomicCAS(&depth[u], INF32, level + 1) == INF32) qout[atomicAdd(qn, 1u)] = u;
     }
   }
@@ -259,16 +280,23 @@ __device__ void process_item(const BatchArgs& a, uint32_t gi, uint32_t m) {
     float* co = a.c1 + G.vbase;
     const float r0 = 1.0f / (float)G.n;
     for (uint32_t v = v0 + threadIdx.x; v < v1; v += BNT) {
-      const uint32_t d = cfield(O, (uint64_t)(v + 1) * G.w_O, G.w_O) - cfield(O, (uint64_t)v * G.w_O, G.w_O);
+      const uint32_t d = sfield(O, (uint64_t)(v + 1) * G.w_O, G.w_O) - sfield(O, (uint64_t)v * G.w_O, G.w_O);
       ci[v] = d ? r0 / (float)d : 0.f;
     }
     if (!team_sync(a, bar, p, ++round)) return;
     for (uint32_t t = 0; t < a.iters; t++) {
       const bool last = t + 1 == a.iters;
-      if (T == 1) pr_sweep<1>(a, G, v0, v1, ci, co, last);
-      else if (T == 4) pr_sweep<4>(a, G, v0, v1, ci, co, last);
-      else if (T == 8) pr_sweep<8>(a, G, v0, v1, ci, co, last);
-      else pr_sweep<32>(a, G, v0, v1, ci, co, last);
+      if (p > 1) {
+        if (T == 1) pr_sweep<1, true>(a, G, v0, v1, ci, co, last);
+        else if (T == 4) pr_sweep<4, true>(a, G, v0, v1, ci, co, last);
+        else if (T == 8) pr_sweep<8, true>(a, G, v0, v1, ci, co, last);
+        else pr_sweep<32, true>(a, G, v0, v1, ci, co, last);
+      } else {
+        if (T == 1) pr_sweep<1, false>(a, G, v0, v1, ci, co, last);
+        else if (T == 4) pr_sweep<4, false>(a, G, v0, v1, ci, co, last);
+        else if (T == 8) pr_sweep<8, false>(a, G, v0, v1, ci, co, last);
+        else pr_sweep<32, false>(a, G, v0, v1, ci, co, last);
+      }
       if (!team_sync(a, bar, p, ++round)) return;
       float* x = ci;
       ci = co;
@@ -277,7 +305,7 @@ __device__ void process_item(const BatchArgs& a, uint32_t gi, uint32_t m) {
   }
 }
 
-__global__ void __launch_bounds__(BNT) k_batch(BatchArgs a) {
+__global__ void __launch_bounds__(BNT, 8) k_batch(BatchArgs a) {
   __shared__ unsigned int slot_s;
   for (;;) {
     if (threadIdx.x == 0) slot_s = atomicAdd(a.next, 1u);
@@ -581,8 +609,8 @@ lg_status batch_create_impl(lg_batch* b, const uint64_t* graph_vptr, cudaStream_
     x.o_word = ow;
     const uint64_t wa = ((uint64_t)x.arcs * x.s + 63) / 64;
     const uint64_t wo = ((uint64_t)(x.n + 1) * x.w_O + 63) / 64;
-    aw += wa + (wa & 1);  // each graph starts on a 16-byte boundary
-    ow += wo + (wo & 1);
+    aw += (wa + 15) / 16 * 16;  // each graph's streams start on a 128-byte line
+    ow += (wo + 15) / 16 * 16;
   }
   b->words_A = aw + 4;  // + zero guard
   b->words_O = ow + 4;
