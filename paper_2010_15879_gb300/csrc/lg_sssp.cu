@@ -82,37 +82,76 @@ __global__ void __launch_bounds__(256) k_sssp_relax_lb(GView g, SsspArgs a, cons
       if (eoff[m] <= first) lo = m; else hi = m - 1;
     }
     uint32_t q = lo;
-    for (uint32_t t = 0; t < CH / 32; t++) {
+    // Distances are read with ordinary (L1-cached) loads: they only decrease,
+    // so a stale value is never below the true one; a stale dist[u] only costs
+    // an atomicMin that changes nothing, and a stale dist[v] only weakens one
+    // relaxation -- a vertex improved during a round is queued again, and the
+    // next round is a new launch that sees the new value.
+    // The chunk runs in phases so that each lane has its 8 slots' loads in
+    // flight together: decode all, load all distances, then the atomics.
+    constexpr int S = CH / 32;
+    uint32_t uu[S];
+    uint64_t nd[S];
+    uint32_t qv = 0xffffffffu;
+    uint64_t dv = 0, st = 0;
+#pragma unroll
+    for (int t = 0; t < S; t++) {
       const uint64_t slot = c + lane + 32u * t;
-      bool to_near = false, to_far = false;
-      uint32_t u = 0;
+      uu[t] = 0xffffffffu;
+      nd[t] = DINF;
       if (slot < E) {
         while (eoff[q + 1] <= slot) q++;
-        const uint32_t v = a.near_in[q];
+        if (q != qv) {  // a new near vertex for this lane
+          qv = q;
+          dv = a.dist[a.near_in[q]];
+          st = start[q];
+        }
         const uint64_t k = slot - eoff[q];
-        const uint64_t st = start[q];
-        u = IDM == ID_CSR32 ? __ldg(g.A32 + (st >> 5) + k) : ext32(g.A32, st + k * g.r, g.s);
-        const uint64_t nd = __ldcg(a.dist + v) + arc_weight(g, IDM, st, k);
-        if (nd < __ldcg(a.dist + u)) {
-          const uint64_t old = atomicMin(a.dist + u, (unsigned long long)nd);
-          if (nd < old) {
-            if (nd < a.hi) to_near = atomicExch(a.stamp_near + u, a.round) != a.round;
-            else to_far = atomicExch(a.stamp_far + u, a.bucket) != a.bucket;
-          }
+        uu[t] = IDM == ID_CSR32 ? __ldg(g.A32 + (st >> 5) + k) : ext32(g.A32, st + k * g.r, g.s);
+        nd[t] = dv + arc_weight(g, IDM, st, k);
+      }
+    }
+    uint64_t du[S];
+#pragma unroll
+    for (int t = 0; t < S; t++) du[t] = uu[t] != 0xffffffffu ? a.dist[uu[t]] : 0;
+    // all atomics of the chunk are issued before any result is used
+#pragma unroll
+    for (int t = 0; t < S; t++)
+      du[t] = (uu[t] != 0xffffffffu && nd[t] < du[t]) ? atomicMin(a.dist + uu[t], (unsigned long long)nd[t]) : 0;
+    uint32_t stamp_old[S];
+#pragma unroll
+    for (int t = 0; t < S; t++) {
+      stamp_old[t] = 0;
+      if (nd[t] < du[t]) {  // improved (du now holds the value before the atomicMin)
+        stamp_old[t] = nd[t] < a.hi ? atomicExch(a.stamp_near + uu[t], a.round)
+                                    : atomicExch(a.stamp_far + uu[t], a.bucket);
+      }
+    }
+    uint32_t near_bits = 0, far_bits = 0;
+#pragma unroll
+    for (int t = 0; t < S; t++) {
+      if (nd[t] < du[t]) {
+        if (nd[t] < a.hi) {
+          if (stamp_old[t] != a.round) near_bits |= 1u << t;
+        } else if (stamp_old[t] != a.bucket) {
+          far_bits |= 1u << t;
         }
       }
-      const uint32_t bn = __ballot_sync(LG_FULL_MASK, to_near);
-      const uint32_t bf = __ballot_sync(LG_FULL_MASK, to_far);
-      uint32_t pn = 0, pf = 0;
-      if (lane == 0) {
-        if (bn) pn = atomicAdd(&a.counters[0], (uint32_t)__popc(bn));
-        if (bf) pf = atomicAdd(&a.counters[1], (uint32_t)__popc(bf));
-      }
-      pn = __shfl_sync(LG_FULL_MASK, pn, 0);
-      pf = __shfl_sync(LG_FULL_MASK, pf, 0);
-      const uint32_t below = lane_lt_mask();
-      if (to_near) a.near_out[pn + __popc(bn & below)] = u;
-      if (to_far) a.far[pf + __popc(bf & below)] = u;
+    }
+    // one warp-aggregated append per list
+    const uint32_t cn = __popc(near_bits), cf = __popc(far_bits);
+    const uint32_t in = warp_incl_scan<uint32_t>(cn), inf = warp_incl_scan<uint32_t>(cf);
+    uint32_t bn = 0, bf = 0;
+    if (lane == 31) {
+      if (in) bn = atomicAdd(&a.counters[0], in);
+      if (inf) bf = atomicAdd(&a.counters[1], inf);
+    }
+    bn = __shfl_sync(LG_FULL_MASK, bn, 31) + in - cn;
+    bf = __shfl_sync(LG_FULL_MASK, bf, 31) + inf - cf;
+#pragma unroll
+    for (int t = 0; t < S; t++) {
+      if ((near_bits >> t) & 1u) a.near_out[bn++] = uu[t];
+      if ((far_bits >> t) & 1u) a.far[bf++] = uu[t];
     }
   }
 }
