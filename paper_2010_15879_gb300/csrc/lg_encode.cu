@@ -106,55 +106,103 @@ cudaError_t scan_excl_u32(const uint32_t* in, uint64_t n, uint64_t* out, uint64_
 }
 
 // =========================================================================
-// validation (one warp per row; never reads outside the given arrays)
+// validation (never reads outside the given arrays)
 // =========================================================================
-// One warp takes 32 consecutive rows: lane l loads row l's bounds, then the
-// warp walks all their entries flattened (every lane busy).
-__global__ void __launch_bounds__(256) k_validate(const uint64_t* __restrict__ rp, const uint32_t* __restrict__ col,
-                                                  const uint32_t* __restrict__ w, uint64_t n, uint64_t arcs,
-                                                  uint32_t wbits, int* err, unsigned long long* max_deg,
-                                                  uint32_t* max_w) {
-  __shared__ uint64_t pre_s[8][33];
-  __shared__ uint64_t lo_s[8][32];
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-  uint32_t wmax = 0, dmax = 0;
+// Streaming validation.  Rows are strictly increasing iff every "break"
+// (a position j > 0 with col[j-1] >= col[j]) is the first arc of a row, i.e.
+// iff the number of breaks equals the number of breaks at the starts of
+// nonempty rows (each such row has its own start).  A row pass checks the
+// bounds, takes the largest degree and counts breaks at row starts; an arc
+// pass (16-byte loads when aligned) checks ID ranges and weights and counts
+// all breaks; a last thread compares the two counts.
+__global__ void __launch_bounds__(256) k_validate_rows(const uint64_t* __restrict__ rp, const uint32_t* __restrict__ col,
+                                                       uint64_t n, uint64_t arcs, int* err,
+                                                       unsigned long long* max_deg, unsigned long long* start_breaks) {
+  uint64_t dmax = 0, sb = 0;
   int flags = 0;
-  for (uint64_t v0 = ((uint64_t)blockIdx.x * (blockDim.x >> 5) + wp) * 32; v0 < n; v0 += warps * 32) {
-    const uint64_t mv = v0 + lane;
-    uint64_t mlo = 0, mhi = 0;
-    if (mv < n) { mlo = rp[mv]; mhi = rp[mv + 1]; }
-    const bool mbad = mv < n && (mhi < mlo || mhi > arcs || (mv == 0 && mlo != 0) || (mv == n - 1 && mhi != arcs) ||
-                                 mhi - mlo > n);
-    if (mbad) flags |= DERR_ROWPTR;
-    const uint64_t cnt = (mv < n && !mbad) ? mhi - mlo : 0;
-    dmax = max(dmax, (uint32_t)cnt);
-    lo_s[wp][lane] = mlo;
-    warp_flat(pre_s[wp], cnt, [&](int r, uint64_t k) {
-      const uint64_t j = lo_s[wp][r] + k;
-      const uint32_t c = col[j];
-      if (c >= n) flags |= DERR_COL_RANGE;
-      if (k > 0 && col[j - 1] >= c) flags |= DERR_UNSORTED;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t lo = rp[v], hi = rp[v + 1];
+    if (hi < lo || hi > arcs || (v == 0 && lo != 0) || (v == n - 1 && hi != arcs) || hi - lo > n) {
+      flags |= DERR_ROWPTR;
+      continue;
+    }
+    dmax = max(dmax, hi - lo);
+    if (hi > lo && lo > 0 && col[lo - 1] >= col[lo]) sb++;
+  }
+  flags = __reduce_or_sync(LG_FULL_MASK, flags);
+  for (int o = 16; o > 0; o >>= 1) {
+    dmax = max(dmax, (uint64_t)__shfl_xor_sync(LG_FULL_MASK, dmax, o));
+    sb += __shfl_xor_sync(LG_FULL_MASK, sb, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (flags) atomicOr(err, flags);
+    if (dmax) atomicMax(max_deg, (unsigned long long)dmax);
+    if (sb) atomicAdd(start_breaks, (unsigned long long)sb);
+  }
+}
+
+template <bool VEC>
+__global__ void __launch_bounds__(256) k_validate_arcs(const uint32_t* __restrict__ col, const uint32_t* __restrict__ w,
+                                                       uint64_t n, uint64_t arcs, uint32_t wbits, int* err,
+                                                       uint32_t* max_w, unsigned long long* breaks) {
+  uint64_t nb = 0;
+  uint32_t wmax = 0;
+  int flags = 0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i * 4 < arcs; i += stride) {
+    const uint64_t j0 = i * 4;
+    uint32_t c[4], x[4] = {0, 0, 0, 0};
+    if (VEC && j0 + 4 <= arcs) {
+      const uint4 q = __ldcs(reinterpret_cast<const uint4*>(col) + i);
+      c[0] = q.x; c[1] = q.y; c[2] = q.z; c[3] = q.w;
       if (w) {
-        const uint32_t x = w[j];
-        wmax = max(wmax, x);
-        if (wbits && wbits < 32 && (x >> wbits)) flags |= DERR_WEIGHT;
+        const uint4 r = __ldcs(reinterpret_cast<const uint4*>(w) + i);
+        x[0] = r.x; x[1] = r.y; x[2] = r.z; x[3] = r.w;
       }
-    });
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        c[k] = j0 + k < arcs ? col[j0 + k] : 0xffffffffu;
+        if (w && j0 + k < arcs) x[k] = w[j0 + k];
+      }
+    }
+    uint32_t prev = j0 > 0 ? col[j0 - 1] : 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      if (j0 + k >= arcs) break;
+      if (c[k] >= n) flags |= DERR_COL_RANGE;
+      if (j0 + k > 0 && prev >= c[k]) nb++;
+      prev = c[k];
+      wmax = max(wmax, x[k]);
+      if (w && wbits && wbits < 32 && (x[k] >> wbits)) flags |= DERR_WEIGHT;
+    }
   }
   flags = __reduce_or_sync(LG_FULL_MASK, flags);
   wmax = __reduce_max_sync(LG_FULL_MASK, wmax);
-  dmax = __reduce_max_sync(LG_FULL_MASK, dmax);
-  if (lane == 0) {
+  for (int o = 16; o > 0; o >>= 1) nb += __shfl_xor_sync(LG_FULL_MASK, nb, o);
+  if ((threadIdx.x & 31) == 0) {
     if (flags) atomicOr(err, flags);
-    if (w) atomicMax(max_w, wmax);
-    if (dmax) atomicMax(max_deg, (unsigned long long)dmax);
+    if (w && wmax) atomicMax(max_w, wmax);
+    if (nb) atomicAdd(breaks, (unsigned long long)nb);
   }
+}
+
+__global__ void k_validate_sorted(const unsigned long long* breaks, const unsigned long long* start_breaks, int* err) {
+  if (threadIdx.x == 0 && breaks[0] != start_breaks[0]) atomicOr(err, DERR_UNSORTED);
 }
 
 cudaError_t enc_validate(const uint64_t* rp, const uint32_t* col, const uint32_t* w, uint64_t n, uint64_t arcs,
                          uint32_t wbits, int* err, unsigned long long* max_deg, uint32_t* max_w, cudaStream_t st) {
-  k_validate<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(rp, col, w, n, arcs, wbits, err, max_deg, max_w);
+  // two counters after max_w in the caller's zeroed 64-byte block
+  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(err) + 24);
+  k_validate_rows<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(rp, col, n, arcs, err, max_deg, cnt + 1);
+  count_launch();
+  const bool vec = ((reinterpret_cast<uintptr_t>(col) | reinterpret_cast<uintptr_t>(w)) & 15) == 0;
+  const unsigned grid = grid_for((arcs + 3) / 4, 256, 152 * 16);
+  if (vec) k_validate_arcs<true><<<grid, 256, 0, st>>>(col, w, n, arcs, wbits, err, max_w, cnt);
+  else k_validate_arcs<false><<<grid, 256, 0, st>>>(col, w, n, arcs, wbits, err, max_w, cnt);
+  count_launch();
+  k_validate_sorted<<<1, 32, 0, st>>>(cnt, cnt + 1, err);
   count_launch();
   return cudaGetLastError();
 }
@@ -204,8 +252,8 @@ __global__ void __launch_bounds__(256) k_local_lengths(const uint64_t* __restric
     if (mv < n) { mlo = rp[mv]; mhi = rp[mv + 1]; }
     uint32_t mw = 0;  // lane l ends with the width of row v0 + l
     if (!gap && mv < n && mhi > mlo) mw = max(1u, bits_u32(col[mhi - 1]));
-    const int rows = (int)min((uint64_t)32, n - v0);
     if (gap) {
+      const int rows = (int)min((uint64_t)32, n - v0);
       for (int r = 0; r < rows; r++) {
         const uint64_t lo = __shfl_sync(LG_FULL_MASK, mlo, r), hi = __shfl_sync(LG_FULL_MASK, mhi, r);
         if (hi - lo < 2) continue;
