@@ -140,6 +140,12 @@ __device__ __forceinline__ float ldg_gather(const float* p, uint64_t pol) {
   asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
   return v;
 }
+// one 32-bit word with an L2 cache policy
+__device__ __forceinline__ uint32_t ldg_hint(const uint32_t* p, uint64_t pol) {
+  uint32_t v;
+  asm("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+  return v;
+}
 // four consecutive floats (16-byte aligned), same policy
 __device__ __forceinline__ float4 ldg_gather4(const float* p, uint64_t pol) {
   float4 v;

@@ -342,27 +342,12 @@ cudaError_t enc_pack_u64(const uint64_t* vals, uint64_t count, uint32_t w, uint6
 }
 
 // =========================================================================
-// variable-width local packing (Sections 3.2.2 / 3.6): each CTA owns a window
-// of PW u64 output words, finds the neighborhoods overlapping it by binary
-// search on the bit offsets x, ORs the overlapping fields into shared memory
-// (clipped to the window) and writes the window out.  Differences are
-// independent of each other, so any field can be produced without a prefix.
+// variable-width local packing (Sections 3.2.2 / 3.6).  Differences are
+// independent of each other, so any field can be produced without a prefix;
+// a table of the vertex holding the first bit of every PW-word window bounds
+// the search for the vertex holding any given bit.
 // =========================================================================
 constexpr int PW = 1024;
-
-// OR a w <= 32 bit field at stream bit p into the window (32-bit words
-// [w0, w0 + wcnt) of the stream), dropping the parts outside it
-__device__ __forceinline__ void put_clip(uint32_t* win, uint64_t w0, uint64_t wcnt, uint64_t p, uint32_t wbits,
-                                         uint32_t val) {
-  if (wbits == 0) return;
-  const uint64_t q0 = p >> 5;
-  const uint32_t sh = (uint32_t)p & 31u;
-  if (q0 >= w0 && q0 < w0 + wcnt) atomicOr(&win[q0 - w0], val << sh);
-  if (sh + wbits > 32) {
-    const uint64_t q1 = q0 + 1;
-    if (q1 >= w0 && q1 < w0 + wcnt) atomicOr(&win[q1 - w0], val >> (32 - sh));
-  }
-}
 
 // first[w] = the vertex whose bit range holds the first bit of window w
 // (x strictly increasing in the local modes: every neighborhood has a header)
@@ -375,66 +360,87 @@ __global__ void k_window_first(const uint64_t* __restrict__ x, uint64_t n, uint6
   }
 }
 
+// Each thread owns RW consecutive output words (bits [b0, b1)): it finds the
+// vertex holding bit b0 (binary search between the window table's bounds) and
+// writes its bits sequentially -- the stream is dense, so after the first
+// (clipped) field every field starts where the previous one ended: one shift,
+// one OR and, when a word fills up, one store per field.  Every word has one
+// writer: no atomics.
+constexpr int RW = 8;
+
+struct RunWriter {
+  uint64_t* out;
+  uint64_t b0;    // first bit of the run
+  uint64_t wq;    // next output word
+  uint64_t wend;  // one past the run's last word
+  uint64_t acc;   // bits of word wq gathered so far
+  uint32_t fill;  // how many
+  // field [p, p + w) (w <= 32); returns true once the run is complete
+  __device__ __forceinline__ bool emit(uint64_t p, uint32_t w, uint64_t val) {
+    if (p + w <= b0) return false;
+    if (p < b0) {  // the field straddling the run's first bit
+      val >>= (b0 - p);
+      w -= (uint32_t)(b0 - p);
+    }
+    acc |= val << fill;
+    if (fill + w >= 64) {
+      __stcs(out + wq, acc);
+      wq++;
+      acc = fill ? (val >> (64u - fill)) : 0;
+      fill = fill + w - 64;
+      return wq >= wend;
+    }
+    fill += w;
+    return false;
+  }
+};
+
+template <bool GAP>
 __global__ void __launch_bounds__(256) k_pack_local(const uint64_t* __restrict__ rp, const uint32_t* __restrict__ col,
                                                     const uint64_t* __restrict__ x, const uint8_t* __restrict__ wid,
-                                                    const uint32_t* __restrict__ first, uint64_t n, int gap,
+                                                    const uint32_t* __restrict__ first, uint64_t nwin, uint64_t n,
                                                     uint32_t s, uint32_t H, uint64_t* __restrict__ out,
                                                     uint64_t data_words) {
-  __shared__ uint32_t win[2 * PW];
-  const uint64_t w0 = (uint64_t)blockIdx.x * PW;
-  const uint64_t wcnt = min((uint64_t)PW, data_words - w0);
-  const uint64_t b0 = w0 * 64, b1 = (w0 + wcnt) * 64;
-  const uint64_t v0w = 2 * w0, v0c = 2 * wcnt;  // the window in 32-bit words
-  for (int i = threadIdx.x; i < 2 * PW; i += blockDim.x) win[i] = 0;
-  __syncthreads();
-  // vertices overlapping [b0, b1): from the owner of b0 up to (and including)
-  // the owner of the next window's first bit
-  const uint64_t vb = first[blockIdx.x];
-  const uint64_t ve = (blockIdx.x + 1 < gridDim.x) ? (uint64_t)first[blockIdx.x + 1] + 1 : n;
-  // warps take 32 vertices at a time: lane r owns vertex vb + 32 t + r (header,
-  // first ID, field range inside the window), then the warp packs the fields of
-  // all 32 flattened
-  __shared__ uint64_t pre_s[8][33];
-  __shared__ uint64_t fs_s[8][32], src_s[8][32];
-  __shared__ uint32_t w_s[8][32];
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const uint64_t vend = ve < n ? ve : n;
-  for (uint64_t v0 = vb + 32 * (uint64_t)wp; v0 < vend; v0 += 32 * (uint64_t)nw) {
-    const uint64_t v = v0 + lane;
-    uint64_t cnt = 0, fs = 0, src = 0;
-    uint32_t wv = 0;
-    if (v < vend) {
-      const uint64_t lo = rp[v], d = rp[v + 1] - lo;
-      wv = wid[v];
+  const uint64_t nruns = (data_words + RW - 1) / RW;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nruns; r += stride) {
+    const uint64_t w0 = r * RW;
+    RunWriter rw{out, w0 * 64, w0, min(w0 + RW, data_words), 0, 0};
+    const uint64_t b1 = rw.wend * 64;
+    const uint64_t win = w0 / PW;
+    uint64_t lo = first[win];
+    uint64_t hi = win + 1 < nwin ? (uint64_t)first[win + 1] : n - 1;  // inclusive
+    while (lo < hi) {  // last v in [lo, hi] with x[v] <= b0
+      const uint64_t m = (lo + hi + 1) >> 1;
+      if (x[m] <= rw.b0) lo = m; else hi = m - 1;
+    }
+    bool done = false;
+    for (uint64_t v = lo; v < n && !done; v++) {
       const uint64_t base = x[v];
-      put_clip(win, v0w, v0c, base, H, wv);
-      if (gap && d >= 1) put_clip(win, v0w, v0c, base + H, s, col[lo]);
-      // fields k = 0.. of width wv starting at fs: IDs (local) or differences (gap)
-      fs = base + H + (gap ? s : 0);
-      const uint64_t nf = gap ? (d >= 1 ? d - 1 : 0) : d;
-      if (nf && wv) {
-        const uint64_t klo = b0 > fs ? (b0 - fs) / wv : 0;
-        const uint64_t khi = min(nf, b1 > fs ? (b1 - fs + wv - 1) / wv : 0);
-        if (khi > klo) {
-          cnt = khi - klo;
-          fs += klo * wv;       // bit of the first field inside the window
-          src = lo + klo;       // col index of that field (gap: its left neighbor)
+      if (base >= b1) break;
+      const uint64_t rlo = rp[v], d = rp[v + 1] - rlo;
+      const uint32_t wv = wid[v];
+      done = rw.emit(base, H, wv);
+      uint64_t fs = base + H;
+      if (GAP && d >= 1 && !done) {
+        done = rw.emit(fs, s, col[rlo]);
+        fs += s;
+      }
+      const uint64_t nf = GAP ? (d >= 1 ? d - 1 : 0) : d;
+      if (nf && wv && !done) {
+        uint64_t k = rw.b0 > fs ? (rw.b0 - fs) / wv : 0;
+        for (; k < nf && !done; k++) {
+          const uint32_t val = GAP ? col[rlo + k + 1] - col[rlo + k] : col[rlo + k];
+          done = rw.emit(fs + k * wv, wv, val);
         }
       }
     }
-    fs_s[wp][lane] = fs;
-    src_s[wp][lane] = src;
-    w_s[wp][lane] = wv;
-    warp_flat(pre_s[wp], cnt, [&](int r, uint64_t k) {
-      const uint64_t j = src_s[wp][r] + k;
-      const uint32_t wr = w_s[wp][r];
-      const uint32_t val = gap ? col[j + 1] - col[j] : col[j];
-      put_clip(win, v0w, v0c, fs_s[wp][r] + k * wr, wr, val);
-    });
+    // the stream ended inside the run: its last partial word, then zeros
+    if (rw.wq < rw.wend) {
+      __stcs(out + rw.wq, rw.acc);
+      for (uint64_t q = rw.wq + 1; q < rw.wend; q++) __stcs(out + q, 0ull);
+    }
   }
-  __syncthreads();
-  for (uint64_t i = threadIdx.x; i < wcnt; i += blockDim.x)
-    out[w0 + i] = (uint64_t)win[2 * i] | ((uint64_t)win[2 * i + 1] << 32);
 }
 
 cudaError_t enc_pack_local(const uint64_t* rp, const uint32_t* col, const uint64_t* x, const uint8_t* wid, uint64_t n,
@@ -446,7 +452,9 @@ cudaError_t enc_pack_local(const uint64_t* rp, const uint32_t* col, const uint64
   if (e != cudaSuccess) return e;
   k_window_first<<<grid_for(n, 256, 152 * 32), 256, 0, st>>>(x, n, nwin, first);
   count_launch();
-  k_pack_local<<<(unsigned)nwin, 256, 0, st>>>(rp, col, x, wid, first, n, gap, s, H, out, data_words);
+  const unsigned grid = grid_for((data_words + RW - 1) / RW, 256, 152 * 32);
+  if (gap) k_pack_local<true><<<grid, 256, 0, st>>>(rp, col, x, wid, first, nwin, n, s, H, out, data_words);
+  else k_pack_local<false><<<grid, 256, 0, st>>>(rp, col, x, wid, first, nwin, n, s, H, out, data_words);
   count_launch();
   e = cudaGetLastError();
   cudaFreeAsync(first, st);

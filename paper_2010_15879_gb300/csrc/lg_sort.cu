@@ -387,19 +387,23 @@ __global__ void k_dm_perm(const uint32_t* __restrict__ inv, uint64_t n, uint32_t
   }
 }
 // one warp per new row: copy the old row mapped through perm (rows are sorted
-// afterwards; one row per warp keeps the most independent rows in flight)
+// afterwards; one row per warp keeps the most independent rows in flight).
+// The rows stream through L2 (evict-first loads, streaming stores) so that the
+// randomly gathered perm array stays resident (evict-last).
 __global__ void __launch_bounds__(256) k_dm_scatter(const uint64_t* __restrict__ rp, const uint32_t* __restrict__ col,
                                                     const uint32_t* __restrict__ w, const uint32_t* __restrict__ inv,
                                                     const uint32_t* __restrict__ perm, const uint64_t* __restrict__ nrp,
                                                     uint32_t* __restrict__ ncol, uint32_t* __restrict__ nw, uint64_t n) {
   const int lane = threadIdx.x & 31;
   const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  const uint64_t pstream = policy_stream(), pkeep = policy_keep();
   for (uint64_t i = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
     const uint32_t v = inv[i];
     const uint64_t lo = rp[v], d = rp[v + 1] - lo, o = nrp[i];
     for (uint64_t k = lane; k < d; k += 32) {
-      ncol[o + k] = perm[col[lo + k]];
-      if (w) nw[o + k] = w[lo + k];
+      const uint32_t c = ldg_hint(col + lo + k, pstream);
+      __stcs(ncol + o + k, ldg_hint(perm + c, pkeep));
+      if (w) __stcs(nw + o + k, ldg_hint(w + lo + k, pstream));
     }
   }
 }
