@@ -135,25 +135,55 @@ cudaError_t radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, u
 constexpr uint32_t SEG_SMALL = 32;    // one warp per row, bitonic network in registers
 constexpr uint32_t SEG_MEDIUM = 8192; // one CTA per row, bitonic in shared memory
 
-template <bool VALS>
-__device__ __forceinline__ void warp_bitonic_t(uint32_t& key, uint32_t& val) {
-  const int lane = threadIdx.x & 31;
+// bitonic sort of each aligned group of W lanes (ascending within the group)
+template <int W, bool VALS>
+__device__ __forceinline__ void warp_bitonic_w(uint32_t& key, uint32_t& val) {
+  const int li = threadIdx.x & (W - 1);
 #pragma unroll
-  for (int k = 2; k <= 32; k <<= 1) {
+  for (int k = 2; k <= W; k <<= 1) {
 #pragma unroll
     for (int j = k >> 1; j > 0; j >>= 1) {
       const uint32_t ok = __shfl_xor_sync(LG_FULL_MASK, key, j);
       uint32_t ov = 0;
       if (VALS) ov = __shfl_xor_sync(LG_FULL_MASK, val, j);
-      const bool up = ((lane & k) == 0);
-      const bool lower = ((lane & j) == 0);
+      const bool up = ((li & k) == 0);
+      const bool lower = ((li & j) == 0);
       const bool take_other = lower ? (up ? (ok < key) : (ok > key)) : (up ? (ok > key) : (ok < key));
       if (take_other) { key = ok; if (VALS) val = ov; }
     }
   }
 }
 
-// rows of <= 32 keys: one warp per row, 32 rows per warp batch
+// sort the rows whose bits are set in `todo` (each of <= W keys): 32 / W rows
+// at a time, lane group g taking the g-th next row
+template <int W, bool VALS>
+__device__ __forceinline__ void sort_rows_w(uint32_t todo, uint64_t mlo, uint64_t md, uint32_t* keys,
+                                            uint32_t* vals) {
+  const int lane = threadIdx.x & 31;
+  const int grp = lane / W, li = lane & (W - 1);
+  while (todo) {
+    int src = -1;  // the row of this lane's group in this round
+#pragma unroll
+    for (int g = 0; g < 32 / W; g++) {
+      const int r = todo ? __ffs(todo) - 1 : -1;
+      if (r >= 0) todo &= todo - 1;
+      if (g == grp) src = r;
+    }
+    const uint64_t lo = __shfl_sync(LG_FULL_MASK, mlo, src < 0 ? 0 : src);
+    uint64_t d = __shfl_sync(LG_FULL_MASK, md, src < 0 ? 0 : src);
+    if (src < 0) d = 0;
+    uint32_t key = (uint64_t)li < d ? keys[lo + li] : 0xffffffffu;
+    uint32_t val = (VALS && (uint64_t)li < d) ? vals[lo + li] : 0u;
+    warp_bitonic_w<W, VALS>(key, val);
+    if ((uint64_t)li < d) {
+      keys[lo + li] = key;
+      if (VALS) vals[lo + li] = val;
+    }
+  }
+}
+
+// rows of <= 32 keys, 32 rows per warp batch: rows of <= 8 keys four at a
+// time (8-lane networks), <= 16 two at a time, the rest one per warp
 template <bool VALS>
 __global__ void __launch_bounds__(256) k_seg_small(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                                                    const uint64_t* __restrict__ off, uint64_t rows) {
@@ -163,19 +193,9 @@ __global__ void __launch_bounds__(256) k_seg_small(uint32_t* __restrict__ keys, 
     const uint64_t mr = r0 + lane;
     uint64_t mlo = 0, md = 0;
     if (mr < rows) { mlo = off[mr]; md = off[mr + 1] - mlo; }
-    uint32_t todo = __ballot_sync(LG_FULL_MASK, md > 1 && md <= SEG_SMALL);
-    while (todo) {
-      const int r = __ffs(todo) - 1;
-      todo &= todo - 1;
-      const uint64_t lo = __shfl_sync(LG_FULL_MASK, mlo, r), d = __shfl_sync(LG_FULL_MASK, md, r);
-      uint32_t key = lane < d ? keys[lo + lane] : 0xffffffffu;
-      uint32_t val = (VALS && lane < d) ? vals[lo + lane] : 0u;
-      warp_bitonic_t<VALS>(key, val);
-      if (lane < d) {
-        keys[lo + lane] = key;
-        if (VALS) vals[lo + lane] = val;
-      }
-    }
+    sort_rows_w<8, VALS>(__ballot_sync(LG_FULL_MASK, md > 1 && md <= 8), mlo, md, keys, vals);
+    sort_rows_w<16, VALS>(__ballot_sync(LG_FULL_MASK, md > 8 && md <= 16), mlo, md, keys, vals);
+    sort_rows_w<32, VALS>(__ballot_sync(LG_FULL_MASK, md > 16 && md <= SEG_SMALL), mlo, md, keys, vals);
   }
 }
 
