@@ -132,115 +132,276 @@ cudaError_t radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, u
 // =========================================================================
 // segmented sort of CSR rows
 // =========================================================================
-constexpr uint32_t SEG_SMALL = 32;    // one warp per row, bitonic network in registers
-constexpr uint32_t SEG_MEDIUM = 8192; // one CTA per row, bitonic in shared memory
+constexpr uint32_t SEG_SMALL = 32;    // one thread per row, sorting network in registers
+constexpr uint32_t SEG_MEDIUM = 4096; // 16 keys per lane, 4 lanes .. 8 warps per row
+constexpr int SROW = 33;              // shared slot stride of a small row (conflict-free lanes)
 
-// bitonic sort of each aligned group of W lanes (ascending within the group)
-template <int W, bool VALS>
-__device__ __forceinline__ void warp_bitonic_w(uint32_t& key, uint32_t& val) {
-  const int li = threadIdx.x & (W - 1);
+// compare-exchange into ascending order, without branches
+template <bool VALS>
+__device__ __forceinline__ void ce_asc(uint32_t& a, uint32_t& b, uint32_t& va, uint32_t& vb) {
+  if (VALS) {
+    const bool sw = a > b;
+    const uint32_t ta = sw ? b : a, tb = sw ? a : b;
+    const uint32_t tva = sw ? vb : va, tvb = sw ? va : vb;
+    a = ta; b = tb; va = tva; vb = tvb;
+  } else {
+    const uint32_t lo = min(a, b), hi = max(a, b);
+    a = lo; b = hi;
+  }
+}
+
+// compare-exchange into ascending (up) or descending order
+template <bool VALS>
+__device__ __forceinline__ void ce_dir(uint32_t& a, uint32_t& b, uint32_t& va, uint32_t& vb, bool up) {
+  if (VALS) {
+    const bool sw = up ? (a > b) : (a < b);
+    const uint32_t ta = sw ? b : a, tb = sw ? a : b;
+    const uint32_t tva = sw ? vb : va, tvb = sw ? va : vb;
+    a = ta; b = tb; va = tva; vb = tvb;
+  } else {
+    const uint32_t lo = min(a, b), hi = max(a, b);
+    a = up ? lo : hi; b = up ? hi : lo;
+  }
+}
+
+// Batcher's odd-even merge sort network on N = 2^m registers (19, 63 and 191
+// comparators for N = 8, 16, 32): merges of sorted runs of length p into runs
+// of 2p, each merge comparing elements k apart for k = p, p/2, .., 1 within
+// the same 2p-run.  One instantiation per (p, k), so that every register
+// index is a compile-time constant.
+template <int N, bool VALS, int P, int K>
+__device__ __forceinline__ void oem_pk(uint32_t (&x)[N], uint32_t (&y)[N]) {
+  if constexpr (P < N) {
+    if constexpr (K == 0) {
+      oem_pk<N, VALS, 2 * P, 2 * P>(x, y);
+    } else {
 #pragma unroll
-  for (int k = 2; k <= W; k <<= 1) {
+      for (int j = K % P; j + K < N; j += 2 * K) {
 #pragma unroll
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      const uint32_t ok = __shfl_xor_sync(LG_FULL_MASK, key, j);
-      uint32_t ov = 0;
-      if (VALS) ov = __shfl_xor_sync(LG_FULL_MASK, val, j);
-      const bool up = ((li & k) == 0);
-      const bool lower = ((li & j) == 0);
-      const bool take_other = lower ? (up ? (ok < key) : (ok > key)) : (up ? (ok > key) : (ok < key));
-      if (take_other) { key = ok; if (VALS) val = ov; }
+        for (int i = 0; i < K; i++) {
+          if (i + j + K < N && (i + j) / (2 * P) == (i + j + K) / (2 * P))
+            ce_asc<VALS>(x[i + j], x[i + j + K], y[i + j], y[i + j + K]);
+        }
+      }
+      oem_pk<N, VALS, P, K / 2>(x, y);
     }
   }
 }
 
-// sort the rows whose bits are set in `todo` (each of <= W keys): 32 / W rows
-// at a time, lane group g taking the g-th next row
-template <int W, bool VALS>
-__device__ __forceinline__ void sort_rows_w(uint32_t todo, uint64_t mlo, uint64_t md, uint32_t* keys,
-                                            uint32_t* vals) {
-  const int lane = threadIdx.x & 31;
-  const int grp = lane / W, li = lane & (W - 1);
-  while (todo) {
-    int src = -1;  // the row of this lane's group in this round
+template <int N, bool VALS>
+__device__ __forceinline__ void oem_sort(uint32_t (&x)[N], uint32_t (&y)[N]) {
+  oem_pk<N, VALS, 1, 1>(x, y);
+}
+
+// one thread sorts the d <= N keys of its shared slot (padded with UINT32_MAX)
+template <int N, bool VALS>
+__device__ __forceinline__ void slot_sort(uint32_t* sk, uint32_t* sv, uint32_t d) {
+  uint32_t x[N], y[N];
 #pragma unroll
-    for (int g = 0; g < 32 / W; g++) {
-      const int r = todo ? __ffs(todo) - 1 : -1;
-      if (r >= 0) todo &= todo - 1;
-      if (g == grp) src = r;
-    }
-    const uint64_t lo = __shfl_sync(LG_FULL_MASK, mlo, src < 0 ? 0 : src);
-    uint64_t d = __shfl_sync(LG_FULL_MASK, md, src < 0 ? 0 : src);
-    if (src < 0) d = 0;
-    uint32_t key = (uint64_t)li < d ? keys[lo + li] : 0xffffffffu;
-    uint32_t val = (VALS && (uint64_t)li < d) ? vals[lo + li] : 0u;
-    warp_bitonic_w<W, VALS>(key, val);
-    if ((uint64_t)li < d) {
-      keys[lo + li] = key;
-      if (VALS) vals[lo + li] = val;
+  for (int t = 0; t < N; t++) {
+    x[t] = (uint32_t)t < d ? sk[t] : 0xffffffffu;
+    y[t] = (VALS && (uint32_t)t < d) ? sv[t] : 0u;
+  }
+  oem_sort<N, VALS>(x, y);
+#pragma unroll
+  for (int t = 0; t < N; t++) {
+    if ((uint32_t)t < d) {
+      sk[t] = x[t];
+      if (VALS) sv[t] = y[t];
     }
   }
 }
 
-// rows of <= 32 keys, 32 rows per warp batch: rows of <= 8 keys four at a
-// time (8-lane networks), <= 16 two at a time, the rest one per warp
+// Each lane sorts slot `lane` (d keys, d <= 32) of its warp's 32 shared slots.
+// A warp runs at most two networks: 8 keys, and 16 or 32 (32 if any of its
+// rows needs it).
+template <bool VALS>
+__device__ __forceinline__ void warp_sort_slots(uint32_t* sk, uint32_t* sv, uint32_t d, bool small, int lane) {
+  const bool any32 = __any_sync(LG_FULL_MASK, small && d > 16);
+  if (small && d > 1) {
+    uint32_t* k = sk + lane * SROW;
+    uint32_t* v = sv + lane * SROW;
+    if (d <= 8) slot_sort<8, VALS>(k, v, d);
+    else if (any32) slot_sort<32, VALS>(k, v, d);
+    else slot_sort<16, VALS>(k, v, d);
+  }
+  __syncwarp();
+}
+
+// rows of <= 32 keys, in place: a warp takes 32 consecutive rows, copies the
+// small ones into its shared slots (coalesced, a row per step), sorts a row
+// per lane and copies them back.
 template <bool VALS>
 __global__ void __launch_bounds__(256) k_seg_small(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                                                    const uint64_t* __restrict__ off, uint64_t rows) {
+  extern __shared__ uint32_t ssm[];  // 8 warps x 32 slots of keys, then of values
   const int lane = threadIdx.x & 31;
+  uint32_t* sk = ssm + (threadIdx.x >> 5) * 32 * SROW;
+  uint32_t* sv = ssm + 8 * 32 * SROW + (threadIdx.x >> 5) * 32 * SROW;
   const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-  for (uint64_t r0 = ((uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; r0 < rows; r0 += warps * 32) {
-    const uint64_t mr = r0 + lane;
-    uint64_t mlo = 0, md = 0;
-    if (mr < rows) { mlo = off[mr]; md = off[mr + 1] - mlo; }
-    sort_rows_w<8, VALS>(__ballot_sync(LG_FULL_MASK, md > 1 && md <= 8), mlo, md, keys, vals);
-    sort_rows_w<16, VALS>(__ballot_sync(LG_FULL_MASK, md > 8 && md <= 16), mlo, md, keys, vals);
-    sort_rows_w<32, VALS>(__ballot_sync(LG_FULL_MASK, md > 16 && md <= SEG_SMALL), mlo, md, keys, vals);
-  }
-}
-
-// one CTA per row, bitonic network in shared memory over P = 2^k >= d keys
-// (padded with UINT32_MAX); blockDim = min(P/2, 256), each thread owns pairs
-__global__ void __launch_bounds__(256) k_seg_bitonic(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
-                                                     const uint64_t* __restrict__ off, const uint32_t* __restrict__ list,
-                                                     uint32_t nlist, uint32_t P) {
-  extern __shared__ uint32_t sm[];
-  uint32_t* sk = sm;
-  uint32_t* sv = sm + P;
-  const uint32_t half = P >> 1;
-  for (uint32_t li = blockIdx.x; li < nlist; li += gridDim.x) {
-    const uint64_t r = list[li];
-    const uint64_t lo = off[r];
-    const uint32_t d = (uint32_t)(off[r + 1] - lo);
-    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
-      sk[i] = i < d ? keys[lo + i] : 0xffffffffu;
-      if (vals) sv[i] = i < d ? vals[lo + i] : 0u;
+  for (uint64_t r0 = ((uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; r0 < rows;
+       r0 += warps * 32) {
+    const uint64_t r = r0 + lane;
+    uint64_t lo = 0;
+    uint32_t d = 0;
+    if (r < rows) {
+      lo = off[r];
+      d = (uint32_t)(off[r + 1] - lo);
     }
-    __syncthreads();
-    for (uint32_t k = 2; k <= P; k <<= 1) {
-      for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-        for (uint32_t t = threadIdx.x; t < half; t += blockDim.x) {
-          const uint32_t i = ((t & ~(j - 1)) << 1) | (t & (j - 1));
-          const uint32_t ixj = i + j;
-          const bool up = (i & k) == 0;
-          const uint32_t a = sk[i], b = sk[ixj];
-          if (up ? (a > b) : (a < b)) {
-            sk[i] = b; sk[ixj] = a;
-            if (vals) { const uint32_t tv = sv[i]; sv[i] = sv[ixj]; sv[ixj] = tv; }
-          }
-        }
-        __syncthreads();
+    const bool small = d > 1 && d <= SEG_SMALL;
+    const uint32_t todo = __ballot_sync(LG_FULL_MASK, small);
+    if (!todo) continue;
+    for (uint32_t t = todo; t; t &= t - 1) {
+      const int q = __ffs(t) - 1;
+      const uint64_t lq = __shfl_sync(LG_FULL_MASK, lo, q);
+      const uint32_t dq = __shfl_sync(LG_FULL_MASK, d, q);
+      if ((uint32_t)lane < dq) {
+        sk[q * SROW + lane] = keys[lq + lane];
+        if (VALS) sv[q * SROW + lane] = vals[lq + lane];
       }
     }
-    for (uint32_t i = threadIdx.x; i < d; i += blockDim.x) {
-      keys[lo + i] = sk[i];
-      if (vals) vals[lo + i] = sv[i];
+    __syncwarp();
+    warp_sort_slots<VALS>(sk, sv, d, small, lane);
+    for (uint32_t t = todo; t; t &= t - 1) {
+      const int q = __ffs(t) - 1;
+      const uint64_t lq = __shfl_sync(LG_FULL_MASK, lo, q);
+      const uint32_t dq = __shfl_sync(LG_FULL_MASK, d, q);
+      if ((uint32_t)lane < dq) {
+        keys[lq + lane] = sk[q * SROW + lane];
+        if (VALS) vals[lq + lane] = sv[q * SROW + lane];
+      }
     }
-    __syncthreads();
+    __syncwarp();
   }
 }
 
-// size class of a row: 0 = warp path (d <= 32), 1..8 = P = 64..8192, 9 = radix
+// ---------------------------------------------------------------------------
+// Rows of 32 < d <= 4096 keys from a size-class list, P = 16 G W >= d keys per
+// row (padded with UINT32_MAX): G lanes per row in a warp (G <= 32), or W
+// warps per row (G = 32).  Lane g of warp w holds keys 16 (32 w + g) + e,
+// e < 16, so a bitonic compare-exchange at distance j is a register pair for
+// j < 16, a shuffle with lane g ^ (j / 16) for 16 <= j < 512 and an exchange
+// through shared memory with warp w ^ (j / 512) beyond.  The first four
+// levels are unrolled; the rest run as a loop (an unrolled network of this
+// size would outgrow the instruction cache).
+// ---------------------------------------------------------------------------
+template <int J, bool VALS>
+__device__ __forceinline__ void blk_pairs(uint32_t (&x)[16], uint32_t (&y)[16], uint32_t base16, uint32_t k) {
+#pragma unroll
+  for (int e = 0; e < 16; e++) {
+    if ((e & J) == 0) ce_dir<VALS>(x[e], x[e | J], y[e], y[e | J], ((base16 | (uint32_t)e) & k) == 0);
+  }
+}
+
+// the four register stages j = 8, 4, 2, 1 of a level k >= 16 (direction set
+// by the lane's block only)
+template <bool VALS>
+__device__ __forceinline__ void blk_tail(uint32_t (&x)[16], uint32_t (&y)[16], bool up) {
+#pragma unroll
+  for (int j = 8; j >= 1; j >>= 1) {
+#pragma unroll
+    for (int e = 0; e < 16; e++) {
+      if ((e & j) == 0) ce_dir<VALS>(x[e], x[e | j], y[e], y[e | j], up);
+    }
+  }
+}
+
+template <bool VALS>
+__device__ __forceinline__ void blk_shfl(uint32_t (&x)[16], uint32_t (&y)[16], uint32_t lanemask, bool keep_min) {
+#pragma unroll
+  for (int e = 0; e < 16; e++) {
+    const uint32_t ok = __shfl_xor_sync(LG_FULL_MASK, x[e], lanemask);
+    if (VALS) {
+      const uint32_t ov = __shfl_xor_sync(LG_FULL_MASK, y[e], lanemask);
+      const bool take = keep_min ? (ok < x[e]) : (ok > x[e]);
+      x[e] = take ? ok : x[e];
+      y[e] = take ? ov : y[e];
+    } else {
+      x[e] = keep_min ? min(x[e], ok) : max(x[e], ok);
+    }
+  }
+}
+
+template <int G, int W, bool VALS>
+__global__ void __launch_bounds__(256) k_seg_blk(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                                 const uint64_t* __restrict__ off, const uint32_t* __restrict__ list,
+                                                 uint32_t nlist) {
+  constexpr uint32_t P = 16u * G * W;
+  constexpr int RPB = 256 / (G * W);  // rows per block pass
+  extern __shared__ uint32_t bsm[];   // W > 1: RPB rows x P keys, then values
+  const int lane = threadIdx.x & 31;
+  const int g = lane % G;
+  const int wv = W > 1 ? (threadIdx.x >> 5) % W : 0;
+  const int grp = threadIdx.x / (G * W);
+  const uint32_t base16 = 16u * (32u * wv + g);
+  uint32_t* gk = bsm + grp * P;
+  uint32_t* gv = bsm + RPB * P + grp * P;
+  for (uint64_t base = (uint64_t)blockIdx.x * RPB; base < nlist; base += (uint64_t)gridDim.x * RPB) {
+    const uint64_t li = base + grp;
+    uint64_t lo = 0;
+    uint32_t d = 0;
+    if (li < nlist) {
+      const uint64_t r = list[li];
+      lo = off[r];
+      d = (uint32_t)(off[r + 1] - lo);
+    }
+    uint32_t x[16], y[16];
+#pragma unroll
+    for (int e = 0; e < 16; e++) {
+      const uint32_t i = base16 + e;
+      x[e] = i < d ? keys[lo + i] : 0xffffffffu;
+      y[e] = (VALS && i < d) ? vals[lo + i] : 0u;
+    }
+    // levels k = 2 .. 16 inside the lane's block
+    blk_pairs<1, VALS>(x, y, base16, 2);
+    blk_pairs<2, VALS>(x, y, base16, 4);
+    blk_pairs<1, VALS>(x, y, base16, 4);
+    blk_pairs<4, VALS>(x, y, base16, 8);
+    blk_pairs<2, VALS>(x, y, base16, 8);
+    blk_pairs<1, VALS>(x, y, base16, 8);
+    blk_tail<VALS>(x, y, (base16 & 16u) == 0);
+#pragma unroll 1
+    for (uint32_t k = 32; k <= P; k <<= 1) {
+      const bool up = (base16 & k) == 0;
+#pragma unroll 1
+      for (uint32_t j = k >> 1; j >= 16; j >>= 1) {
+        if (W > 1 && j >= 512) {  // partner warp wv ^ (j / 512), same lane and register
+          const int jw = (int)(j >> 9);
+          __syncthreads();
+#pragma unroll
+          for (int e = 0; e < 16; e++) {
+            gk[wv * 512 + e * 32 + lane] = x[e];
+            if (VALS) gv[wv * 512 + e * 32 + lane] = y[e];
+          }
+          __syncthreads();
+          const bool keep_min = (((wv & jw) == 0) == up);
+#pragma unroll
+          for (int e = 0; e < 16; e++) {
+            const int at = (wv ^ jw) * 512 + e * 32 + lane;
+            const uint32_t ok = gk[at];
+            const bool take = keep_min ? (ok < x[e]) : (ok > x[e]);
+            if (VALS) y[e] = take ? gv[at] : y[e];
+            x[e] = take ? ok : x[e];
+          }
+        } else {
+          const uint32_t m = j >> 4;
+          blk_shfl<VALS>(x, y, m, ((g & m) == 0) == up);
+        }
+      }
+      blk_tail<VALS>(x, y, up);
+    }
+#pragma unroll
+    for (int e = 0; e < 16; e++) {
+      const uint32_t i = base16 + e;
+      if (i < d) {
+        keys[lo + i] = x[e];
+        if (VALS) vals[lo + i] = y[e];
+      }
+    }
+  }
+}
+
+// size class of a row: 0 = warp path (d <= 32), 1..7 = P = 64..4096, 9 = radix
 __device__ __forceinline__ int seg_class(uint64_t d) {
   if (d <= SEG_SMALL) return 0;
   if (d > SEG_MEDIUM) return 9;
@@ -264,11 +425,21 @@ __global__ void k_seg_count(const uint64_t* __restrict__ off, uint64_t rows, uin
   if (threadIdx.x < SEG_NCLASS && c[threadIdx.x]) atomicAdd(&cnt[threadIdx.x], c[threadIdx.x]);
 }
 
-__global__ void k_seg_fill(const uint64_t* __restrict__ off, uint64_t rows, const uint32_t* __restrict__ base,
-                           uint32_t* __restrict__ cursor, uint32_t* __restrict__ list) {
-  for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += (uint64_t)gridDim.x * blockDim.x) {
-    const int k = seg_class(off[r + 1] - off[r]);
-    if (k) list[base[k] + atomicAdd(&cursor[k], 1u)] = (uint32_t)r;
+__global__ void __launch_bounds__(256) k_seg_fill(const uint64_t* __restrict__ off, uint64_t rows,
+                                                  const uint32_t* __restrict__ base, uint32_t* __restrict__ cursor,
+                                                  uint32_t* __restrict__ list) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t r0 = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); r0 < rows; r0 += stride) {
+    const uint64_t r = r0 + lane;
+    const int k = r < rows ? seg_class(off[r + 1] - off[r]) : 0;
+    // one cursor atomic per class present in the warp
+    const uint32_t peers = __match_any_sync(LG_FULL_MASK, k);
+    const int leader = __ffs(peers) - 1;
+    uint32_t at = 0;
+    if (k && lane == leader) at = base[k] + atomicAdd(&cursor[k], (uint32_t)__popc(peers));
+    at = __shfl_sync(LG_FULL_MASK, at, leader);
+    if (k) list[at + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)r;
   }
 }
 
@@ -340,16 +511,51 @@ static cudaError_t seg_sort_big(uint32_t* keys, uint32_t* vals, const uint64_t* 
   return e;
 }
 
+template <int G, int W, bool VALS>
+static cudaError_t seg_blk_launch(uint32_t* keys, uint32_t* vals, const uint64_t* off, const uint32_t* list,
+                                  uint32_t nlist, cudaStream_t st) {
+  constexpr int RPB = 256 / (G * W);
+  const size_t smem = W > 1 ? (size_t)RPB * 16 * G * W * sizeof(uint32_t) * (VALS ? 2 : 1) : 0;
+  k_seg_blk<G, W, VALS><<<grid_for(nlist, RPB, 152 * 16), 256, smem, st>>>(keys, vals, off, list, nlist);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// size class k holds rows of 2^(4+k) < d <= 2^(5+k) keys
+template <bool VALS>
+static cudaError_t seg_blk_class(int k, uint32_t* keys, uint32_t* vals, const uint64_t* off, const uint32_t* list,
+                                 uint32_t nlist, cudaStream_t st) {
+  switch (k) {
+    case 1: return seg_blk_launch<4, 1, VALS>(keys, vals, off, list, nlist, st);
+    case 2: return seg_blk_launch<8, 1, VALS>(keys, vals, off, list, nlist, st);
+    case 3: return seg_blk_launch<16, 1, VALS>(keys, vals, off, list, nlist, st);
+    case 4: return seg_blk_launch<32, 1, VALS>(keys, vals, off, list, nlist, st);
+    case 5: return seg_blk_launch<32, 2, VALS>(keys, vals, off, list, nlist, st);
+    case 6: return seg_blk_launch<32, 4, VALS>(keys, vals, off, list, nlist, st);
+    case 7: return seg_blk_launch<32, 8, VALS>(keys, vals, off, list, nlist, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+static cudaError_t seg_small_launch(uint32_t* keys, uint32_t* vals, const uint64_t* off, uint64_t rows,
+                                    cudaStream_t st) {
+  const size_t smem = (size_t)8 * 32 * SROW * sizeof(uint32_t) * (vals ? 2 : 1);
+  if (vals) {
+    const cudaError_t e = cudaFuncSetAttribute(k_seg_small<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  if (vals) k_seg_small<true><<<grid_for(rows, 256, 152 * 16), 256, smem, st>>>(keys, vals, off, rows);
+  else k_seg_small<false><<<grid_for(rows, 256, 152 * 16), 256, smem, st>>>(keys, vals, off, rows);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t segmented_sort(uint32_t* keys, uint32_t* vals, const uint64_t* off, uint64_t rows, uint64_t total,
                            uint64_t max_row, cudaStream_t st, bool small_done) {
   if (rows == 0 || total == 0 || max_row <= 1) return cudaSuccess;
   cudaError_t e;
-  if (!small_done) {
-    if (vals) k_seg_small<true><<<grid_for(rows, 256, 152 * 16), 256, 0, st>>>(keys, vals, off, rows);
-    else k_seg_small<false><<<grid_for(rows, 256, 152 * 16), 256, 0, st>>>(keys, vals, off, rows);
-    count_launch();
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
+  if (!small_done && (e = seg_small_launch(keys, vals, off, rows, st)) != cudaSuccess) return e;
   if (max_row <= SEG_SMALL) return cudaSuccess;
   // rows by power-of-two size class
   uint32_t* meta = nullptr;  // cnt[10], base[10], cursor[10]
@@ -370,16 +576,9 @@ cudaError_t segmented_sort(uint32_t* keys, uint32_t* vals, const uint64_t* off, 
   cudaMemcpyAsync(meta + SEG_NCLASS, base, sizeof(base), cudaMemcpyHostToDevice, st);
   k_seg_fill<<<grid_for(rows, 256, 152 * 16), 256, 0, st>>>(off, rows, meta + SEG_NCLASS, meta + 2 * SEG_NCLASS, list);
   count_launch();
-  for (int k = 1; k <= 8 && e == cudaSuccess; k++) {
-    if (!cnt[k]) continue;
-    const uint32_t P = 32u << k;
-    const unsigned threads = P / 2 < 256 ? P / 2 : 256;
-    const size_t smem = (size_t)P * sizeof(uint32_t) * (vals ? 2 : 1);
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k_seg_bitonic, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_seg_bitonic<<<grid_for(cnt[k], 1, 152 * 32), threads, smem, st>>>(keys, vals, off, list + base[k], cnt[k], P);
-    count_launch();
-    e = cudaGetLastError();
-  }
+  for (int k = 1; k <= 7 && e == cudaSuccess; k++)
+    if (cnt[k]) e = vals ? seg_blk_class<true>(k, keys, vals, off, list + base[k], cnt[k], st)
+                         : seg_blk_class<false>(k, keys, vals, off, list + base[k], cnt[k], st);
   if (e == cudaSuccess && cnt[9]) e = seg_sort_big(keys, vals, off, list + base[9], cnt[9], st);
   cudaFreeAsync(list, st);
   cudaFreeAsync(meta, st);
@@ -406,24 +605,82 @@ __global__ void k_dm_perm(const uint32_t* __restrict__ inv, uint64_t n, uint32_t
     newdeg[i] = (uint32_t)(rp[v + 1] - rp[v]);
   }
 }
-// one warp per new row: copy the old row mapped through perm (rows are sorted
-// afterwards; one row per warp keeps the most independent rows in flight).
-// The rows stream through L2 (evict-first loads, streaming stores) so that the
+// New rows P(v) = { P(u) : u in N_v }.  A warp takes 32 consecutive new rows.
+// Rows of <= 32 arcs are gathered into the warp's shared slots (a row per
+// step, coalesced reads of the old row, four rows' perm lookups in flight),
+// sorted one per lane in registers and written out coalesced, so they are
+// final here.  Longer rows are copied unsorted (the size-class sorts follow).
+// Rows stream through L2 (evict-first loads, streaming stores) so that the
 // randomly gathered perm array stays resident (evict-last).
-__global__ void __launch_bounds__(256) k_dm_scatter(const uint64_t* __restrict__ rp, const uint32_t* __restrict__ col,
-                                                    const uint32_t* __restrict__ w, const uint32_t* __restrict__ inv,
-                                                    const uint32_t* __restrict__ perm, const uint64_t* __restrict__ nrp,
-                                                    uint32_t* __restrict__ ncol, uint32_t* __restrict__ nw, uint64_t n) {
+template <bool VALS>
+__global__ void __launch_bounds__(256) k_dm_rows(const uint64_t* __restrict__ rp, const uint32_t* __restrict__ col,
+                                                 const uint32_t* __restrict__ w, const uint32_t* __restrict__ inv,
+                                                 const uint32_t* __restrict__ perm, const uint64_t* __restrict__ nrp,
+                                                 uint32_t* __restrict__ ncol, uint32_t* __restrict__ nw, uint64_t n) {
+  extern __shared__ uint32_t dsm[];  // 8 warps x 32 slots of keys, then of weights
   const int lane = threadIdx.x & 31;
+  uint32_t* sk = dsm + (threadIdx.x >> 5) * 32 * SROW;
+  uint32_t* sv = dsm + 8 * 32 * SROW + (threadIdx.x >> 5) * 32 * SROW;
   const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
   const uint64_t pstream = policy_stream(), pkeep = policy_keep();
-  for (uint64_t i = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
-    const uint32_t v = inv[i];
-    const uint64_t lo = rp[v], d = rp[v + 1] - lo, o = nrp[i];
-    for (uint64_t k = lane; k < d; k += 32) {
-      const uint32_t c = ldg_hint(col + lo + k, pstream);
-      __stcs(ncol + o + k, ldg_hint(perm + c, pkeep));
-      if (w) __stcs(nw + o + k, ldg_hint(w + lo + k, pstream));
+  for (uint64_t i0 = ((uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; i0 < n;
+       i0 += warps * 32) {
+    const uint64_t i = i0 + lane;
+    uint64_t lo = 0, o = 0;
+    uint32_t d = 0;
+    if (i < n) {
+      const uint32_t v = inv[i];
+      lo = rp[v];
+      d = (uint32_t)(rp[v + 1] - lo);
+      o = nrp[i];
+    }
+    const bool small = d <= SEG_SMALL;
+    const uint32_t todo = __ballot_sync(LG_FULL_MASK, small && d > 0);
+    for (uint32_t t = todo; t;) {
+      int q[4];
+      uint32_t c[4];
+      bool on[4];
+#pragma unroll
+      for (int z = 0; z < 4; z++) {
+        q[z] = t ? __ffs(t) - 1 : 0;
+        on[z] = t != 0;
+        if (t) t &= t - 1;
+      }
+#pragma unroll
+      for (int z = 0; z < 4; z++) {
+        const uint64_t lq = __shfl_sync(LG_FULL_MASK, lo, q[z]);
+        const uint32_t dq = __shfl_sync(LG_FULL_MASK, d, q[z]);
+        on[z] = on[z] && (uint32_t)lane < dq;
+        c[z] = on[z] ? ldg_hint(col + lq + lane, pstream) : 0u;
+        if (VALS && on[z]) sv[q[z] * SROW + lane] = ldg_hint(w + lq + lane, pstream);
+      }
+#pragma unroll
+      for (int z = 0; z < 4; z++) {
+        if (on[z]) sk[q[z] * SROW + lane] = ldg_hint(perm + c[z], pkeep);
+      }
+    }
+    __syncwarp();
+    warp_sort_slots<VALS>(sk, sv, d, small, lane);
+    for (uint32_t t = todo; t; t &= t - 1) {
+      const int q = __ffs(t) - 1;
+      const uint64_t oq = __shfl_sync(LG_FULL_MASK, o, q);
+      const uint32_t dq = __shfl_sync(LG_FULL_MASK, d, q);
+      if ((uint32_t)lane < dq) {
+        __stcs(ncol + oq + lane, sk[q * SROW + lane]);
+        if (VALS) __stcs(nw + oq + lane, sv[q * SROW + lane]);
+      }
+    }
+    __syncwarp();
+    for (uint32_t t = __ballot_sync(LG_FULL_MASK, !small); t; t &= t - 1) {
+      const int q = __ffs(t) - 1;
+      const uint64_t lq = __shfl_sync(LG_FULL_MASK, lo, q);
+      const uint64_t oq = __shfl_sync(LG_FULL_MASK, o, q);
+      const uint32_t dq = __shfl_sync(LG_FULL_MASK, d, q);
+      for (uint32_t k = lane; k < dq; k += 32) {
+        const uint32_t cc = ldg_hint(col + lq + k, pstream);
+        __stcs(ncol + oq + k, ldg_hint(perm + cc, pkeep));
+        if (VALS) __stcs(nw + oq + k, ldg_hint(w + lq + k, pstream));
+      }
     }
   }
 }
@@ -526,11 +783,19 @@ cudaError_t enc_dm_relabel(const uint64_t* rp, const uint32_t* col, const uint32
     e = scan_excl_u32(newdeg, n, nrp, stmp, st);
   }
   if (e == cudaSuccess) {
-    k_dm_scatter<<<grid_for(n, 8, 152 * 64), 256, 0, st>>>(rp, col, w, inv_perm, perm, nrp, ncol, nw, n);
+    const size_t smem = (size_t)8 * 32 * SROW * sizeof(uint32_t) * (w ? 2 : 1);
+    if (w) {
+      e = cudaFuncSetAttribute(k_dm_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess)
+        k_dm_rows<true><<<grid_for(n, 256, 152 * 16), 256, smem, st>>>(rp, col, w, inv_perm, perm, nrp, ncol, nw, n);
+    } else {
+      k_dm_rows<false><<<grid_for(n, 256, 152 * 16), 256, smem, st>>>(rp, col, w, inv_perm, perm, nrp, ncol, nw, n);
+    }
     count_launch();
-    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaGetLastError();
   }
-  if (e == cudaSuccess) e = segmented_sort(ncol, w ? nw : nullptr, nrp, n, arcs, max_deg, st);
+  // rows of <= 32 arcs left k_dm_rows sorted
+  if (e == cudaSuccess) e = segmented_sort(ncol, w ? nw : nullptr, nrp, n, arcs, max_deg, st, true);
   cudaFreeAsync(keys, st); cudaFreeAsync(k2, st); cudaFreeAsync(v2, st); cudaFreeAsync(newdeg, st);
   cudaFreeAsync(stmp, st); cudaFreeAsync(rtmp, st);
   return e;
