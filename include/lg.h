@@ -228,9 +228,28 @@ lg_status lg_pagerank(const lg_graph *g, float damping, uint32_t iters,
 lg_status lg_pagerank_noalloc(const lg_graph *g, float damping, uint32_t iters,
                               const uint32_t *personalize_source, float *ranks, void *stream);
 
-/* lg_free -- release a graph and all of its device memory.  NULL-safe.  The
-   caller must make sure no enqueued work still uses g. */
+/* lg_free -- release a graph and all of its device memory.  NULL-safe.
+   Waits for the graph's device to be idle, then returns the graph's arrays
+   to the library pool of that device (below). */
 void lg_free(lg_graph *g);
+
+/* ------------------------------------------------------------------------
+ * Device memory pool.  Graph arrays and the scratch of every call are
+ * stream-ordered allocations from one pool per device owned by the library.
+ * Freed blocks stay mapped in the pool and serve later calls, so a loop of
+ * encode / traverse / free maps its memory once.  The pool never returns
+ * memory by itself; lg_pool_trim does.
+ * ------------------------------------------------------------------------ */
+
+/* lg_pool_trim -- wait for `device` to be idle, then release pooled memory
+   that no live graph or call holds until at most keep_bytes stay reserved.
+   LG_ECUDA for an invalid device. */
+lg_status lg_pool_trim(int device, uint64_t keep_bytes);
+
+/* lg_pool_usage -- bytes the pool of `device` holds from the system
+   (*reserved, host) and of those, bytes in live allocations (*used, host).
+   No GPU work.  LG_EINVAL if an output is NULL, LG_ECUDA for an invalid device. */
+lg_status lg_pool_usage(int device, uint64_t *reserved, uint64_t *used);
 
 /* ------------------------------------------------------------------------
  * Batches: many independent graphs encoded and traversed in one launch.

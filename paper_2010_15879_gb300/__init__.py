@@ -30,6 +30,7 @@ __all__ = [
     "LG_RELABEL_NONE", "LG_RELABEL_DM", "LG_RELABEL_GREEDY",
     "LgError", "LogGraph", "build", "load", "lg_encode", "lg_stats_get", "lg_arrays_get", "lg_neighbors",
     "lg_bfs", "lg_sssp", "lg_pagerank", "lg_pagerank_noalloc", "lg_free", "lg_last_error", "lg_kernel_launches",
+    "lg_pool_trim", "lg_pool_usage",
     "LgBatch", "lg_batch_create", "lg_batch_run", "lg_batch_status", "lg_batch_info_get", "lg_batch_free",
     "LG_BATCH_FLAG_DROP_MEMBER",
     "LG_REQ_NEIGHBORS", "LG_REQ_BFS", "LG_REQ_PPR", "LgServer", "lg_server_create", "lg_server_submit",
@@ -139,6 +140,10 @@ def load(auto_build: bool = False):
         h.lg_pagerank.argtypes = [_vp, _f32, _u32, ctypes.POINTER(_u32), _vp, _vp]
         h.lg_pagerank_noalloc.argtypes = [_vp, _f32, _u32, ctypes.POINTER(_u32), _vp, _vp]
         h.lg_free.argtypes = [_vp]
+        h.lg_pool_trim.argtypes = [ctypes.c_int, _u64]
+        h.lg_pool_trim.restype = ctypes.c_int
+        h.lg_pool_usage.argtypes = [ctypes.c_int, ctypes.POINTER(_u64), ctypes.POINTER(_u64)]
+        h.lg_pool_usage.restype = ctypes.c_int
         h.lg_free.restype = None
         h.lg_last_error.restype = ctypes.c_char_p
         h.lg_kernel_launches.argtypes = []
@@ -176,6 +181,18 @@ def lg_last_error() -> str:
 def lg_kernel_launches() -> int:
     """Kernels launched by liblg.so in this process so far."""
     return int(load().lg_kernel_launches())
+
+
+def lg_pool_trim(device: int = 0, keep_bytes: int = 0) -> None:
+    """Release pooled device memory of `device` down to keep_bytes reserved."""
+    _check(load().lg_pool_trim(int(device), int(keep_bytes)), "lg_pool_trim")
+
+
+def lg_pool_usage(device: int = 0) -> tuple:
+    """(reserved, used) bytes of the library's device memory pool."""
+    r, u = _u64(0), _u64(0)
+    _check(load().lg_pool_usage(int(device), ctypes.byref(r), ctypes.byref(u)), "lg_pool_usage")
+    return int(r.value), int(u.value)
 
 
 def _check(status: int, what: str):
@@ -216,9 +233,10 @@ class LogGraph:
         return lg_stats_get(self)
 
     def free(self):
-        if self._h is not None and self._h.value:
-            lg_free(self)
-            self._h = None
+        """Release the graph (once; later calls and the destructor do nothing)."""
+        h, self._h = self._h, None
+        if h is not None and h.value:
+            load().lg_free(h)
 
     def __del__(self):
         try:
@@ -249,7 +267,8 @@ def lg_encode(row_ptr, col, weights=None, *, id_mode: int = LG_ID_GLOBAL, off_mo
 
 
 def lg_free(g: LogGraph) -> None:
-    load().lg_free(g.handle)
+    """Release g's device memory; g is unusable afterwards."""
+    g.free()
 
 
 def lg_stats_get(g: LogGraph) -> dict:

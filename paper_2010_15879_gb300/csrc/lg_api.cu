@@ -45,7 +45,7 @@ struct Tmp {
   }
   Tmp(const Tmp&) = delete;
   Tmp& operator=(const Tmp&) = delete;
-  cudaError_t alloc(size_t bytes) { return cudaMallocAsync(&p, bytes ? bytes : 16, st); }
+  cudaError_t alloc(size_t bytes) { return lg::pool_alloc(&p, bytes ? bytes : 16, st); }
   template <typename T> T* as() const { return reinterpret_cast<T*>(p); }
 };
 
@@ -75,7 +75,7 @@ lg_status describe_dev_err(int flags) {
 }
 
 cudaError_t alloc_words(uint64_t** p, uint64_t words, cudaStream_t st) {
-  cudaError_t e = cudaMalloc((void**)p, words * sizeof(uint64_t));
+  cudaError_t e = lg::pool_alloc((void**)p, words * sizeof(uint64_t), st);
   if (e != cudaSuccess) return e;
   return cudaMemsetAsync(*p, 0, words * sizeof(uint64_t), st);
 }
@@ -104,11 +104,52 @@ uint32_t pull_divisor() {
 }  // namespace
 
 #include <atomic>
+#include <mutex>
 
 namespace lg {
 
 static std::atomic<unsigned long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// One pool per device, created on first use, release threshold unlimited:
+// repeated encodes, traversals and frees reuse mapped memory instead of
+// mapping and unmapping gigabytes per call.
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pools[64] = {};
+
+static cudaError_t device_pool(int dev, cudaMemPool_t* out) {
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pools[dev]) {
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool;
+    cudaError_t e = cudaMemPoolCreate(&pool, &props);
+    if (e != cudaSuccess) return e;
+    uint64_t keep = UINT64_MAX;
+    e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) {
+      cudaMemPoolDestroy(pool);
+      return e;
+    }
+    g_pools[dev] = pool;
+  }
+  *out = g_pools[dev];
+  return cudaSuccess;
+}
+
+cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t st) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  cudaMemPool_t pool = nullptr;
+  if (e == cudaSuccess) e = device_pool(dev, &pool);
+  if (e != cudaSuccess) return e;
+  return cudaMallocFromPoolAsync(p, bytes, pool, st);
+}
 
 void set_error_message(const char* msg) { snprintf(g_err, sizeof g_err, "%s", msg); }
 
@@ -322,11 +363,36 @@ extern "C" uint64_t lg_kernel_launches(void) { return (uint64_t)g_launches.load(
 extern "C" void lg_free(lg_graph* g) {
   if (!g) return;
   DeviceGuard dg(g->device);
+  // nothing still uses g once the device is idle; the blocks go back to the
+  // pool (they stay mapped for the next graph)
   cudaDeviceSynchronize();
-  cudaFree(g->A); cudaFree(g->O); cudaFree(g->ef_low); cudaFree(g->ef_high); cudaFree(g->ef_samples);
-  cudaFree(g->perm); cudaFree(g->inv_perm); cudaFree(g->W);
-  cudaFree(g->items); cudaFree(g->multi);
+  void* bufs[] = {g->A, g->O, g->ef_low, g->ef_high, g->ef_samples, g->perm, g->inv_perm, g->W, g->items, g->multi};
+  for (void* p : bufs)
+    if (p) cudaFreeAsync(p, cudaStreamLegacy);
   delete g;
+}
+
+extern "C" lg_status lg_pool_trim(int device, uint64_t keep_bytes) {
+  g_err[0] = 0;
+  cudaMemPool_t pool = nullptr;
+  LG_TRY(device_pool(device, &pool));
+  DeviceGuard dg(device);
+  LG_TRY(cudaDeviceSynchronize());
+  LG_TRY(cudaMemPoolTrimTo(pool, (size_t)keep_bytes));
+  return LG_OK;
+}
+
+extern "C" lg_status lg_pool_usage(int device, uint64_t* reserved, uint64_t* used) {
+  g_err[0] = 0;
+  if (!reserved || !used) { set_errf("lg_pool_usage: null argument"); return LG_EINVAL; }
+  cudaMemPool_t pool = nullptr;
+  LG_TRY(device_pool(device, &pool));
+  unsigned long long r = 0, u = 0;
+  LG_TRY(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &r));
+  LG_TRY(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &u));
+  *reserved = (uint64_t)r;
+  *used = (uint64_t)u;
+  return LG_OK;
 }
 
 extern "C" lg_status lg_stats_get(const lg_graph* g, lg_stats* out) {
@@ -390,8 +456,8 @@ static lg_status build_schedule(lg_graph* g, cudaStream_t st) {
   g->n_items = tot[0];
   g->n_multi = tot[1];
   if (g->n_items == 0) return LG_OK;
-  LG_TRY(cudaMalloc((void**)&g->items, g->n_items * sizeof(HeavyItem)));
-  if (g->n_multi) LG_TRY(cudaMalloc((void**)&g->multi, g->n_multi * sizeof(uint32_t)));
+  LG_TRY(pool_alloc((void**)&g->items, g->n_items * sizeof(HeavyItem), st));
+  if (g->n_multi) LG_TRY(pool_alloc((void**)&g->multi, g->n_multi * sizeof(uint32_t), st));
   p.items = g->items;
   p.multi = g->multi;
   LG_TRY(ops->plan_fill(v, p, st));
@@ -446,8 +512,8 @@ static lg_status encode_impl(lg_graph* g, const uint64_t* row_ptr, const uint32_
   const uint32_t* wt = weights;
   Tmp t_nrp(st), t_ncol(st), t_nw(st);
   if (g->relabel) {
-    LG_TRY(cudaMalloc((void**)&g->perm, n * sizeof(uint32_t)));
-    LG_TRY(cudaMalloc((void**)&g->inv_perm, n * sizeof(uint32_t)));
+    LG_TRY(pool_alloc((void**)&g->perm, n * sizeof(uint32_t), st));
+    LG_TRY(pool_alloc((void**)&g->inv_perm, n * sizeof(uint32_t), st));
     LG_TRY(t_nrp.alloc((n + 1) * sizeof(uint64_t)));
     LG_TRY(t_ncol.alloc(arcs * sizeof(uint32_t)));
     if (weights) LG_TRY(t_nw.alloc(arcs * sizeof(uint32_t)));
@@ -470,7 +536,7 @@ static lg_status encode_impl(lg_graph* g, const uint64_t* row_ptr, const uint32_
     LG_TRY(alloc_words(&g->O, g->words_O, st));
     LG_TRY(cudaMemcpyAsync(g->O, rp, (n + 1) * sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
     if (wt) {
-      LG_TRY(cudaMalloc((void**)&g->W, (arcs ? arcs : 1) * sizeof(uint32_t)));
+      LG_TRY(pool_alloc((void**)&g->W, (arcs ? arcs : 1) * sizeof(uint32_t), st));
       if (arcs) LG_TRY(cudaMemcpyAsync(g->W, wt, arcs * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
     }
     g->off_mode = OFF_ROWPTR;

@@ -448,7 +448,7 @@ cudaError_t enc_pack_local(const uint64_t* rp, const uint32_t* col, const uint64
   if (data_words == 0) return cudaSuccess;
   const uint64_t nwin = (data_words + PW - 1) / PW;
   uint32_t* first = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&first, nwin * sizeof(uint32_t), st);
+  cudaError_t e = lg::pool_alloc((void**)&first, nwin * sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
   k_window_first<<<grid_for(n, 256, 152 * 32), 256, 0, st>>>(x, n, nwin, first);
   count_launch();

@@ -55,6 +55,11 @@ GView make_view(const lg_graph* g);
 // every kernel launch site calls this right after its <<<...>>> (instrumentation)
 void count_launch();
 
+// Stream-ordered allocation from the library's pool on the current device.
+// Graph arrays and every call's scratch come from it; blocks released with
+// cudaFreeAsync stay mapped for reuse (lg_pool_trim returns them).
+cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t st);
+
 // sets the calling thread's lg_last_error() message
 void set_error_message(const char* msg);
 

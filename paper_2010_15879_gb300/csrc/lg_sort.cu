@@ -480,9 +480,9 @@ static cudaError_t seg_sort_big(uint32_t* keys, uint32_t* vals, const uint64_t* 
   uint32_t *cv = nullptr, *cv2 = nullptr;
   void* rtmp = nullptr;
   uint64_t nb_total = 0;
-  cudaError_t e = cudaMallocAsync((void**)&sizes, nbig * sizeof(uint64_t), st);
-  if (e == cudaSuccess) e = cudaMallocAsync((void**)&boff, (nbig + 1) * sizeof(uint64_t), st);
-  if (e == cudaSuccess) e = cudaMallocAsync((void**)&stmp, scan_tmp_words(nbig) * sizeof(uint64_t), st);
+  cudaError_t e = lg::pool_alloc((void**)&sizes, nbig * sizeof(uint64_t), st);
+  if (e == cudaSuccess) e = lg::pool_alloc((void**)&boff, (nbig + 1) * sizeof(uint64_t), st);
+  if (e == cudaSuccess) e = lg::pool_alloc((void**)&stmp, scan_tmp_words(nbig) * sizeof(uint64_t), st);
   if (e == cudaSuccess) {
     k_seg_big_sizes<<<grid_for(nbig, 256, 1024), 256, 0, st>>>(off, big, nbig, sizes);
     count_launch();
@@ -490,11 +490,11 @@ static cudaError_t seg_sort_big(uint32_t* keys, uint32_t* vals, const uint64_t* 
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(&nb_total, boff + nbig, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e == cudaSuccess) e = cudaMallocAsync((void**)&ck, nb_total * sizeof(uint64_t), st);
-  if (e == cudaSuccess) e = cudaMallocAsync((void**)&ck2, nb_total * sizeof(uint64_t), st);
-  if (e == cudaSuccess) e = cudaMallocAsync((void**)&cv, nb_total * sizeof(uint32_t), st);
-  if (e == cudaSuccess) e = cudaMallocAsync((void**)&cv2, nb_total * sizeof(uint32_t), st);
-  if (e == cudaSuccess) e = cudaMallocAsync(&rtmp, radix_tmp_bytes(nb_total), st);
+  if (e == cudaSuccess) e = lg::pool_alloc((void**)&ck, nb_total * sizeof(uint64_t), st);
+  if (e == cudaSuccess) e = lg::pool_alloc((void**)&ck2, nb_total * sizeof(uint64_t), st);
+  if (e == cudaSuccess) e = lg::pool_alloc((void**)&cv, nb_total * sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = lg::pool_alloc((void**)&cv2, nb_total * sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = lg::pool_alloc(&rtmp, radix_tmp_bytes(nb_total), st);
   if (e == cudaSuccess) {
     k_seg_big_gather<<<grid_for(nbig, 1, 4096), 256, 0, st>>>(keys, vals, off, big, boff, nbig, ck, cv);
     count_launch();
@@ -559,7 +559,7 @@ cudaError_t segmented_sort(uint32_t* keys, uint32_t* vals, const uint64_t* off, 
   if (max_row <= SEG_SMALL) return cudaSuccess;
   // rows by power-of-two size class
   uint32_t* meta = nullptr;  // cnt[10], base[10], cursor[10]
-  if ((e = cudaMallocAsync((void**)&meta, 3 * SEG_NCLASS * sizeof(uint32_t), st)) != cudaSuccess) return e;
+  if ((e = lg::pool_alloc((void**)&meta, 3 * SEG_NCLASS * sizeof(uint32_t), st)) != cudaSuccess) return e;
   cudaMemsetAsync(meta, 0, 3 * SEG_NCLASS * sizeof(uint32_t), st);
   k_seg_count<<<grid_for(rows, 256, 152 * 16), 256, 0, st>>>(off, rows, meta);
   count_launch();
@@ -569,7 +569,7 @@ cudaError_t segmented_sort(uint32_t* keys, uint32_t* vals, const uint64_t* off, 
   uint32_t tot = 0;
   for (int k = 0; k < SEG_NCLASS; k++) { base[k] = tot; tot += cnt[k]; }
   uint32_t* list = nullptr;
-  if ((e = cudaMallocAsync((void**)&list, (tot ? tot : 1) * sizeof(uint32_t), st)) != cudaSuccess) {
+  if ((e = lg::pool_alloc((void**)&list, (tot ? tot : 1) * sizeof(uint32_t), st)) != cudaSuccess) {
     cudaFreeAsync(meta, st);
     return e;
   }
@@ -734,18 +734,18 @@ cudaError_t enc_dm_relabel(const uint64_t* rp, const uint32_t* col, const uint32
   uint32_t *keys = nullptr, *k2 = nullptr, *v2 = nullptr, *newdeg = nullptr;
   uint64_t* stmp = nullptr;
   void* rtmp = nullptr;
-  e = cudaMallocAsync((void**)&keys, n * sizeof(uint32_t), st);
-  if (e == cudaSuccess) e = cudaMallocAsync((void**)&k2, n * sizeof(uint32_t), st);
-  if (e == cudaSuccess) e = cudaMallocAsync((void**)&v2, n * sizeof(uint32_t), st);
-  if (e == cudaSuccess) e = cudaMallocAsync((void**)&newdeg, n * sizeof(uint32_t), st);
-  if (e == cudaSuccess) e = cudaMallocAsync((void**)&stmp, scan_tmp_words(n) * sizeof(uint64_t), st);
-  if (e == cudaSuccess) e = cudaMallocAsync(&rtmp, radix_tmp_bytes(n), st);
+  e = lg::pool_alloc((void**)&keys, n * sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = lg::pool_alloc((void**)&k2, n * sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = lg::pool_alloc((void**)&v2, n * sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = lg::pool_alloc((void**)&newdeg, n * sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = lg::pool_alloc((void**)&stmp, scan_tmp_words(n) * sizeof(uint64_t), st);
+  if (e == cudaSuccess) e = lg::pool_alloc(&rtmp, radix_tmp_bytes(n), st);
   if (e == cudaSuccess && mode == 2) {
     // greedy: order by (degree asc, ID asc), first appearances, sort by them
     uint64_t *pos0 = nullptr, *first = nullptr, *first2 = nullptr;
-    e = cudaMallocAsync((void**)&pos0, (n + 1) * sizeof(uint64_t), st);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&first, n * sizeof(uint64_t), st);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&first2, n * sizeof(uint64_t), st);
+    e = lg::pool_alloc((void**)&pos0, (n + 1) * sizeof(uint64_t), st);
+    if (e == cudaSuccess) e = lg::pool_alloc((void**)&first, n * sizeof(uint64_t), st);
+    if (e == cudaSuccess) e = lg::pool_alloc((void**)&first2, n * sizeof(uint64_t), st);
     if (e == cudaSuccess) {
       k_gr_keys<<<grid_for(n, 256, 152 * 32), 256, 0, st>>>(rp, n, keys, inv_perm);  // inv_perm: the order
       count_launch();

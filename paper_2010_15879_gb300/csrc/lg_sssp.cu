@@ -253,7 +253,7 @@ struct DevBuf {
   ~DevBuf() {
     if (p) cudaFreeAsync(p, st);
   }
-  cudaError_t alloc(size_t b) { return cudaMallocAsync(&p, b, st); }
+  cudaError_t alloc(size_t b) { return lg::pool_alloc(&p, b, st); }
   template <typename T>
   T* as() const {
     return reinterpret_cast<T*>(p);
