@@ -233,6 +233,14 @@ lg_status lg_pagerank_noalloc(const lg_graph *g, float damping, uint32_t iters,
    to the library pool of that device (below). */
 void lg_free(lg_graph *g);
 
+/* lg_free_async -- release a graph without waiting: its arrays return to
+   the pool in stream order on `stream` (a cudaStream_t; NULL = legacy default
+   stream).  Every use of g must be enqueued on `stream` before this call or
+   ordered before it by the caller.  The host object is released at once; g is
+   unusable afterwards.  NULL g is a no-op.  LG_ECUDA if a release fails (the
+   remaining arrays are still released). */
+lg_status lg_free_async(lg_graph *g, void *stream);
+
 /* ------------------------------------------------------------------------
  * Device memory pool.  Graph arrays and the scratch of every call are
  * stream-ordered allocations from one pool per device owned by the library.

@@ -16,6 +16,8 @@ Quick use::
 from __future__ import annotations
 
 import ctypes
+import functools
+import inspect
 import os
 import threading
 from typing import Optional
@@ -30,7 +32,7 @@ __all__ = [
     "LG_RELABEL_NONE", "LG_RELABEL_DM", "LG_RELABEL_GREEDY",
     "LgError", "LogGraph", "build", "load", "lg_encode", "lg_stats_get", "lg_arrays_get", "lg_neighbors",
     "lg_bfs", "lg_sssp", "lg_pagerank", "lg_pagerank_noalloc", "lg_free", "lg_last_error", "lg_kernel_launches",
-    "lg_pool_trim", "lg_pool_usage",
+    "lg_free_async", "lg_pool_trim", "lg_pool_usage",
     "LgBatch", "lg_batch_create", "lg_batch_run", "lg_batch_status", "lg_batch_info_get", "lg_batch_free",
     "LG_BATCH_FLAG_DROP_MEMBER",
     "LG_REQ_NEIGHBORS", "LG_REQ_BFS", "LG_REQ_PPR", "LgServer", "lg_server_create", "lg_server_submit",
@@ -140,6 +142,8 @@ def load(auto_build: bool = False):
         h.lg_pagerank.argtypes = [_vp, _f32, _u32, ctypes.POINTER(_u32), _vp, _vp]
         h.lg_pagerank_noalloc.argtypes = [_vp, _f32, _u32, ctypes.POINTER(_u32), _vp, _vp]
         h.lg_free.argtypes = [_vp]
+        h.lg_free_async.argtypes = [_vp, _vp]
+        h.lg_free_async.restype = ctypes.c_int
         h.lg_pool_trim.argtypes = [ctypes.c_int, _u64]
         h.lg_pool_trim.restype = ctypes.c_int
         h.lg_pool_usage.argtypes = [ctypes.c_int, ctypes.POINTER(_u64), ctypes.POINTER(_u64)]
@@ -205,8 +209,9 @@ def _stream(stream) -> int:
     return s.cuda_stream
 
 
-def _dev(t: torch.Tensor, dtype: torch.dtype, name: str) -> torch.Tensor:
-    """Device-resident contiguous tensor of the given dtype (host tensors are copied)."""
+def _dev(t: torch.Tensor, dtype: torch.dtype, name: str, stream=None) -> torch.Tensor:
+    """Device-resident contiguous tensor of the given dtype (host tensors are
+    copied, in order on `stream` when one is given)."""
     if not isinstance(t, torch.Tensor):
         t = torch.as_tensor(np.ascontiguousarray(t))
     if t.dtype != dtype:
@@ -214,8 +219,27 @@ def _dev(t: torch.Tensor, dtype: torch.dtype, name: str) -> torch.Tensor:
             raise TypeError(f"{name}: expected {dtype}, got {t.dtype}")
         t = t.view(dtype)
     if not t.is_cuda:
+        if stream is not None:
+            with torch.cuda.stream(stream):
+                return t.to("cuda", non_blocking=True).contiguous()
         t = t.to("cuda", non_blocking=True)
     return t.contiguous()
+
+
+def _on_stream(fn):
+    """Run the call with `stream` (when given) as torch's current stream, so
+    that its host copies, allocations and reads are ordered with the library's
+    work on that stream."""
+    sig = inspect.signature(fn)
+
+    @functools.wraps(fn)
+    def call(*args, **kwargs):
+        st = sig.bind_partial(*args, **kwargs).arguments.get("stream")
+        if st is None:
+            return fn(*args, **kwargs)
+        with torch.cuda.stream(st):
+            return fn(*args, **kwargs)
+    return call
 
 
 class LogGraph:
@@ -232,11 +256,16 @@ class LogGraph:
     def stats(self) -> dict:
         return lg_stats_get(self)
 
-    def free(self):
-        """Release the graph (once; later calls and the destructor do nothing)."""
+    def free(self, stream=None):
+        """Release the graph (once; later calls and the destructor do nothing).
+        Without a stream this waits for the device to be idle (lg_free); with
+        one the arrays are released in stream order on it (lg_free_async)."""
         h, self._h = self._h, None
         if h is not None and h.value:
-            load().lg_free(h)
+            if stream is None:
+                load().lg_free(h)
+            else:
+                _check(load().lg_free_async(h, _stream(stream)), "lg_free_async")
 
     def __del__(self):
         try:
@@ -245,6 +274,7 @@ class LogGraph:
             pass
 
 
+@_on_stream
 def lg_encode(row_ptr, col, weights=None, *, id_mode: int = LG_ID_GLOBAL, off_mode: int = LG_OFF_PACKED,
               relabel: int = 0, select_sample: int = 512, weight_bits: int = 0,
               check_symmetric: bool = False, stream=None) -> LogGraph:
@@ -252,9 +282,9 @@ def lg_encode(row_ptr, col, weights=None, *, id_mode: int = LG_ID_GLOBAL, off_mo
     col uint32[arcs], optional weights uint32[arcs]; int64/int32 tensors are
     reinterpreted).  Host tensors are copied to the current device first."""
     lib = load()
-    rp = _dev(row_ptr, torch.int64, "row_ptr")
-    cl = _dev(col, torch.int32, "col")
-    wt = None if weights is None else _dev(weights, torch.int32, "weights")
+    rp = _dev(row_ptr, torch.int64, "row_ptr", stream)
+    cl = _dev(col, torch.int32, "col", stream)
+    wt = None if weights is None else _dev(weights, torch.int32, "weights", stream)
     n = rp.numel() - 1
     opts = _Opts(id_mode, off_mode, int(relabel), select_sample, weight_bits,
                  LG_FLAG_CHECK_SYMMETRIC if check_symmetric else 0)
@@ -269,6 +299,12 @@ def lg_encode(row_ptr, col, weights=None, *, id_mode: int = LG_ID_GLOBAL, off_mo
 def lg_free(g: LogGraph) -> None:
     """Release g's device memory; g is unusable afterwards."""
     g.free()
+
+
+def lg_free_async(g: LogGraph, stream=None) -> None:
+    """Release g's device memory in stream order on `stream` (default: the
+    current stream) without waiting; g is unusable afterwards."""
+    g.free(stream if stream is not None else torch.cuda.current_stream())
 
 
 def lg_stats_get(g: LogGraph) -> dict:
@@ -310,6 +346,7 @@ def lg_arrays_get(g: LogGraph) -> dict:
     return out
 
 
+@_on_stream
 def lg_neighbors(g: LogGraph, vertices, with_weights: bool = False, stream=None):
     """lg_neighbors: (offsets int64[k+1], ids uint32-as-int32[total][, weights])
     for the given original vertex IDs; each slice ascending."""
@@ -331,6 +368,7 @@ def lg_neighbors(g: LogGraph, vertices, with_weights: bool = False, stream=None)
     return (off, ids, wts[:total]) if with_weights else (off, ids)
 
 
+@_on_stream
 def lg_bfs(g: LogGraph, sources, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
     """lg_bfs: depths (S, n) as int32 holding uint32 values (UINT32_MAX = -1:
     unreachable)."""
@@ -344,6 +382,7 @@ def lg_bfs(g: LogGraph, sources, out: Optional[torch.Tensor] = None, stream=None
     return out
 
 
+@_on_stream
 def lg_sssp(g: LogGraph, source: int, delta: int = 0, out: Optional[torch.Tensor] = None,
             stream=None) -> torch.Tensor:
     """lg_sssp: shortest-path distances (n,) as int64 holding uint64 values
@@ -355,6 +394,7 @@ def lg_sssp(g: LogGraph, source: int, delta: int = 0, out: Optional[torch.Tensor
     return out
 
 
+@_on_stream
 def lg_pagerank_noalloc(g: LogGraph, damping: float, iters: int, out: torch.Tensor,
                         personalize: Optional[int] = None, stream=None) -> torch.Tensor:
     """lg_pagerank_noalloc: PageRank into ``out`` (n float32, on the device) for
@@ -366,6 +406,7 @@ def lg_pagerank_noalloc(g: LogGraph, damping: float, iters: int, out: torch.Tens
     return out
 
 
+@_on_stream
 def lg_pagerank(g: LogGraph, damping: float = 0.85, iters: int = 20, personalize: Optional[int] = None,
                 out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
     """lg_pagerank: FP32 ranks (n,) indexed by original vertex ID."""
@@ -406,6 +447,7 @@ class LgBatch:
             pass
 
 
+@_on_stream
 def lg_batch_create(graph_vptr, row_ptr, col, *, autotune: bool = True, lanes: int = 0, tile_arcs: int = 0,
                     wait_limit_us: int = 0, flags: int = 0, stream=None) -> LgBatch:
     """lg_batch_create: plan a batch of graphs given as one CSR over the batch
@@ -424,6 +466,7 @@ def lg_batch_create(graph_vptr, row_ptr, col, *, autotune: bool = True, lanes: i
     return LgBatch(h.value, keepalive=(vp, rp, cl))
 
 
+@_on_stream
 def lg_batch_run(b: LgBatch, damping: float = 0.85, iters: int = 10, depths: Optional[torch.Tensor] = None,
                  ranks: Optional[torch.Tensor] = None, stream=None):
     """lg_batch_run: encode + BFS from each graph's vertex 0 + PageRank, one
@@ -438,6 +481,7 @@ def lg_batch_run(b: LgBatch, damping: float = 0.85, iters: int = 10, depths: Opt
     return depths, ranks
 
 
+@_on_stream
 def lg_batch_status(b: LgBatch, stream=None) -> None:
     """lg_batch_status: synchronize and raise LgError (LG_ETIMEOUT) if a team
     barrier of the last run ran out of time."""

@@ -372,6 +372,23 @@ extern "C" void lg_free(lg_graph* g) {
   delete g;
 }
 
+extern "C" lg_status lg_free_async(lg_graph* g, void* stream) {
+  g_err[0] = 0;
+  if (!g) return LG_OK;
+  DeviceGuard dg(g->device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t first = cudaSuccess;
+  void* bufs[] = {g->A, g->O, g->ef_low, g->ef_high, g->ef_samples, g->perm, g->inv_perm, g->W, g->items, g->multi};
+  for (void* p : bufs) {
+    if (!p) continue;
+    const cudaError_t e = cudaFreeAsync(p, st);
+    if (first == cudaSuccess) first = e;
+  }
+  delete g;
+  if (first != cudaSuccess) return from_cuda(first, "lg_free_async");
+  return LG_OK;
+}
+
 extern "C" lg_status lg_pool_trim(int device, uint64_t keep_bytes) {
   g_err[0] = 0;
   cudaMemPool_t pool = nullptr;

@@ -59,3 +59,35 @@ def test_pool_bad_device():
         lg.lg_pool_usage(-1)
     with pytest.raises(lg.LgError):
         lg.lg_pool_trim(64, 0)
+
+
+def test_two_streams_host_inputs_and_async_free():
+    """Steps alternating between two streams (host CSR copied on the call's
+    stream, arrays released in stream order) give the default-stream results."""
+    g0 = gen.rmat(14, 16, seed=23)
+    rp_p = torch.from_numpy(g0.row_ptr.view(np.int64)).pin_memory()
+    col_p = torch.from_numpy(g0.col.view(np.int32)).pin_memory()
+    src = np.array([0, 5, 77, 1000], dtype=np.uint32)
+    opts = dict(id_mode=lg.LG_ID_LOCAL_GAP, off_mode=lg.LG_OFF_EF, relabel=1)
+    g = lg.lg_encode(rp_p, col_p, **opts)
+    want_d = lg.lg_bfs(g, src).cpu().numpy()
+    want_r = lg.lg_pagerank(g, 0.85, 5).cpu().numpy()
+    lg.lg_free(g)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    outs = []
+    for k in range(4):
+        s = streams[k & 1]
+        g = lg.lg_encode(rp_p, col_p, stream=s, **opts)
+        d = lg.lg_bfs(g, torch.from_numpy(src.view(np.int32)), stream=s)
+        r = lg.lg_pagerank(g, 0.85, 5, stream=s)
+        with torch.cuda.stream(s):
+            dh = torch.empty(d.shape, dtype=d.dtype).pin_memory()
+            rh = torch.empty(r.shape, dtype=r.dtype).pin_memory()
+            dh.copy_(d, non_blocking=True)
+            rh.copy_(r, non_blocking=True)
+        lg.lg_free_async(g, s)
+        outs.append((s, dh, rh))
+    torch.cuda.synchronize()
+    for _, dh, rh in outs:
+        assert np.array_equal(dh.numpy(), want_d)
+        assert np.array_equal(rh.numpy(), want_r)
