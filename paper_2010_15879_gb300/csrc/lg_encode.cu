@@ -238,32 +238,58 @@ cudaError_t enc_check_symmetric(const uint64_t* rp, const uint32_t* col, uint64_
 // local widths: w_v = max(1, bits(maxN_v)) (Section 3.2.2) or
 // g_v = max(1, bits(max gap)) (Section 3.6); len_v = bits of the neighborhood
 // =========================================================================
-// one warp takes 32 consecutive rows (bounds loaded one per lane), then the
-// largest difference of each row is reduced over the warp row by row
+// One warp takes 32 consecutive rows (bounds loaded one per lane).  Local IDs:
+// a row's width is that of its last (largest) ID.  Gaps: when the 32 rows hold
+// at most LL_STAGE arcs (contiguous in col) the warp copies them to shared
+// memory with coalesced loads and each lane scans its own row there; warps
+// with a longer row (near the hubs) reduce row by row over the warp.
+constexpr int LL_STAGE = 1024;
 __global__ void __launch_bounds__(256) k_local_lengths(const uint64_t* __restrict__ rp,
                                                        const uint32_t* __restrict__ col, uint64_t n, int gap,
                                                        uint32_t s, uint32_t H, uint8_t* __restrict__ wid,
                                                        uint64_t* __restrict__ len) {
+  __shared__ uint32_t stage[8][LL_STAGE];
   const int lane = threadIdx.x & 31;
+  uint32_t* sk = stage[threadIdx.x >> 5];
   const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
   for (uint64_t v0 = ((uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; v0 < n; v0 += warps * 32) {
+    const int rows = (int)min((uint64_t)32, n - v0);
     const uint64_t mv = v0 + lane;
     uint64_t mlo = 0, mhi = 0;
-    if (mv < n) { mlo = rp[mv]; mhi = rp[mv + 1]; }
+    if (lane < rows) { mlo = rp[mv]; mhi = rp[mv + 1]; }
     uint32_t mw = 0;  // lane l ends with the width of row v0 + l
-    if (!gap && mv < n && mhi > mlo) mw = max(1u, bits_u32(col[mhi - 1]));
+    if (!gap && lane < rows && mhi > mlo) mw = max(1u, bits_u32(col[mhi - 1]));
     if (gap) {
-      const int rows = (int)min((uint64_t)32, n - v0);
-      for (int r = 0; r < rows; r++) {
-        const uint64_t lo = __shfl_sync(LG_FULL_MASK, mlo, r), hi = __shfl_sync(LG_FULL_MASK, mhi, r);
-        if (hi - lo < 2) continue;
-        uint32_t mg = 0;
-        for (uint64_t j = lo + 1 + lane; j < hi; j += 32) mg = max(mg, col[j] - col[j - 1]);
-        mg = __reduce_max_sync(LG_FULL_MASK, mg);
-        if (lane == r) mw = max(1u, bits_u32(mg));
+      const uint64_t r0 = __shfl_sync(LG_FULL_MASK, mlo, 0);
+      const uint64_t r1 = __shfl_sync(LG_FULL_MASK, mhi, rows - 1);
+      if (r1 - r0 <= (uint64_t)LL_STAGE) {
+        const uint32_t tot = (uint32_t)(r1 - r0);
+        for (uint32_t q = lane; q < tot; q += 32) sk[q] = col[r0 + q];
+        __syncwarp();
+        if (lane < rows && mhi - mlo >= 2) {
+          const uint32_t* row = sk + (mlo - r0);
+          const uint32_t d = (uint32_t)(mhi - mlo);
+          uint32_t prev = row[0], mg = 0;
+          for (uint32_t t = 1; t < d; t++) {
+            const uint32_t x = row[t];
+            mg = max(mg, x - prev);
+            prev = x;
+          }
+          mw = max(1u, bits_u32(mg));
+        }
+        __syncwarp();
+      } else {
+        for (int r = 0; r < rows; r++) {
+          const uint64_t lo = __shfl_sync(LG_FULL_MASK, mlo, r), hi = __shfl_sync(LG_FULL_MASK, mhi, r);
+          if (hi - lo < 2) continue;
+          uint32_t mg = 0;
+          for (uint64_t j = lo + 1 + lane; j < hi; j += 32) mg = max(mg, col[j] - col[j - 1]);
+          mg = __reduce_max_sync(LG_FULL_MASK, mg);
+          if (lane == r) mw = max(1u, bits_u32(mg));
+        }
       }
     }
-    if (mv < n) {
+    if (lane < rows) {
       const uint64_t d = mhi - mlo;
       wid[mv] = (uint8_t)mw;
       len[mv] = gap ? (uint64_t)H + (d >= 1 ? s : 0) + (d >= 2 ? (d - 1) * (uint64_t)mw : 0)
