@@ -275,7 +275,7 @@ const TravOps* trav_ops(int id_mode, int off_mode) {
 // duplicates merge into one frontier entry.
 template <typename M>
 __global__ void k_bfs_seed(M* vis, M* front, uint32_t* depth, uint64_t n, const uint32_t* src, uint32_t S,
-                           uint32_t* queue, uint32_t* counters) {
+                           uint32_t vmajor, uint32_t* queue, uint32_t* counters) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
   uint32_t q = 0;
   for (uint32_t i = 0; i < S; i++) {
@@ -284,16 +284,16 @@ __global__ void k_bfs_seed(M* vis, M* front, uint32_t* depth, uint64_t n, const 
     if (front[v] == 0) queue[q++] = v;
     front[v] = (M)(front[v] | bit);
     vis[v] = (M)(vis[v] | bit);
-    depth[(uint64_t)i * n + v] = 0;
+    depth[vmajor ? (uint64_t)v * S + i : (uint64_t)i * n + v] = 0;
   }
   counters[0] = q;
 }
 
 cudaError_t bfs_seed(void* vis, void* front, uint32_t* depth, uint64_t n, const uint32_t* src, uint32_t S,
-                     int mb, uint32_t* queue, uint32_t* counters, cudaStream_t st) {
-  if (mb == 2) { k_bfs_seed<uint16_t><<<1, 32, 0, st>>>((uint16_t*)vis, (uint16_t*)front, depth, n, src, S, queue, counters); count_launch(); }
-  else if (mb == 4) { k_bfs_seed<uint32_t><<<1, 32, 0, st>>>((uint32_t*)vis, (uint32_t*)front, depth, n, src, S, queue, counters); count_launch(); }
-  else { k_bfs_seed<uint64_t><<<1, 32, 0, st>>>((uint64_t*)vis, (uint64_t*)front, depth, n, src, S, queue, counters); count_launch(); }
+                     uint32_t vmajor, int mb, uint32_t* queue, uint32_t* counters, cudaStream_t st) {
+  if (mb == 2) { k_bfs_seed<uint16_t><<<1, 32, 0, st>>>((uint16_t*)vis, (uint16_t*)front, depth, n, src, S, vmajor, queue, counters); count_launch(); }
+  else if (mb == 4) { k_bfs_seed<uint32_t><<<1, 32, 0, st>>>((uint32_t*)vis, (uint32_t*)front, depth, n, src, S, vmajor, queue, counters); count_launch(); }
+  else { k_bfs_seed<uint64_t><<<1, 32, 0, st>>>((uint64_t*)vis, (uint64_t*)front, depth, n, src, S, vmajor, queue, counters); count_launch(); }
   return cudaGetLastError();
 }
 
@@ -307,20 +307,34 @@ __global__ void k_clear_queue(uint8_t* masks, int mb, const uint32_t* queue, uin
   }
 }
 
-// out[s][o] = tmp[s][perm[o]]: row-major by source so one destination row is
-// L2-resident at a time
-__global__ void k_permute_depths(const uint32_t* __restrict__ tmp, uint32_t* __restrict__ out,
-                                 const uint32_t* __restrict__ perm, uint64_t n, uint32_t S) {
-  const uint64_t total = (uint64_t)S * n;
-  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t s = t / n, o = t - s * n;
-    out[t] = tmp[s * n + perm[o]];
+// out[s][o] = tmp[perm[o]][s]: the relabeled depths are one record of S
+// values per vertex, so a thread gathers the record of perm[o] (16-byte loads
+// when S is a multiple of 4) and writes its S values, each store coalesced
+// over the warp's consecutive o
+template <bool VEC>
+__global__ void __launch_bounds__(256) k_permute_depths(const uint32_t* __restrict__ tmp, uint32_t* __restrict__ out,
+                                                        const uint32_t* __restrict__ perm, uint64_t n, uint32_t S) {
+  for (uint64_t o = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t p = perm[o];
+    if (VEC) {
+      const uint4* rec = reinterpret_cast<const uint4*>(tmp + p * S);
+      for (uint32_t q = 0; q < S / 4; q++) {
+        const uint4 x = __ldg(rec + q);
+        __stcs(out + (uint64_t)(4 * q) * n + o, x.x);
+        __stcs(out + (uint64_t)(4 * q + 1) * n + o, x.y);
+        __stcs(out + (uint64_t)(4 * q + 2) * n + o, x.z);
+        __stcs(out + (uint64_t)(4 * q + 3) * n + o, x.w);
+      }
+    } else {
+      for (uint32_t s = 0; s < S; s++) __stcs(out + (uint64_t)s * n + o, __ldg(tmp + p * S + s));
+    }
   }
 }
 
 cudaError_t bfs_permute_depths(const uint32_t* tmp, uint32_t* out, const uint32_t* perm, uint64_t n, uint32_t S,
                                cudaStream_t st) {
-  k_permute_depths<<<grid_for((uint64_t)S * n, 256, 152 * 32), 256, 0, st>>>(tmp, out, perm, n, S);
+  if (S % 4 == 0) k_permute_depths<true><<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(tmp, out, perm, n, S);
+  else k_permute_depths<false><<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(tmp, out, perm, n, S);
   count_launch();
   return cudaGetLastError();
 }
@@ -735,7 +749,8 @@ extern "C" lg_status lg_bfs(const lg_graph* g, const uint32_t* sources, uint32_t
     LG_TRY(cudaMemsetAsync(t_fa.p, 0, n * mb, st));
     LG_TRY(cudaMemsetAsync(t_fb.p, 0, n * mb, st));
     LG_TRY(cudaMemsetAsync(counters, 0, 16, st));
-    LG_TRY(bfs_seed(t_vis.p, t_fa.p, depth_b, n, t_src.as<uint32_t>() + b0, Sb, mb, t_qa.as<uint32_t>(), counters, st));
+    LG_TRY(bfs_seed(t_vis.p, t_fa.p, depth_b, n, t_src.as<uint32_t>() + b0, Sb, g->relabel ? 1u : 0u, mb,
+                    t_qa.as<uint32_t>(), counters, st));
     uint32_t hc[2] = {0, 0};
     LG_TRY(cudaMemcpyAsync(hc, counters, 8, cudaMemcpyDeviceToHost, st));
     LG_TRY(cudaStreamSynchronize(st));
@@ -750,6 +765,7 @@ extern "C" lg_status lg_bfs(const lg_graph* g, const uint32_t* sources, uint32_t
     a.depth = depth_b;
     a.all_mask = Sb == 64 ? ~0ull : ((1ull << Sb) - 1ull);
     a.S = Sb;
+    a.vmajor = g->relabel ? 1u : 0u;  // relabeled depths are permuted afterwards
     a.counters = counters;
     a.hacc = t_hacc.p;
     a.err = d_err;

@@ -133,12 +133,13 @@ struct BfsArgs {
   void* vis;                 // visited masks [n]
   const void* front_in;      // frontier masks of this level [n]
   void* front_out;           // frontier masks of the next level [n] (zero before a push level)
-  uint32_t* depth;           // S x n depths in stored labels
+  uint32_t* depth;           // depths in stored labels: S x n, or n x S when vmajor
   uint32_t* const* rows;     // or, if not null, one depth row per source (device array of S pointers)
   const uint32_t* row_base;  // with rows: level at which each source joined (depth = level - base)
   const uint32_t* row_perm;  // with rows: row index of stored vertex v (inv_perm), or null = v
   uint64_t all_mask;         // bits of the active sources
   uint32_t S;
+  uint32_t vmajor;           // depth[v * S + s] (one record per vertex) instead of depth[s * n + v]
   uint32_t level;            // depth of the current frontier
   const uint32_t* queue_in;  // frontier vertices (push levels)
   uint32_t queue_in_len;
@@ -204,9 +205,10 @@ const TravOps* trav_ops_gap_packed();
 const TravOps* trav_ops_gap_ef();
 const TravOps* trav_ops_csr32();
 
-// BFS helpers (lg_bfs_host.cu)
+// BFS helpers (lg_api.cu); vmajor: depth[v * S + s] instead of depth[s * n + v]
 cudaError_t bfs_seed(void* vis, void* front, uint32_t* depth, uint64_t n, const uint32_t* sources_stored,
-                     uint32_t S, int mask_bytes, uint32_t* queue, uint32_t* counters, cudaStream_t st);
+                     uint32_t S, uint32_t vmajor, int mask_bytes, uint32_t* queue, uint32_t* counters,
+                     cudaStream_t st);
 cudaError_t bfs_permute_depths(const uint32_t* tmp, uint32_t* out, const uint32_t* perm, uint64_t n,
                                uint32_t S, cudaStream_t st);
 cudaError_t map_ids(const uint32_t* in, uint32_t* out, const uint32_t* perm, uint64_t k, uint64_t n,

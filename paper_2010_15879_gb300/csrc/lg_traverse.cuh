@@ -64,6 +64,7 @@ __device__ __forceinline__ void write_depths(const BfsArgs& a, uint64_t n, uint6
     const int s = __ffsll((long long)b) - 1;
     b &= b - 1;
     if (a.rows) a.rows[s][a.row_perm ? (uint64_t)a.row_perm[v] : v] = d - a.row_base[s];
+    else if (a.vmajor) a.depth[v * a.S + s] = d;
     else a.depth[(uint64_t)s * n + v] = d;
   }
 }
