@@ -86,10 +86,14 @@ SSSP_DELTA = 32
 class Workload:
     """The input graph on the device (and on the host, made on demand)."""
 
-    def __init__(self, name, dev):
+    def __init__(self, name, dev, log2n=None):
         import torch
 
         self.desc, make, self.opts, self.S, self.T = WORKLOADS[name]
+        if log2n is not None:
+            if name != "community":
+                raise SystemExit("--profile-log2n applies to the community workload only")
+            make = lambda: gen.community_2p24(seed=2, log2n=log2n)  # noqa: E731
         t0 = time.time()
         if make is None:
             rp, col, w = gen.rmat_gpu(27, 16, seed=5, weighted=True)
@@ -849,7 +853,7 @@ def profile_pass(args):
     import paper_2010_15879_gb300 as lg
 
     lg.load(auto_build=True)
-    wl = Workload(args.workload, torch.device("cuda", 0))
+    wl = Workload(args.workload, torch.device("cuda", 0), log2n=args.profile_log2n)
     opts, T = wl.opts, (args.pr_iters if args.pr_iters is not None else wl.T)
     rp, col, w = wl.rp_d, wl.col_d, wl.w_d
     src = torch.from_numpy(wl.sources().view(np.int32)).cuda()
@@ -1031,6 +1035,8 @@ def main():
     ap.add_argument("--profile", choices=["lg", "csr32", "both"], default=None,
                     help="run one untimed pass of the hot path (for ncu) and exit")
     ap.add_argument("--pr-iters", type=int, default=None, help="PageRank iterations in --profile mode")
+    ap.add_argument("--profile-log2n", type=int, default=None,
+                    help="--profile mode of the community workload on a 2^k-vertex graph (a small capture case)")
     ap.add_argument("--batch-count", type=int, default=None, help="graphs in --profile mode of the batch workload")
     ap.add_argument("--serve-requests", type=int, default=100000, help="requests per rate (serve workload)")
     ap.add_argument("--serve-no-relabel", dest="serve_relabel", action="store_false",
