@@ -74,9 +74,16 @@ lg_status describe_dev_err(int flags) {
   return LG_EINVAL;
 }
 
+// graph arrays: the bit readers fetch whole 32-byte sectors of them, so a
+// block that is not 32-byte aligned is refused (pool blocks are)
 cudaError_t alloc_words(uint64_t** p, uint64_t words, cudaStream_t st) {
   cudaError_t e = lg::pool_alloc((void**)p, words * sizeof(uint64_t), st);
   if (e != cudaSuccess) return e;
+  if (reinterpret_cast<uintptr_t>(*p) & 31u) {
+    cudaFreeAsync(*p, st);
+    *p = nullptr;
+    return cudaErrorMisalignedAddress;
+  }
   return cudaMemsetAsync(*p, 0, words * sizeof(uint64_t), st);
 }
 

@@ -124,12 +124,11 @@ __device__ __forceinline__ uint64_t policy_keep() {
   asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
   return p;
 }
-__device__ __forceinline__ uint4 ldg128_stream(const uint32_t* p, uint64_t pol) {
-  uint4 v;
-  asm("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
-      : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+// one whole 32-byte sector (p 32-byte aligned) in a single request
+__device__ __forceinline__ void ldg256_stream(const uint32_t* p, uint64_t pol, uint4& a, uint4& b) {
+  asm("ld.global.nc.L2::cache_hint.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8], %9;"
+      : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
       : "l"(p), "l"(pol));
-  return v;
 }
 // Gathers of per-vertex arrays keep the default L1 allocation (on this GPU a
 // no-allocate L1 hint made 392M random 4-byte gathers 3.5x slower, measured)
@@ -180,9 +179,9 @@ struct BitReader {
   uint32_t n0, n1;    // valid words in q0, q1
 
   __device__ __forceinline__ void load_sector() {
-    const uint64_t c = wnext & ~7ull;
-    uint4 a = ldg128_stream(A + c, pol);
-    uint4 b = ldg128_stream(A + c + 4, pol);
+    const uint64_t c = wnext & ~7ull;  // the stream is 32-byte aligned (alloc_words)
+    uint4 a, b;
+    ldg256_stream(A + c, pol, a, b);
     uint32_t skip = (uint32_t)(wnext - c);
     if (skip >= 4) { a = b; n1 = 0; skip -= 4; } else { n1 = 4; }
     if (skip >= 1) { a.x = a.y; a.y = a.z; a.z = a.w; }
