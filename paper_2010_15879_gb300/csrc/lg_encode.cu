@@ -368,123 +368,157 @@ cudaError_t enc_pack_u64(const uint64_t* vals, uint64_t count, uint32_t w, uint6
 }
 
 // =========================================================================
-// variable-width local packing (Sections 3.2.2 / 3.6).  Differences are
-// independent of each other, so any field can be produced without a prefix;
-// a table of the vertex holding the first bit of every PW-word window bounds
-// the search for the vertex holding any given bit.
+// variable-width local packing (Sections 3.2.2 / 3.6): vertex v's record
+// [w_v : H][first : s][(d-1) gaps : w_v] (gaps) or [w_v : H][d IDs : w_v]
+// starts at bit x[v].  A warp takes PK_ROWS consecutive rows.  If they hold at
+// most PK_ARCS arcs, their arcs are staged in shared memory with coalesced
+// loads and each lane emits its row's record into a shared copy of the
+// group's bit range (shared atomicOr, as neighbouring records share words).
+// Otherwise the warp packs the rows one at a time, in windows of up to
+// PK_ARCS fields, a lane per field.  Either way the warp then writes the bit
+// range out coalesced: its inner 64-bit words are its own, its first and last
+// word may be shared with the neighbouring range and are OR-ed into A (zeroed
+// at allocation).
 // =========================================================================
-constexpr int PW = 1024;
+constexpr int PK_ROWS = 32;
+constexpr int PK_ARCS = 1024;
+constexpr int PK_STAGE = PK_ARCS + 8;  // a window's fields, plus the ID before them (gaps)
+constexpr int PK_W32 = 1104;           // >= 2 * ceil((PK_ARCS * 32 + PK_ROWS * 64 + 63) / 64), even
+constexpr int PK_WARPS = 4;
 
-// first[w] = the vertex whose bit range holds the first bit of window w
-// (x strictly increasing in the local modes: every neighborhood has a header)
-__global__ void k_window_first(const uint64_t* __restrict__ x, uint64_t n, uint64_t nwin,
-                               uint32_t* __restrict__ first) {
-  constexpr uint64_t WB = (uint64_t)PW * 64;
-  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t a = x[v], b = x[v + 1];  // bits [a, b)
-    for (uint64_t w = (a + WB - 1) / WB; w * WB < b && w < nwin; w++) first[w] = (uint32_t)v;
+__device__ __forceinline__ void pk_emit(uint32_t* ob, uint64_t p, uint32_t w, uint32_t val) {
+  if (w == 0) return;
+  const uint32_t i = (uint32_t)(p >> 5), sh = (uint32_t)p & 31u;
+  atomicOr(&ob[i], val << sh);
+  if (sh + w > 32) atomicOr(&ob[i + 1], val >> (32 - sh));
+}
+
+// bits [b0, b1) of A, held in ob from bit (b0 & ~63): inner words stored,
+// the first and last OR-ed in
+__device__ __forceinline__ void pk_flush(const uint32_t* ob, uint64_t b0, uint64_t b1, uint64_t* out, int lane) {
+  const uint64_t base = b0 & ~63ull;
+  const uint32_t nw64 = (uint32_t)((b1 - base + 63) >> 6);
+  for (uint32_t j = lane; j < nw64; j += 32) {
+    const uint64_t val = (uint64_t)ob[2 * j] | ((uint64_t)ob[2 * j + 1] << 32);
+    uint64_t* dst = out + (base >> 6) + j;
+    if (j == 0 || j + 1 == nw64) atomicOr(reinterpret_cast<unsigned long long*>(dst), (unsigned long long)val);
+    else __stcs(dst, val);
   }
 }
 
-// Each thread owns RW consecutive output words (bits [b0, b1)): it finds the
-// vertex holding bit b0 (binary search between the window table's bounds) and
-// writes its bits sequentially -- the stream is dense, so after the first
-// (clipped) field every field starts where the previous one ended: one shift,
-// one OR and, when a word fills up, one store per field.  Every word has one
-// writer: no atomics.
-constexpr int RW = 8;
-
-struct RunWriter {
-  uint64_t* out;
-  uint64_t b0;    // first bit of the run
-  uint64_t wq;    // next output word
-  uint64_t wend;  // one past the run's last word
-  uint64_t acc;   // bits of word wq gathered so far
-  uint32_t fill;  // how many
-  // field [p, p + w) (w <= 32); returns true once the run is complete
-  __device__ __forceinline__ bool emit(uint64_t p, uint32_t w, uint64_t val) {
-    if (p + w <= b0) return false;
-    if (p < b0) {  // the field straddling the run's first bit
-      val >>= (b0 - p);
-      w -= (uint32_t)(b0 - p);
-    }
-    acc |= val << fill;
-    if (fill + w >= 64) {
-      __stcs(out + wq, acc);
-      wq++;
-      acc = fill ? (val >> (64u - fill)) : 0;
-      fill = fill + w - 64;
-      return wq >= wend;
-    }
-    fill += w;
-    return false;
-  }
-};
+__device__ __forceinline__ void pk_clear(uint32_t* ob, uint64_t b0, uint64_t b1, int lane) {
+  const uint32_t n32 = 2 * (uint32_t)((b1 - (b0 & ~63ull) + 63) >> 6);
+  for (uint32_t q = lane; q < n32; q += 32) ob[q] = 0;
+}
 
 template <bool GAP>
-__global__ void __launch_bounds__(256) k_pack_local(const uint64_t* __restrict__ rp, const uint32_t* __restrict__ col,
-                                                    const uint64_t* __restrict__ x, const uint8_t* __restrict__ wid,
-                                                    const uint32_t* __restrict__ first, uint64_t nwin, uint64_t n,
-                                                    uint32_t s, uint32_t H, uint64_t* __restrict__ out,
-                                                    uint64_t data_words) {
-  const uint64_t nruns = (data_words + RW - 1) / RW;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nruns; r += stride) {
-    const uint64_t w0 = r * RW;
-    RunWriter rw{out, w0 * 64, w0, min(w0 + RW, data_words), 0, 0};
-    const uint64_t b1 = rw.wend * 64;
-    const uint64_t win = w0 / PW;
-    uint64_t lo = first[win];
-    uint64_t hi = win + 1 < nwin ? (uint64_t)first[win + 1] : n - 1;  // inclusive
-    while (lo < hi) {  // last v in [lo, hi] with x[v] <= b0
-      const uint64_t m = (lo + hi + 1) >> 1;
-      if (x[m] <= rw.b0) lo = m; else hi = m - 1;
+__global__ void __launch_bounds__(PK_WARPS * 32) k_pack_local(const uint64_t* __restrict__ rp,
+                                                             const uint32_t* __restrict__ col,
+                                                             const uint64_t* __restrict__ x,
+                                                             const uint8_t* __restrict__ wid, uint64_t n, uint32_t s,
+                                                             uint32_t H, uint64_t* __restrict__ out) {
+  __shared__ uint32_t stg_all[PK_WARPS][PK_STAGE];
+  __shared__ uint32_t ob_all[PK_WARPS][PK_W32];
+  const int lane = threadIdx.x & 31;
+  uint32_t* stg = stg_all[threadIdx.x >> 5];
+  uint32_t* ob = ob_all[threadIdx.x >> 5];
+  const uint64_t groups = (n + PK_ROWS - 1) / PK_ROWS;
+  const uint64_t warps = (uint64_t)gridDim.x * PK_WARPS;
+  for (uint64_t gi = (uint64_t)blockIdx.x * PK_WARPS + (threadIdx.x >> 5); gi < groups; gi += warps) {
+    const uint64_t v0 = gi * PK_ROWS;
+    const int rows = (int)min((uint64_t)PK_ROWS, n - v0);
+    uint64_t mlo = 0, mhi = 0, xb = 0, xe = 0;
+    uint32_t wv = 0;
+    if (lane < rows) {
+      mlo = rp[v0 + lane];
+      mhi = rp[v0 + lane + 1];
+      xb = x[v0 + lane];
+      xe = x[v0 + lane + 1];
+      wv = wid[v0 + lane];
     }
-    bool done = false;
-    for (uint64_t v = lo; v < n && !done; v++) {
-      const uint64_t base = x[v];
-      if (base >= b1) break;
-      const uint64_t rlo = rp[v], d = rp[v + 1] - rlo;
-      const uint32_t wv = wid[v];
-      done = rw.emit(base, H, wv);
-      uint64_t fs = base + H;
-      if (GAP && d >= 1 && !done) {
-        done = rw.emit(fs, s, col[rlo]);
-        fs += s;
-      }
-      const uint64_t nf = GAP ? (d >= 1 ? d - 1 : 0) : d;
-      if (nf && wv && !done) {
-        uint64_t k = rw.b0 > fs ? (rw.b0 - fs) / wv : 0;
-        for (; k < nf && !done; k++) {
-          const uint32_t val = GAP ? col[rlo + k + 1] - col[rlo + k] : col[rlo + k];
-          done = rw.emit(fs + k * wv, wv, val);
+    const uint64_t r0 = __shfl_sync(LG_FULL_MASK, mlo, 0);
+    const uint64_t r1 = __shfl_sync(LG_FULL_MASK, mhi, rows - 1);
+    if (r1 - r0 <= (uint64_t)PK_ARCS) {  // the whole group at once, a lane per row
+      const uint64_t B0 = __shfl_sync(LG_FULL_MASK, xb, 0);
+      const uint64_t B1 = __shfl_sync(LG_FULL_MASK, xe, rows - 1);
+      const uint64_t base = B0 & ~63ull;
+      const uint32_t tot = (uint32_t)(r1 - r0);
+      for (uint32_t q = lane; q < tot; q += 32) stg[q] = col[r0 + q];
+      pk_clear(ob, B0, B1, lane);
+      __syncwarp();
+      if (lane < rows) {
+        const uint32_t* row = stg + (mlo - r0);
+        const uint32_t d = (uint32_t)(mhi - mlo);
+        uint64_t p = xb - base;
+        pk_emit(ob, p, H, wv);
+        p += H;
+        if (GAP) {
+          if (d >= 1) {
+            pk_emit(ob, p, s, row[0]);
+            p += s;
+            uint32_t prev = row[0];
+            for (uint32_t t = 1; t < d; t++) {
+              const uint32_t cur = row[t];
+              pk_emit(ob, p, wv, cur - prev);
+              prev = cur;
+              p += wv;
+            }
+          }
+        } else {
+          for (uint32_t t = 0; t < d; t++) {
+            pk_emit(ob, p, wv, row[t]);
+            p += wv;
+          }
         }
       }
+      __syncwarp();
+      pk_flush(ob, B0, B1, out, lane);
+      __syncwarp();
+      continue;
     }
-    // the stream ended inside the run: its last partial word, then zeros
-    if (rw.wq < rw.wend) {
-      __stcs(out + rw.wq, rw.acc);
-      for (uint64_t q = rw.wq + 1; q < rw.wend; q++) __stcs(out + q, 0ull);
+    // long rows present: one row at a time, windows of up to PK_ARCS fields
+    for (int r = 0; r < rows; r++) {
+      const uint64_t lo = __shfl_sync(LG_FULL_MASK, mlo, r), hi = __shfl_sync(LG_FULL_MASK, mhi, r);
+      const uint64_t rb = __shfl_sync(LG_FULL_MASK, xb, r), re = __shfl_sync(LG_FULL_MASK, xe, r);
+      const uint32_t w = __shfl_sync(LG_FULL_MASK, wv, r);
+      const uint64_t d = hi - lo;
+      const uint64_t f0 = rb + H + (GAP && d >= 1 ? s : 0);  // bit of data field 0
+      const uint64_t nf = GAP ? (d >= 1 ? d - 1 : 0) : d;    // data fields
+      // data field k: gaps col[lo+k+1] - col[lo+k], or IDs col[lo+k]
+      for (uint64_t k0 = 0; k0 == 0 || k0 < nf; k0 += PK_ARCS) {
+        const uint32_t kn = (uint32_t)min((uint64_t)PK_ARCS, nf - min(nf, k0));
+        const uint64_t b0 = k0 == 0 ? rb : f0 + k0 * w;
+        const uint64_t b1 = k0 + kn >= nf ? re : f0 + (k0 + kn) * w;
+        const uint64_t base = b0 & ~63ull;
+        // staged IDs: the window's fields, plus the ID before the first gap
+        const uint32_t ns = GAP ? (d >= 1 ? kn + 1u : 0u) : kn;
+        for (uint32_t q = lane; q < ns; q += 32) stg[q] = col[lo + k0 + q];
+        pk_clear(ob, b0, b1, lane);
+        __syncwarp();
+        if (k0 == 0 && lane == 0) {
+          pk_emit(ob, rb - base, H, w);
+          if (GAP && d >= 1) pk_emit(ob, rb + H - base, s, stg[0]);
+        }
+        for (uint32_t q = lane; q < kn; q += 32) {
+          const uint32_t val = GAP ? stg[q + 1] - stg[q] : stg[q];
+          pk_emit(ob, f0 + (k0 + q) * w - base, w, val);
+        }
+        __syncwarp();
+        pk_flush(ob, b0, b1, out, lane);
+        __syncwarp();
+      }
     }
   }
 }
 
 cudaError_t enc_pack_local(const uint64_t* rp, const uint32_t* col, const uint64_t* x, const uint8_t* wid, uint64_t n,
                            int gap, uint32_t s, uint32_t H, uint64_t* out, uint64_t data_words, cudaStream_t st) {
-  if (data_words == 0) return cudaSuccess;
-  const uint64_t nwin = (data_words + PW - 1) / PW;
-  uint32_t* first = nullptr;
-  cudaError_t e = lg::pool_alloc((void**)&first, nwin * sizeof(uint32_t), st);
-  if (e != cudaSuccess) return e;
-  k_window_first<<<grid_for(n, 256, 152 * 32), 256, 0, st>>>(x, n, nwin, first);
+  if (data_words == 0 || n == 0) return cudaSuccess;
+  const unsigned grid = grid_for((n + PK_ROWS - 1) / PK_ROWS, PK_WARPS, 152 * 16);
+  if (gap) k_pack_local<true><<<grid, PK_WARPS * 32, 0, st>>>(rp, col, x, wid, n, s, H, out);
+  else k_pack_local<false><<<grid, PK_WARPS * 32, 0, st>>>(rp, col, x, wid, n, s, H, out);
   count_launch();
-  const unsigned grid = grid_for((data_words + RW - 1) / RW, 256, 152 * 32);
-  if (gap) k_pack_local<true><<<grid, 256, 0, st>>>(rp, col, x, wid, first, nwin, n, s, H, out, data_words);
-  else k_pack_local<false><<<grid, 256, 0, st>>>(rp, col, x, wid, first, nwin, n, s, H, out, data_words);
-  count_launch();
-  e = cudaGetLastError();
-  cudaFreeAsync(first, st);
-  return e;
+  return cudaGetLastError();
 }
 
 // =========================================================================
