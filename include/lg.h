@@ -144,6 +144,23 @@ lg_status lg_stats_get(const lg_graph *g, lg_stats *out);
 lg_status lg_arrays_get(const lg_graph *g, lg_arrays *out);
 
 /*
+ * lg_decode -- decode the whole graph back into a CSR in stored order: the
+ * neighborhood access of Section 3.7.2 applied to every vertex, the inverse
+ * of lg_encode.
+ *   row_ptr   device, n+1 u64 arc offsets
+ *   col       device, capacity u32: row i is the neighborhood of stored vertex
+ *             i, IDs as stored labels, ascending.  Without relabeling this is
+ *             the input CSR; with it, stored vertex i is original vertex
+ *             inv_perm[i] and label l is original ID inv_perm[l] (lg_arrays_get)
+ *   weights   device, capacity u32, or NULL (a weighted graph only, else
+ *             LG_EINVAL)
+ * LG_ERANGE if capacity < arcs (nothing written).  Asynchronous on `stream`:
+ * no host wait.
+ */
+lg_status lg_decode(const lg_graph *g, uint64_t *row_ptr, uint32_t *col, uint32_t *weights, uint64_t capacity,
+                    void *stream);
+
+/*
  * lg_neighbors -- decode N_v for a list of vertices (getNeighbors of Listing 3,
  * the edge and neighborhood access of Section 3.7.2, the degree of 3.7.3).
  *   vertices     device, k u32 original IDs (< n; repeats allowed)

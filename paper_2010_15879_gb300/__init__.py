@@ -32,7 +32,7 @@ __all__ = [
     "LG_RELABEL_NONE", "LG_RELABEL_DM", "LG_RELABEL_GREEDY",
     "LgError", "LogGraph", "build", "load", "lg_encode", "lg_stats_get", "lg_arrays_get", "lg_neighbors",
     "lg_bfs", "lg_sssp", "lg_pagerank", "lg_pagerank_noalloc", "lg_free", "lg_last_error", "lg_kernel_launches",
-    "lg_free_async", "lg_pool_trim", "lg_pool_usage",
+    "lg_decode", "lg_free_async", "lg_pool_trim", "lg_pool_usage",
     "LgBatch", "lg_batch_create", "lg_batch_run", "lg_batch_status", "lg_batch_info_get", "lg_batch_free",
     "LG_BATCH_FLAG_DROP_MEMBER",
     "LG_REQ_NEIGHBORS", "LG_REQ_BFS", "LG_REQ_PPR", "LgServer", "lg_server_create", "lg_server_submit",
@@ -142,6 +142,8 @@ def load(auto_build: bool = False):
         h.lg_pagerank.argtypes = [_vp, _f32, _u32, ctypes.POINTER(_u32), _vp, _vp]
         h.lg_pagerank_noalloc.argtypes = [_vp, _f32, _u32, ctypes.POINTER(_u32), _vp, _vp]
         h.lg_free.argtypes = [_vp]
+        h.lg_decode.argtypes = [_vp, _vp, _vp, _vp, _u64, _vp]
+        h.lg_decode.restype = ctypes.c_int
         h.lg_free_async.argtypes = [_vp, _vp]
         h.lg_free_async.restype = ctypes.c_int
         h.lg_pool_trim.argtypes = [ctypes.c_int, _u64]
@@ -344,6 +346,21 @@ def lg_arrays_get(g: LogGraph) -> dict:
         else:
             out[name] = np.zeros(0, dtype=np.uint32)
     return out
+
+
+@_on_stream
+def lg_decode(g: LogGraph, with_weights: bool = False, stream=None):
+    """lg_decode: the whole graph as a CSR in stored order: (row_ptr int64[n+1],
+    col uint32-as-int32[arcs][, weights]); stored labels for relabeled graphs."""
+    lib = load()
+    st_ = lg_stats_get(g)
+    n, arcs = st_["n"], st_["arcs"]
+    rp = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+    col = torch.empty(max(arcs, 1), dtype=torch.int32, device="cuda")
+    wts = torch.empty(max(arcs, 1), dtype=torch.int32, device="cuda") if with_weights else None
+    _check(lib.lg_decode(g.handle, rp.data_ptr(), col.data_ptr(), None if wts is None else wts.data_ptr(), arcs,
+                         _stream(stream)), "lg_decode")
+    return (rp, col[:arcs], wts[:arcs]) if with_weights else (rp, col[:arcs])
 
 
 @_on_stream

@@ -393,6 +393,39 @@ extern "C" void lg_free(lg_graph* g) {
   delete g;
 }
 
+extern "C" lg_status lg_decode(const lg_graph* g, uint64_t* row_ptr, uint32_t* col, uint32_t* weights,
+                               uint64_t capacity, void* stream) {
+  g_err[0] = 0;
+  if (!g || !row_ptr || (g->arcs && !col)) { set_errf("lg_decode: null argument"); return LG_EINVAL; }
+  if (weights && !g->weighted) { set_errf("lg_decode: weights requested from an unweighted graph"); return LG_EINVAL; }
+  if (capacity < g->arcs) {
+    set_errf("lg_decode: capacity %llu < %llu arcs", (unsigned long long)capacity, (unsigned long long)g->arcs);
+    return LG_ERANGE;
+  }
+  DeviceGuard dg(g->device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const uint64_t n = g->n;
+  if (n == 0) {
+    LG_TRY(cudaMemsetAsync(row_ptr, 0, sizeof(uint64_t), st));
+    return LG_OK;
+  }
+  Tmp t_deg(st), t_stmp(st);
+  LG_TRY(t_deg.alloc(n * sizeof(uint64_t)));
+  LG_TRY(t_stmp.alloc(scan_tmp_words(n) * sizeof(uint64_t)));
+  const GView v = make_view(g);
+  const TravOps* ops = trav_ops((int)g->id_mode, (int)g->off_mode);
+  DecArgs a;
+  memset(&a, 0, sizeof(a));
+  a.degrees = t_deg.as<uint64_t>();
+  a.row_ptr = row_ptr;
+  a.ids = col;
+  a.weights = weights;
+  LG_TRY(ops->dec_degrees(v, a, st));
+  LG_TRY(scan_excl_u64(t_deg.as<uint64_t>(), n, row_ptr, t_stmp.as<uint64_t>(), st));
+  if (g->arcs) LG_TRY(ops->dec_all(v, a, st));
+  return LG_OK;
+}
+
 extern "C" lg_status lg_free_async(lg_graph* g, void* stream) {
   g_err[0] = 0;
   if (!g) return LG_OK;

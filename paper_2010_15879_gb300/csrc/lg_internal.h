@@ -175,6 +175,14 @@ struct NbrArgs {
   int* err;
 };
 
+// whole-graph decode into a CSR in stored order (lg_decode)
+struct DecArgs {
+  uint64_t* degrees;         // n (degree pass output)
+  const uint64_t* row_ptr;   // n+1 arc offsets (decode pass input)
+  uint32_t* ids;             // arcs
+  uint32_t* weights;         // arcs, or null
+};
+
 struct TravOps {
   cudaError_t (*pr_init)(const GView&, const PrArgs&, cudaStream_t);
   cudaError_t (*pr_pull)(const GView&, const PrArgs&, cudaStream_t);
@@ -187,6 +195,8 @@ struct TravOps {
   cudaError_t (*plan_carry)(const GView&, const PlanArgs&, cudaStream_t);
   cudaError_t (*ppr_pull)(const GView&, const PprArgs&, cudaStream_t);
   cudaError_t (*ppr_join)(const GView&, float* cin, uint32_t slot, uint32_t src, cudaStream_t);
+  cudaError_t (*dec_degrees)(const GView&, const DecArgs&, cudaStream_t);
+  cudaError_t (*dec_all)(const GView&, const DecArgs&, cudaStream_t);
 };
 
 // finishing kernels for vertices split into several heavy items (lg_api.cu)

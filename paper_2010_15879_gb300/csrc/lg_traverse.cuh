@@ -1016,6 +1016,147 @@ __global__ void __launch_bounds__(256) k_nbr_decode(GView g, NbrArgs a) {
 }
 
 // ===========================================================================
+// Whole-graph decode (lg_decode): the degree of every vertex, then every
+// neighborhood written to its CSR row in stored order.  Tiles of TV vertices
+// decode their offsets once; each warp takes a run of the tile's light
+// vertices balanced by fields and decodes a vertex 32 fields per step, a lane
+// per field (coalesced writes; gaps prefix-summed across the warp).  Heavy
+// vertices come from the heavy schedule, a warp per item.
+// ===========================================================================
+template <int IDM, int OFF>
+__global__ void __launch_bounds__(TNT) k_dec_degrees(GView g, DecArgs a) {
+  __shared__ uint64_t xs[TV + 1];
+  __shared__ TileScratch ts;
+  const uint64_t v0 = (uint64_t)blockIdx.x * TV;
+  const int cnt = (int)min((uint64_t)TV, g.n - v0);
+  tile_offsets<OFF>(g, v0, cnt, xs, ts);
+  __syncthreads();
+  for (int i = threadIdx.x; i < cnt; i += TNT) {
+    uint64_t start;
+    uint32_t d, w;
+    vgeo<IDM>(g, xs[i], xs[i + 1], start, d, w);
+    a.degrees[v0 + i] = d;
+  }
+}
+
+template <int IDM, int U>
+__device__ __forceinline__ void dec_fields(const GView& g, const DecArgs& a, uint64_t start, uint32_t w, uint32_t f0,
+                                           uint32_t f1, uint32_t carry, uint64_t o) {
+  const uint32_t lane = threadIdx.x & 31u;
+  for (uint32_t base = f0; base < f1; base += 32u * U) {
+    uint32_t id[U];
+    warp_ids<IDM, U>(g, start, w, base, f1, carry, id);
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const uint32_t idx = base + 32u * u + lane;
+      if (idx < f1) {
+        __stcs(a.ids + o + idx, id[u]);
+        if (a.weights) {
+          uint32_t wt = 0;
+          if (IDM == ID_GLOBAL && g.omega) wt = weight_at(g, start, idx);
+          if (IDM == ID_CSR32 && g.W32) wt = __ldg(g.W32 + (start >> 5) + idx);
+          __stcs(a.weights + o + idx, wt);
+        }
+      }
+    }
+  }
+}
+
+template <int IDM, int OFF>
+__global__ void __launch_bounds__(TNT) k_dec_all(GView g, DecArgs a) {
+  __shared__ TileSmem sm;
+  const unsigned hb = heavy_blocks(g.n_items);
+  if (blockIdx.x < hb) {
+    const uint64_t it = (uint64_t)blockIdx.x * (TNT / 32) + (threadIdx.x >> 5);
+    if (it >= g.n_items) return;
+    const HeavyItem h = g.items[it];
+    dec_fields<IDM, HEAVY_U>(g, a, h.bit, h.w, h.f0, h.f0 + h.nf, h.carry, a.row_ptr[h.v]);
+    return;
+  }
+  const uint64_t v0 = (uint64_t)(blockIdx.x - hb) * TV;
+  const int cnt = (int)min((uint64_t)TV, g.n - v0);
+  tile_offsets<OFF>(g, v0, cnt, sm.xs, sm.ts);
+  __syncthreads();
+  tile_classify<IDM>(g, sm, cnt, [](int) { return true; });
+  __shared__ uint64_t orow[TV];  // output row of each light vertex
+  for (uint32_t j = threadIdx.x; j < sm.nlight; j += TNT) orow[j] = a.row_ptr[v0 + sm.clist[j]];
+  __syncthreads();
+  // warp k takes the light vertices whose first field falls in [F k / 8, F (k+1) / 8)
+  constexpr uint32_t NW = TNT / 32;
+  const uint32_t wk = threadIdx.x >> 5;
+  const uint64_t F = sm.nfields;
+  const uint32_t flo = (uint32_t)(F * wk / NW), fhi = (uint32_t)(F * (wk + 1) / NW);
+  uint32_t jb = 0, je = sm.nlight;
+  {
+    uint32_t lo = 0, hi = sm.nlight;
+    while (lo < hi) { const uint32_t m = (lo + hi) >> 1; if (sm.fpre[m] < flo) lo = m + 1; else hi = m; }
+    jb = lo;
+    hi = sm.nlight;
+    while (lo < hi) { const uint32_t m = (lo + hi) >> 1; if (sm.fpre[m] < fhi) lo = m + 1; else hi = m; }
+    je = lo;
+  }
+  if (jb >= je) return;
+  // The warp walks the fields of its vertices [jb, je), contiguous in the
+  // compacted light list, 32 per chunk and DEC_U chunks per step, a lane per
+  // field.  A chunk's vertex starts come from the next 32 entries of fpre (one
+  // per lane), OR-reduced into a mask of the lanes where a vertex begins; a
+  // lane's vertex is the current one plus the starts at or below it.
+  constexpr int DEC_U = 4;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t fend = sm.fpre[je];
+  uint32_t jcur = jb, carry = 0;
+  for (uint32_t b = sm.fpre[jb]; b < fend; b += 32u * DEC_U) {
+    uint32_t vj[DEC_U], vk[DEC_U], val[DEC_U];
+#pragma unroll
+    for (int u = 0; u < DEC_U; u++) {
+      const uint32_t cb = b + 32u * u;
+      const uint32_t nx = jcur + 1 + lane;
+      const uint32_t rel = nx < je ? sm.fpre[nx] - cb : 0xffffffffu;
+      const uint32_t starts = __reduce_or_sync(LG_FULL_MASK, rel < 32u ? (1u << rel) : 0u);
+      const uint32_t upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
+      const uint32_t j = min(jcur + (uint32_t)__popc(starts & upto), je - 1);
+      vj[u] = j;
+      vk[u] = cb + lane - sm.fpre[j];
+      jcur = __shfl_sync(LG_FULL_MASK, j, 31);
+    }
+#pragma unroll
+    for (int u = 0; u < DEC_U; u++) {
+      const uint32_t f = b + 32u * u + lane;
+      const int i = sm.clist[vj[u]];
+      val[u] = f < fend ? field_at<IDM>(g, sm.st[i], sm.wid[i], vk[u]) : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < DEC_U; u++) {
+      const uint32_t f = b + 32u * u + lane;
+      uint32_t x = val[u];
+      if (IDM == ID_LOCAL_GAP) {
+        // segmented inclusive sum: a segment starts at a vertex's first field;
+        // lane 0 continues the previous chunk's vertex with its running ID
+        if (lane == 0 && vk[u] != 0) x += carry;
+        const uint32_t seg0 = vk[u] <= lane ? lane - vk[u] : 0u;  // first lane of this vertex here
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(LG_FULL_MASK, x, o);
+          if (lane >= seg0 + o) x += y;
+        }
+        carry = __shfl_sync(LG_FULL_MASK, x, 31);
+      }
+      if (f < fend) {
+        const int i = sm.clist[vj[u]];
+        const uint64_t o = orow[vj[u]] + vk[u];
+        __stcs(a.ids + o, x);
+        if (a.weights) {
+          uint32_t wt = 0;
+          if (IDM == ID_GLOBAL && g.omega) wt = weight_at(g, sm.st[i], vk[u]);
+          if (IDM == ID_CSR32 && g.W32) wt = __ldg(g.W32 + (sm.st[i] >> 5) + vk[u]);
+          __stcs(a.weights + o, wt);
+        }
+      }
+    }
+  }
+}
+
+// ===========================================================================
 // heavy-vertex schedule, built once per graph from the encoded arrays
 // ===========================================================================
 __device__ __forceinline__ uint32_t items_of(const GView& g, uint32_t d) {
@@ -1189,12 +1330,28 @@ cudaError_t launch_ppr_join(const GView& g, float* cin, uint32_t slot, uint32_t 
 }
 
 template <int IDM, int OFF>
+cudaError_t launch_dec_degrees(const GView& g, const DecArgs& a, cudaStream_t st) {
+  if (g.n == 0) return cudaSuccess;
+  k_dec_degrees<IDM, OFF><<<tiles_of(g.n), TNT, 0, st>>>(g, a);
+  count_launch();
+  return cudaGetLastError();
+}
+template <int IDM, int OFF>
+cudaError_t launch_dec_all(const GView& g, const DecArgs& a, cudaStream_t st) {
+  if (g.n == 0) return cudaSuccess;
+  k_dec_all<IDM, OFF><<<heavy_blocks(g.n_items) + tiles_of(g.n), TNT, 0, st>>>(g, a);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <int IDM, int OFF>
 const TravOps* make_ops() {
   static const TravOps ops = {
       &launch_pr_init<IDM, OFF>,    &launch_pr_pull<IDM, OFF>,     &launch_bfs_pull<IDM, OFF>,
       &launch_bfs_push<IDM, OFF>,   &launch_nbr_degrees<IDM, OFF>, &launch_nbr_decode<IDM, OFF>,
       &launch_plan_count<IDM, OFF>, &launch_plan_fill<IDM, OFF>,   &launch_plan_carry<IDM, OFF>,
-      &launch_ppr_pull<IDM, OFF>,   &launch_ppr_join<IDM, OFF>,
+      &launch_ppr_pull<IDM, OFF>,   &launch_ppr_join<IDM, OFF>,   &launch_dec_degrees<IDM, OFF>,
+      &launch_dec_all<IDM, OFF>,
   };
   return &ops;
 }

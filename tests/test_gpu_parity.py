@@ -78,6 +78,33 @@ def assert_neighbors(g, rp, col, n, w=None, vertices=None):
         assert np.array_equal(wts.cpu().numpy().view(np.uint32), ww)
 
 
+def stored_csr(n, rp, col, w=None, perm=None):
+    """The CSR in stored order: the input, or with a relabel row perm[v] =
+    sorted perm of N_v (weights follow their arcs)."""
+    if perm is None:
+        return rp, col, w
+    perm = np.asarray(perm, dtype=np.int64)
+    deg = np.diff(rp).astype(np.int64)
+    src = np.repeat(np.arange(n, dtype=np.int64), deg)
+    r, c = perm[src], perm[np.asarray(col, dtype=np.int64)]
+    order = np.lexsort((c, r))
+    nrp = np.zeros(n + 1, dtype=np.int64)
+    nrp[1:] = np.cumsum(np.bincount(r, minlength=n))
+    nw = None if w is None else np.asarray(w)[order]
+    return nrp.astype(np.uint64), c[order].astype(np.uint32), nw
+
+
+def assert_decode(g, n, rp, col, w=None, perm=None):
+    want_rp, want_col, want_w = stored_csr(n, rp, col, w, perm)
+    if w is None:
+        grp, gcol = lg.lg_decode(g)
+    else:
+        grp, gcol, gw = lg.lg_decode(g, with_weights=True)
+        assert np.array_equal(gw.cpu().numpy().view(np.uint32), want_w), "decoded weights"
+    assert np.array_equal(grp.cpu().numpy().view(np.uint64), np.asarray(want_rp, dtype=np.uint64)), "decoded row_ptr"
+    assert np.array_equal(gcol.cpu().numpy().view(np.uint32), np.asarray(want_col, dtype=np.uint32)), "decoded col"
+
+
 def assert_bfs(g, n, rp, col, sources):
     d = lg.lg_bfs(g, dev(np.asarray(sources, dtype=np.uint32), np.int32)).cpu().numpy().view(np.uint32)
     for i, s in enumerate(sources):
@@ -103,6 +130,7 @@ def test_exhaustive_tiny_graphs_all_modes(n):
             g, e = encode_both(n, rp, col, mode=mode, off=off, relabel=relabel, sample=64)
             assert_arrays_equal(g, e)
             assert_neighbors(g, rp, col, n)
+            assert_decode(g, n, rp, col, perm=e.perm if relabel else None)
             g.free()
 
 
@@ -257,6 +285,39 @@ def test_relabel_every_row_size_class(weighted):
         assert_neighbors(g, rp, col, n, w=w if weighted and mode == 0 else None)
         if weighted:
             break
+
+
+@pytest.mark.parametrize("mode,off", list(itertools.product(range(3), range(2))))
+@pytest.mark.parametrize("relabel", [False, True])
+def test_decode_whole_graph(rmat16, mode, off, relabel):
+    """lg_decode over R-MAT 2^16 (hubs on the heavy schedule, light runs per
+    warp): the input CSR, or the relabeled CSR in stored order."""
+    g0 = rmat16
+    g, e = encode_both(g0.n, g0.row_ptr, g0.col, mode=mode, off=off, relabel=relabel)
+    assert_decode(g, g0.n, g0.row_ptr, g0.col, perm=e.perm if relabel else None)
+
+
+@pytest.mark.parametrize("relabel", [False, True])
+def test_decode_csr32_and_weights(rmat16, relabel):
+    g0 = rmat16
+    g = lg.lg_encode(dev(g0.row_ptr, np.int64), dev(g0.col, np.int32), id_mode=lg.LG_ID_CSR32, relabel=relabel)
+    perm = lg.lg_arrays_get(g)["perm"] if relabel else None
+    assert_decode(g, g0.n, g0.row_ptr, g0.col, perm=perm)
+    w0 = gen.rmat(12, 16, seed=8, weighted=True)
+    g, e = encode_both(w0.n, w0.row_ptr, w0.col, w0.weights, mode=0, off=1, relabel=relabel, weight_bits=23)
+    assert_decode(g, w0.n, w0.row_ptr, w0.col, w=w0.weights, perm=e.perm if relabel else None)
+
+
+def test_decode_errors(rmat16):
+    g0 = rmat16
+    g, _ = encode_both(g0.n, g0.row_ptr, g0.col, mode=2, off=1)
+    lib = lg.load()
+    rp = torch.empty(g0.n + 1, dtype=torch.int64, device="cuda")
+    col = torch.empty(len(g0.col), dtype=torch.int32, device="cuda")
+    st = torch.cuda.current_stream().cuda_stream
+    assert lib.lg_decode(g.handle, rp.data_ptr(), col.data_ptr(), None, len(g0.col) - 1, st) == 4  # LG_ERANGE
+    assert lib.lg_decode(g.handle, rp.data_ptr(), col.data_ptr(), col.data_ptr(), len(g0.col), st) == 1  # no weights
+    assert lib.lg_decode(None, rp.data_ptr(), col.data_ptr(), None, len(g0.col), st) == 1
 
 
 # ------------------------------------------------------------------ queries and errors
