@@ -607,11 +607,14 @@ __global__ void k_dm_perm(const uint32_t* __restrict__ inv, uint64_t n, uint32_t
 }
 // New rows P(v) = { P(u) : u in N_v }.  A warp takes 32 consecutive new rows.
 // Rows of <= 32 arcs are gathered into the warp's shared slots (a row per
-// step, coalesced reads of the old row, four rows' perm lookups in flight),
+// step, coalesced reads of the old row, DM_INFLIGHT rows' perm lookups in
+// flight),
 // sorted one per lane in registers and written out coalesced, so they are
 // final here.  Longer rows are copied unsorted (the size-class sorts follow).
 // Rows stream through L2 (evict-first loads, streaming stores) so that the
 // randomly gathered perm array stays resident (evict-last).
+constexpr int DM_INFLIGHT = 8;  // rows whose loads and perm lookups are in flight together
+
 template <bool VALS>
 __global__ void __launch_bounds__(256) k_dm_rows(const uint64_t* __restrict__ rp, const uint32_t* __restrict__ col,
                                                  const uint32_t* __restrict__ w, const uint32_t* __restrict__ inv,
@@ -637,17 +640,17 @@ __global__ void __launch_bounds__(256) k_dm_rows(const uint64_t* __restrict__ rp
     const bool small = d <= SEG_SMALL;
     const uint32_t todo = __ballot_sync(LG_FULL_MASK, small && d > 0);
     for (uint32_t t = todo; t;) {
-      int q[4];
-      uint32_t c[4];
-      bool on[4];
+      int q[DM_INFLIGHT];
+      uint32_t c[DM_INFLIGHT];
+      bool on[DM_INFLIGHT];
 #pragma unroll
-      for (int z = 0; z < 4; z++) {
+      for (int z = 0; z < DM_INFLIGHT; z++) {
         q[z] = t ? __ffs(t) - 1 : 0;
         on[z] = t != 0;
         if (t) t &= t - 1;
       }
 #pragma unroll
-      for (int z = 0; z < 4; z++) {
+      for (int z = 0; z < DM_INFLIGHT; z++) {
         const uint64_t lq = __shfl_sync(LG_FULL_MASK, lo, q[z]);
         const uint32_t dq = __shfl_sync(LG_FULL_MASK, d, q[z]);
         on[z] = on[z] && (uint32_t)lane < dq;
@@ -655,7 +658,7 @@ __global__ void __launch_bounds__(256) k_dm_rows(const uint64_t* __restrict__ rp
         if (VALS && on[z]) sv[q[z] * SROW + lane] = ldg_hint(w + lq + lane, pstream);
       }
 #pragma unroll
-      for (int z = 0; z < 4; z++) {
+      for (int z = 0; z < DM_INFLIGHT; z++) {
         if (on[z]) sk[q[z] * SROW + lane] = ldg_hint(perm + c[z], pkeep);
       }
     }
