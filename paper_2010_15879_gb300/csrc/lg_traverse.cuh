@@ -251,7 +251,9 @@ __device__ __forceinline__ uint32_t field_at(const GView& g, uint64_t start, uin
   if (IDM == ID_GLOBAL) return ext32(g.A32, start + i * g.r, g.s);
   if (IDM == ID_CSR32) return __ldg(g.A32 + (start >> 5) + i);
   if (IDM == ID_LOCAL) return ext32(g.A32, start + i * w, w);
-  return i == 0 ? ext32(g.A32, start, g.s) : ext32(g.A32, start + g.s + (i - 1) * (uint64_t)w, w);
+  // the first field holds the absolute ID in s bits, the others gaps in w bits
+  const uint64_t p = i == 0 ? start : start + g.s + (i - 1) * (uint64_t)w;
+  return ext32(g.A32, p, i == 0 ? g.s : w);
 }
 __device__ __forceinline__ uint32_t weight_at(const GView& g, uint64_t start, uint64_t i) {
   return ext32(g.A32, start + i * g.r + g.s, g.omega);
