@@ -125,6 +125,10 @@ class Workload:
         _G.n, _G.row_ptr = self.n, self.host()[0]
         return gen.sources(_G, self.S, seed=7)
 
+    def csr_gb(self):
+        """Bytes of the input CSR (row_ptr, col, weights) in GB."""
+        return ((self.n + 1) * 8 + self.arcs * 4 * (1 if self.w_d is None else 2)) / 1e9
+
     def teps_bfs(self, depths):
         """Graph500 traversed edges summed over the sources (on the device)."""
         total = 0
@@ -132,6 +136,10 @@ class Workload:
             total += int(self.deg_d[row != -1].sum().item()) // 2
         return total
 HBM_FALLBACK_GBS = 6800.0
+# One metric for both arms: GTEPS, a BFS from one source counting (sum of the
+# degrees of the reached vertices) / 2 (Graph500) and a PageRank iteration every
+# stored arc once.  Each line's config / cpu_baseline says what one step ran.
+METRIC_LG = "GTEPS (BFS + PageRank traversed edges per second, Graph500 counting; compressed vs 32-bit CSR)"
 
 
 def log(*a):
@@ -182,6 +190,8 @@ class ClockSampler:
         self.f = None
 
     def __enter__(self):
+        if self.idx is None:  # sampling off
+            return self
         try:
             self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
@@ -240,32 +250,23 @@ def combine_replicas(step_ms, e2e_ms, te_step, world, device=None):
 
 
 # --------------------------------------------------------------------- GPU arm
-def run_lg(args, rank, world):
+def time_arms(lg, wl, steps, warmup, dev, barrier, rank, with_csr_dm=True, clocks=True):
+    """The hot path timed on the device (inputs resident in HBM): the
+    compressed graph and, beside it, the same kernels on the 32-bit CSR (and
+    on the CSR relabeled by the same DM permuter when the compressed arm
+    relabels).  One step = lg_encode + lg_bfs (S sources) + lg_pagerank (T
+    iterations) + lg_free."""
     import torch
 
-    import paper_2010_15879_gb300 as lg
-
-    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
-    torch.cuda.set_device(dev)
-    lg.load(auto_build=True)
-    wl = Workload(args.workload, dev)
-    desc, opts, S, T = wl.desc, wl.opts, wl.S, wl.T
-    src_h = wl.sources()
-    rp_d, col_d, w_d = wl.rp_d, wl.col_d, wl.w_d
-    src_d = torch.from_numpy(src_h.view(np.int32)).to(dev)
+    opts, S, T = wl.opts, wl.S, wl.T
+    src_d = torch.from_numpy(wl.sources().view(np.int32)).to(dev)
     depths = torch.empty((S, wl.n), dtype=torch.int32, device=dev)
     ranks = torch.empty(wl.n, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
-    def step(id_mode_opts, ev=None):
-        """one pass of the hot path; optional events (enc, bfs, pr, end)."""
+    def step(o, ev=None):
         if ev: ev[0].record(stream)
-        g = lg.lg_encode(rp_d, col_d, w_d, **id_mode_opts)
+        g = lg.lg_encode(wl.rp_d, wl.col_d, wl.w_d, **o)
         if ev: ev[1].record(stream)
         lg.lg_bfs(g, src_d, out=depths)
         if ev: ev[2].record(stream)
@@ -275,184 +276,323 @@ def run_lg(args, rank, world):
         g.free()
         return st
 
-    def timed(id_mode_opts, label):
-        for _ in range(args.warmup):
-            step(id_mode_opts)
+    def timed(o, label, sample_clocks=False):
+        for _ in range(warmup):
+            step(o)
         torch.cuda.synchronize(dev)
-        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
         start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
         torch.cuda.synchronize(dev)
         l0 = lg.lg_kernel_launches()
-        start.record(stream)
-        for k in range(args.steps):
-            st = step(id_mode_opts, evs[k])
-        stop.record(stream)
-        torch.cuda.synchronize(dev)
+        with ClockSampler(dev.index if sample_clocks else None) as clk:
+            start.record(stream)
+            for k in range(steps):
+                st = step(o, evs[k])
+            stop.record(stream)
+            torch.cuda.synchronize(dev)
         barrier()
         launches = lg.lg_kernel_launches() - l0
         ms = start.elapsed_time(stop)
         enc = [e[0].elapsed_time(e[1]) for e in evs]
         bfs = [e[1].elapsed_time(e[2]) for e in evs]
         pr = [e[2].elapsed_time(e[3]) for e in evs]
-        log(f"[rank {rank}] {label}: step {ms / args.steps:.2f} ms (encode {np.median(enc):.2f}, "
+        log(f"[rank {rank}] {wl.name} {label}: step {ms / steps:.2f} ms (encode {np.median(enc):.2f}, "
             f"bfs {np.median(bfs):.2f}, pr {np.median(pr):.2f})")
-        return dict(ms=ms, enc=enc, bfs=bfs, pr=pr, stats=st, launches=launches)
+        return dict(ms=ms, enc=enc, bfs=bfs, pr=pr, stats=st, launches=launches, clocks=clk.summary())
 
-    # TEPS accounting from one BFS run
-    step(opts)
+    step(opts)  # TEPS accounting from one untimed run
     torch.cuda.synchronize(dev)
     te_bfs = wl.teps_bfs(depths)
     te_pr = wl.arcs * T
-    te_step = te_bfs + te_pr
-
-    with ClockSampler(dev.index) as clk:
-        res = timed(opts, "log(graph)")
-    clocks = clk.summary()
+    res = timed(opts, "log(graph)", sample_clocks=clocks)
     csr = timed(dict(id_mode=3, relabel=False), "csr32")
-    # the same CSR in the DM order, when the compressed arm relabels (ordering alone changes locality)
-    csr_dm = timed(dict(id_mode=3, relabel=True), "csr32 in DM order") if opts.get("relabel") else None
+    csr_dm = timed(dict(id_mode=3, relabel=True), "csr32 in DM order") if (with_csr_dm and opts.get("relabel")) else None
+    del depths, ranks
+    return dict(lg=res, csr=csr, csr_dm=csr_dm, te_bfs=te_bfs, te_pr=te_pr, te_step=te_bfs + te_pr)
 
-    # whole-graph decode (lg_decode) of the compressed graph: a streaming
-    # kernel (compressed A and O in, the 32-bit CSR out), timed alone
-    gdec = lg.lg_encode(rp_d, col_d, w_d, **opts)
+
+def time_decode(lg, wl, dev, reps=5):
+    """lg_decode of the compressed graph (a streaming kernel: compressed A
+    and O in, the 32-bit CSR out), CUDA events on the launching stream."""
+    import torch
+
+    stream = torch.cuda.current_stream(dev)
+    g = lg.lg_encode(wl.rp_d, wl.col_d, wl.w_d, **wl.opts)
     dec_rp = torch.empty(wl.n + 1, dtype=torch.int64, device=dev)
     dec_col = torch.empty(wl.arcs, dtype=torch.int32, device=dev)
     lib = lg.load()
-    dec_ms = []
-    for k in range(6):
+    ms = []
+    for k in range(reps + 1):
         d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         d0.record(stream)
-        rc = lib.lg_decode(gdec.handle, dec_rp.data_ptr(), dec_col.data_ptr(), None, wl.arcs, stream.cuda_stream)
+        rc = lib.lg_decode(g.handle, dec_rp.data_ptr(), dec_col.data_ptr(), None, wl.arcs, stream.cuda_stream)
         d1.record(stream)
         torch.cuda.synchronize(dev)
         if rc != 0:
             raise SystemExit(f"lg_decode failed: {lg.lg_last_error()}")
         if k:
-            dec_ms.append(d0.elapsed_time(d1))
-    dst = gdec.stats()
-    gdec.free()
+            ms.append(d0.elapsed_time(d1))
+    st = g.stats()
+    g.free()
     del dec_rp, dec_col
-    dec_ms = float(np.median(dec_ms))
-    dec_bytes = (dst["bits_A"] + dst["bits_O"]) // 8 + 8 * (wl.n + 1) + 4 * wl.arcs
+    peak, _ = peaks()
+    t = float(np.median(ms))
+    alg = (st["bits_A"] + st["bits_O"]) // 8 + 8 * (wl.n + 1) + 4 * wl.arcs
+    kern = ("k_dec_degrees (row pass) + k_dec_flat (records in arc order)" if wl.opts["id_mode"] == 0 else
+            "k_dec_degrees + scan + k_dec_local (tile rounds staged in shared memory)")
+    return {"kernel": f"lg_decode: whole graph to 32-bit CSR ({kern})", "ms": t, "algorithmic_bytes": alg,
+            "achieved_gbs": alg / (t * 1e-3) / 1e9, "frac": alg / (t * 1e-3) / 1e9 / peak, "peak_gbs": peak}
 
-    # e2e: host CSR in pinned memory -> device -> hot path -> results to pinned host
+
+def gather_ceiling(lg, table_len, count, dev, reps=5):
+    """Rate (G gathers/s) at which the GPU serves uniformly random 4-byte
+    reads from a table of `table_len` floats, with the pull kernels' load and
+    L2 policy (lg_probe_gather), CUDA events on the launching stream."""
+    import torch
+
+    stream = torch.cuda.current_stream(dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(12345)
+    idx = torch.randint(0, table_len, (count,), dtype=torch.int32, device=dev, generator=g)
+    table = torch.rand(table_len, dtype=torch.float32, device=dev)
+    out = torch.empty(min(count, lg.PROBE_THREADS), dtype=torch.float32, device=dev)
+    ms = []
+    for k in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lg.lg_probe_gather(idx, table, out)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if k:
+            ms.append(e0.elapsed_time(e1))
+    del idx, table, out
+    t = float(np.median(ms))
+    return {"table_bytes": 4 * table_len, "gathers": count, "ms": t, "g_gathers_per_s": count / (t * 1e-3) / 1e9}
+
+
+def time_e2e(lg, wl, steps, warmup, dev, barrier):
+    """End to end through the public API: every step copies its CSR from
+    pinned host memory into the device, runs encode + BFS + PageRank and
+    reads the depths and ranks back into pinned host memory.  The steps run
+    back to back on the compute stream over two preallocated sets of device
+    buffers; a copy stream loads the next step's input into the other set and
+    reads the previous step's results back while a step computes (events order
+    each copy after the compute that frees or fills its buffer)."""
+    import torch
+
+    opts, S, T = wl.opts, wl.S, wl.T
+    comp = torch.cuda.current_stream(dev)
+    copy = torch.cuda.Stream(dev)
+    src_h = wl.sources()
     rp_hn, col_hn, w_hn = wl.host()
-    rp_h = torch.from_numpy(rp_hn.view(np.int64))
-    col_h = torch.from_numpy(col_hn.view(np.int32))
-    w_h = None if w_hn is None else torch.from_numpy(w_hn.view(np.int32))
-    rp_p, col_p = rp_h.pin_memory(), col_h.pin_memory()
-    w_p = None if w_h is None else w_h.pin_memory()
+    rp_p = torch.from_numpy(rp_hn.view(np.int64)).pin_memory()
+    col_p = torch.from_numpy(col_hn.view(np.int32)).pin_memory()
+    w_p = None if w_hn is None else torch.from_numpy(w_hn.view(np.int32)).pin_memory()
     src_p = torch.from_numpy(src_h.view(np.int32)).pin_memory()
-    # consecutive steps alternate between two streams, so that one step's
-    # host->device copy and result read-back overlap the other's kernels;
-    # every step still copies its own inputs and reads back its own results
-    e2e_streams = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
-    dep_d = [depths, torch.empty_like(depths)]
-    rk_d = [ranks, torch.empty_like(ranks)]
+
+    def dev_like(t):
+        return None if t is None else torch.empty(t.shape, dtype=t.dtype, device=dev)
+
+    # input set 0 is the workload's own device copy (overwritten with the same bytes)
+    ins = [(wl.rp_d, wl.col_d, wl.w_d, dev_like(src_p)),
+           (dev_like(rp_p), dev_like(col_p), dev_like(w_p), dev_like(src_p))]
+    dep_d = [torch.empty((S, wl.n), dtype=torch.int32, device=dev) for _ in range(2)]
+    rk_d = [torch.empty(wl.n, dtype=torch.float32, device=dev) for _ in range(2)]
     dep_p = [torch.empty((S, wl.n), dtype=torch.int32).pin_memory() for _ in range(2)]
     rk_p = [torch.empty(wl.n, dtype=torch.float32).pin_memory() for _ in range(2)]
-    e2e_k = [0]
+    ev = lambda: torch.cuda.Event()  # noqa: E731
+    in_ready = [ev(), ev()]      # input set i loaded
+    comp_done = [ev(), ev()]     # the step on set i finished (its input and outputs free to copy)
+    out_copied = [ev(), ev()]    # results of set i read back
+    for i in range(2):
+        comp_done[i].record(comp)
+        out_copied[i].record(comp)
 
-    def e2e_step():
-        i = e2e_k[0] & 1
-        e2e_k[0] += 1
-        s = e2e_streams[i]
-        g = lg.lg_encode(rp_p, col_p, w_p, stream=s, **opts)
-        d = lg.lg_bfs(g, src_p, out=dep_d[i], stream=s)
-        r = lg.lg_pagerank(g, 0.85, T, out=rk_d[i], stream=s)
-        with torch.cuda.stream(s):
-            dep_p[i].copy_(d, non_blocking=True)
-            rk_p[i].copy_(r, non_blocking=True)
-        g.free(stream=s)
+    def load(i):
+        rp_i, col_i, w_i, src_i = ins[i]
+        copy.wait_event(comp_done[i])
+        with torch.cuda.stream(copy):
+            rp_i.copy_(rp_p, non_blocking=True)
+            col_i.copy_(col_p, non_blocking=True)
+            if w_i is not None:
+                w_i.copy_(w_p, non_blocking=True)
+            src_i.copy_(src_p, non_blocking=True)
+        in_ready[i].record(copy)
 
-    for _ in range(max(2, args.warmup)):
-        e2e_step()
+    def run(k, total):
+        """step k: compute on set k & 1, then queue the next load and this read-back"""
+        i = k & 1
+        rp_i, col_i, w_i, src_i = ins[i]
+        comp.wait_event(in_ready[i])
+        comp.wait_event(out_copied[i])
+        g = lg.lg_encode(rp_i, col_i, w_i, stream=comp, **opts)
+        lg.lg_bfs(g, src_i, out=dep_d[i], stream=comp)
+        lg.lg_pagerank(g, 0.85, T, out=rk_d[i], stream=comp)
+        g.free(stream=comp)
+        comp_done[i].record(comp)
+        if k + 1 < total:
+            load(1 - i)
+        copy.wait_event(comp_done[i])
+        with torch.cuda.stream(copy):
+            dep_p[i].copy_(dep_d[i], non_blocking=True)
+            rk_p[i].copy_(rk_d[i], non_blocking=True)
+        out_copied[i].record(copy)
+
+    def loop(total):
+        load(0)
+        for k in range(total):
+            run(k, total)
+
+    torch.cuda.synchronize(dev)
+    loop(max(2, warmup))
     torch.cuda.synchronize(dev)
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e2e_marks = []
-    e0.record(stream)
-    for s in e2e_streams:
-        s.wait_stream(stream)
-    for _ in range(args.steps):
-        e2e_step()
+    marks = []
+    e0.record(comp)
+    copy.wait_stream(comp)
+    load(0)
+    for k in range(steps):
+        run(k, steps)
         mk = torch.cuda.Event(enable_timing=True)
-        mk.record(e2e_streams[(e2e_k[0] - 1) & 1])
-        e2e_marks.append(mk)
-    for s in e2e_streams:
-        stream.wait_stream(s)
-    e1.record(stream)
+        mk.record(copy)
+        marks.append(mk)
+    comp.wait_stream(copy)
+    e1.record(comp)
     torch.cuda.synchronize(dev)
-    e2e_done_ms = [e0.elapsed_time(m) for m in e2e_marks]
     barrier()
-    e2e_ms = e0.elapsed_time(e1) / args.steps
-    h2d = rp_h.numel() * 8 + col_h.numel() * 4 + (0 if w_h is None else w_h.numel() * 4) + S * 4
+    done = [e0.elapsed_time(m) for m in marks]
+    ms = e0.elapsed_time(e1) / steps
+    h2d = rp_p.numel() * 8 + col_p.numel() * 4 + (0 if w_p is None else w_p.numel() * 4) + S * 4
     d2h = S * wl.n * 4 + wl.n * 4
+    del ins[1], dep_d, rk_d, dep_p, rk_p
+    return dict(ms=ms, h2d=h2d, d2h=d2h, done=done)
 
-    step_ms = res["ms"] / args.steps
+
+def arms_detail(wl, arms, dec=None):
+    """Kernel-level comparison of one workload: bytes, BFS / PageRank GTEPS,
+    compressed against the 32-bit CSR through the same kernels."""
+    T = wl.T
+    res, csr, csr_dm = arms["lg"], arms["csr"], arms["csr_dm"]
     st = res["stats"]
-    pr_ms_iter = float(np.median(res["pr"])) / T
+    steps = len(res["enc"])
+    pr_ms = float(np.median(res["pr"])) / T
     bfs_ms = float(np.median(res["bfs"]))
-    csr_pr_ms_iter = float(np.median(csr["pr"])) / T
+    csr_pr_ms = float(np.median(csr["pr"])) / T
     csr_bfs_ms = float(np.median(csr["bfs"]))
+    comp = (st["bits_A"] + st["bits_O"]) / 8
+    d = {
+        "workload": wl.desc, "n": wl.n, "arcs": wl.arcs, "bfs_sources": wl.S, "pr_iters": T,
+        "step_ms": res["ms"] / steps, "value_gteps": arms["te_step"] / (res["ms"] / steps * 1e-3) / 1e9,
+        "encode_ms": float(np.median(res["enc"])), "bfs_ms": bfs_ms, "pr_ms_per_iter": pr_ms,
+        "bfs_gteps": arms["te_bfs"] / (bfs_ms * 1e-3) / 1e9, "pr_gteps": arms["te_pr"] / (pr_ms * T * 1e-3) / 1e9,
+        "bits_per_arc": st["bits_per_arc"], "bits_A": st["bits_A"], "bits_O": st["bits_O"],
+        "bytes_total": st["bytes_total"],
+        "csr32": {"step_ms": csr["ms"] / steps, "encode_ms": float(np.median(csr["enc"])),
+                  "bfs_ms": csr_bfs_ms, "pr_ms_per_iter": csr_pr_ms,
+                  "bfs_gteps": arms["te_bfs"] / (csr_bfs_ms * 1e-3) / 1e9,
+                  "pr_gteps": arms["te_pr"] / (csr_pr_ms * T * 1e-3) / 1e9,
+                  "bytes_payload": 4 * wl.arcs + 8 * (wl.n + 1),
+                  "value_gteps": arms["te_step"] / (csr["ms"] / steps * 1e-3) / 1e9},
+        "csr32_dm_order": None if csr_dm is None else {
+            "note": "the same uncompressed CSR relabeled by the same DM permuter",
+            "step_ms": csr_dm["ms"] / steps, "encode_ms": float(np.median(csr_dm["enc"])),
+            "bfs_ms": float(np.median(csr_dm["bfs"])), "pr_ms_per_iter": float(np.median(csr_dm["pr"])) / T,
+            "bfs_gteps_vs": float(np.median(csr_dm["bfs"])) / bfs_ms,
+            "pr_gteps_vs": float(np.median(csr_dm["pr"])) / T / pr_ms,
+            "value_gteps": arms["te_step"] / (csr_dm["ms"] / steps * 1e-3) / 1e9},
+        "bfs_gteps_vs_csr32": csr_bfs_ms / bfs_ms, "pr_gteps_vs_csr32": csr_pr_ms / pr_ms,
+    }
+    if wl.w_d is None:
+        d["bytes_vs_csr32"] = comp / (4 * wl.arcs + 8 * (wl.n + 1))
+    else:
+        # weighted: against the weighted CSR (32-bit IDs + 32-bit weights), and the
+        # same graph encoded without weights against the unweighted CSR-32
+        d["bytes_vs_weighted_csr32"] = comp / (8 * wl.arcs + 8 * (wl.n + 1))
+        unw_bits = st["bits_A"] // (st["s"] + st["omega"]) * st["s"] if st["id_mode"] == 0 else None
+        d["bytes_unweighted_vs_csr32"] = (None if unw_bits is None else
+                                          (unw_bits + st["bits_O"]) / 8 / (4 * wl.arcs + 8 * (wl.n + 1)))
+    if dec is not None:
+        d["decode"] = dec
+    return d
+
+
+def run_lg(args, rank, world):
+    import torch
+
+    import paper_2010_15879_gb300 as lg
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    lg.load(auto_build=True)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    wl = Workload(args.workload, dev)
+    arms = time_arms(lg, wl, args.steps, args.warmup, dev, barrier, rank)
+    dec = time_decode(lg, wl, dev)
+    e2e = time_e2e(lg, wl, args.steps, args.warmup, dev, barrier)
+    res = arms["lg"]
+    st = res["stats"]
+    T = wl.T
+    pr_ms_iter = float(np.median(res["pr"])) / T
     # algorithmic bytes of one PageRank pull launch: the compressed A and O
     # payload, a 4 B contribution gather per arc and a 4 B contribution write
     # per vertex
     alg_bytes = (st["bits_A"] + st["bits_O"]) // 8 + 4 * wl.arcs + 4 * wl.n
     peak, peak_kind = peaks()
     achieved = alg_bytes / (pr_ms_iter * 1e-3) / 1e9
-
+    step_ms = res["ms"] / args.steps
     out = {
-        "metric": "GTEPS (BFS 16 sources + PageRank 20 iterations, Log(Graph) compressed, full step incl. encode)",
+        "metric": METRIC_LG,
         "value": None, "unit": "GTEPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u32 ids / fp32 ranks", "data": "synthetic (seeded generator; no dataset)",
-        "config": {"workload": desc, "n": wl.n, "arcs": wl.arcs, "bfs_sources": S, "pr_iters": T,
-                   "damping": 0.85, "l2": "inputs larger than L2 (CSR %.2f GB)" %
-                   ((wl.n + 1) * 8 / 1e9 + wl.arcs * 4 / 1e9), "parallelism": f"replicas x{world}"},
+        "config": {"workload": wl.desc, "n": wl.n, "arcs": wl.arcs, "bfs_sources": wl.S, "pr_iters": T,
+                   "damping": 0.85, "step": f"lg_encode + lg_bfs ({wl.S} sources) + lg_pagerank ({T} iterations) "
+                   "+ lg_free", "l2": "inputs larger than L2 (CSR %.2f GB)" % wl.csr_gb(),
+                   "parallelism": f"replicas x{world}"},
     }
-    step_ms, e2e_ms, value, e2e_value = combine_replicas(step_ms, e2e_ms, te_step, world, dev)
+    step_ms, e2e_ms, value, e2e_value = combine_replicas(step_ms, e2e["ms"], arms["te_step"], world, dev)
     out["ms_per_step"] = step_ms
     out["value"] = value
     out["e2e"] = {"value": e2e_value, "unit": "GTEPS", "ms_per_step": e2e_ms,
-                  "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                  "overlap": "two streams: one step's copies overlap the other's kernels",
-                  "step_done_ms": e2e_done_ms}
+                  "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
+                  "overlap": "a copy stream loads step k+1's input and reads step k-1's results back while step "
+                             "k computes (two preallocated device buffer sets)", "step_done_ms": e2e["done"]}
     out["gpu_launches"] = int(res["launches"])
-    out["detail"] = {
-        "decode": {"kernel": "k_dec_degrees + scan + k_dec_all (lg_decode: whole graph to 32-bit CSR)",
-                   "ms": dec_ms, "algorithmic_bytes": dec_bytes,
-                   "achieved_gbs": dec_bytes / (dec_ms * 1e-3) / 1e9,
-                   "frac": dec_bytes / (dec_ms * 1e-3) / 1e9 / peak, "peak_gbs": peak},
-        "encode_ms": float(np.median(res["enc"])), "bfs_ms": bfs_ms, "pr_ms_per_iter": pr_ms_iter,
-        "bfs_gteps": te_bfs / (bfs_ms * 1e-3) / 1e9, "pr_gteps": te_pr / (pr_ms_iter * T * 1e-3) / 1e9,
-        "bits_per_arc": st["bits_per_arc"], "bits_A": st["bits_A"], "bits_O": st["bits_O"],
-        "bytes_total": st["bytes_total"],
-        "csr32": {"step_ms": csr["ms"] / args.steps, "encode_ms": float(np.median(csr["enc"])),
-                  "bfs_ms": csr_bfs_ms, "pr_ms_per_iter": csr_pr_ms_iter,
-                  "bfs_gteps": te_bfs / (csr_bfs_ms * 1e-3) / 1e9,
-                  "pr_gteps": te_pr / (csr_pr_ms_iter * T * 1e-3) / 1e9,
-                  "bytes_payload": 4 * wl.arcs + 8 * (wl.n + 1),
-                  "value": te_step / (csr["ms"] / args.steps * 1e-3) / 1e9},
-        "csr32_dm_order": None if csr_dm is None else {
-            "note": "the same uncompressed CSR relabeled by the same DM permuter",
-            "step_ms": csr_dm["ms"] / args.steps, "encode_ms": float(np.median(csr_dm["enc"])),
-            "bfs_ms": float(np.median(csr_dm["bfs"])), "pr_ms_per_iter": float(np.median(csr_dm["pr"])) / T,
-            "value": te_step / (csr_dm["ms"] / args.steps * 1e-3) / 1e9},
-        "bytes_vs_csr32": ((st["bits_A"] + st["bits_O"]) / 8) / (4 * wl.arcs + 8 * (wl.n + 1)),
-        "bfs_gteps_vs_csr32": csr_bfs_ms / bfs_ms, "pr_gteps_vs_csr32": csr_pr_ms_iter / pr_ms_iter,
-    }
+    out["detail"] = arms_detail(wl, arms, dec)
     out["roofline"] = {"kernel": "k_pr_pull (PageRank pull iteration, decode fused)", "bound": "hbm",
                        "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                        "peak_kind": f"{peak_kind} (copy bandwidth)",
                        "algorithmic_bytes_per_launch": alg_bytes,
                        "traffic": ncu_traffic(args.workload)}
-    out["clocks"] = clocks
+    # the rate of scattered 4-byte reads the PageRank gathers run into: at the
+    # workload's contribution-array size and at an L2-resident 64 MiB
+    cnt = min(wl.arcs, 1 << 30)
+    ceil_full = gather_ceiling(lg, wl.n, cnt, dev)
+    ceil_l2 = gather_ceiling(lg, 1 << 24, cnt, dev)
+    pr_rate = wl.arcs / (pr_ms_iter * 1e-3) / 1e9
+    out["detail"]["gather_ceiling"] = {
+        "probe": "lg_probe_gather: uniformly random 4-byte gathers + a coalesced index stream",
+        "contrib_size": ceil_full, "l2_resident_64MiB": ceil_l2, "pr_gathers_per_s": pr_rate,
+        "pr_frac_of_ceiling_at_contrib_size": pr_rate / ceil_full["g_gathers_per_s"]}
+    out["roofline"]["gather_ceiling_frac"] = pr_rate / ceil_full["g_gathers_per_s"]
+    out["clocks"] = res["clocks"]
+    if args.workload == "rmat27" and not args.no_secondary:
+        # the local-gap / DM workload beside the headline: the <= 75 % bytes
+        # evidence and the local-ID decode
+        wl2 = Workload("community", dev)
+        arms2 = time_arms(lg, wl2, max(3, args.steps // 4), 3, dev, barrier, rank, clocks=False)
+        out["detail"]["community_2p24"] = arms_detail(wl2, arms2, time_decode(lg, wl2, dev))
+        del wl2
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rp_hn, col_hn, _ = wl.host()
-        out["cpu_baseline"] = cpu_baseline(wl.n, rp_hn, col_hn, src_h, min_seconds=10.0,
-                                           bfs_only=(args.workload == "rmat27"))
+        out["cpu_baseline"] = cpu_baseline(wl.n, rp_hn, col_hn, wl.sources(), wl.T, args.workload)
     return out, rank
 
 
@@ -869,29 +1009,73 @@ def cpu_baseline_batch(vptr, rp, col, iters, min_seconds=10.0, max_graphs=None):
 
 
 # ------------------------------------------------------------------ CPU oracle
-def cpu_baseline(n, rp, col, src_h, min_seconds=10.0, max_units=None, bfs_only=False):
-    """The oracle as it stands (single-threaded C) on a bounded sample: BFS from
-    the first sources and whole PageRank iterations, until about min_seconds."""
+def host_cores():
+    """Host threads this process may use (os.sched_getaffinity)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def oracle_bfs_teps(n, rp, col, deg, sources, threads):
+    """Graph500 edges of oracle BFS runs from `sources`, `threads` of them at
+    a time (one BFS per thread; the oracle's BFS is sequential)."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+
+    def one(s):
+        d = oracle.bfs(n, rp, col, int(s))
+        return int(deg[d != 0xFFFFFFFF].sum()) // 2
+
+    if threads == 1:
+        return sum(one(s) for s in sources)
+    with ThreadPoolExecutor(threads) as ex:
+        return sum(ex.map(one, sources))
+
+
+def cpu_baseline(n, rp, col, src_h, iters, workload):
+    """The oracle as it stands (plain C, FP64 PageRank, FIFO BFS) on the box's
+    host cores, on bounded samples of the same workload:
+      single thread -- BFS from the first source(s), then whole PageRank
+                       iterations while the sample is under ~10 s;
+      every core    -- one BFS source per thread at once plus whole PageRank
+                       iterations split over every core by OpenMP.
+    At scale 27 one BFS alone takes ~45 s on one core, so there the single-
+    thread sample is one BFS source and the all-core sample is PageRank
+    iterations only."""
     import oracle
 
+    cores = host_cores()
     deg = np.diff(rp).astype(np.int64)
-    te = 0
+    big = col.shape[0] > 1_000_000_000
+    # single thread
     t0 = time.time()
-    nb = npr = 0
-    while True:
-        s = int(src_h[nb % len(src_h)])
-        d = oracle.bfs(n, rp, col, s)
-        te += int(deg[d != 0xFFFFFFFF].sum()) // 2
-        nb += 1
-        if not bfs_only:
-            oracle.pagerank(n, rp, col, 0.85, 1)
-            te += col.shape[0]
-            npr += 1
-        el = time.time() - t0
-        if el >= min_seconds or (max_units and nb >= max_units):
-            break
-    return {"value": te / el / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
-            "sample": f"{nb} BFS source(s) + {npr} PageRank iteration(s) of the same graph, {el:.1f} s"}
+    te = oracle_bfs_teps(n, rp, col, deg, src_h[:1], 1)
+    nb, npr = 1, 0
+    while not big and time.time() - t0 < 10.0:
+        oracle.pagerank(n, rp, col, 0.85, 1)
+        te += col.shape[0]
+        npr += 1
+    el1 = time.time() - t0
+    single = {"value": te / el1 / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+              "sample": f"{nb} BFS source + {npr} PageRank iteration(s) of the same graph, one thread, {el1:.1f} s"}
+    # every core
+    t0 = time.time()
+    te, nb = 0, 0
+    if not big:
+        nb = min(cores, len(src_h))
+        te += oracle_bfs_teps(n, rp, col, deg, src_h[:nb], cores)
+    npr = 0
+    while npr < 1 or time.time() - t0 < 10.0:
+        oracle.pagerank(n, rp, col, 0.85, 1, threads=cores)
+        te += col.shape[0]
+        npr += 1
+    el = time.time() - t0
+    return {"value": te / el / 1e9, "unit": "GTEPS", "cores": cores, "kind": "oracle",
+            "sample": (f"{nb} BFS sources on {cores} threads at once + " if nb else "") +
+                      f"{npr} PageRank iteration(s) on {cores} OpenMP threads, whole graph, {el:.1f} s "
+                      f"(of {iters} in a step)",
+            "single_core": single, "host_cores": cores}
 
 
 def profile_pass(args):
@@ -1046,29 +1230,45 @@ def run_reference(args, rank, world):
     if args.workload == "rmat27":
         wl = Workload(args.workload, dev)
         n, (rp, col, _), src_h, desc, S, T = wl.n, wl.host(), wl.sources(), wl.desc, wl.S, wl.T
+        del wl
+        torch.cuda.empty_cache()
     else:
         desc, make, opts, S, T = WORKLOADS[args.workload]
         g0 = make()
         n, rp, col = g0.n, g0.row_ptr, g0.col
         src_h = gen.sources(g0, S, seed=7)
-    bfs_only = args.workload == "rmat27"
-    for _ in range(args.warmup):
-        cpu_baseline(n, rp, col, src_h, min_seconds=0.0, max_units=1, bfs_only=bfs_only)
+    import oracle
+
+    cores = host_cores()
+    deg = np.diff(rp).astype(np.int64)
+    big = col.shape[0] > 1_000_000_000
+
+    def unit(k):
+        """One bounded step: on the whole input CSR, one PageRank iteration
+        on every core (OpenMP), plus, below 10^9 arcs, BFS from `cores`
+        sources at once (one per thread)."""
+        te = 0
+        if not big:
+            srcs = [src_h[(k * cores + i) % len(src_h)] for i in range(cores)]
+            te += oracle_bfs_teps(n, rp, col, deg, srcs, cores)
+        oracle.pagerank(n, rp, col, 0.85, 1, threads=cores)
+        return te + col.shape[0]
+
+    for k in range(args.warmup):
+        unit(k)
     t0 = time.time()
-    vals = []
-    for _ in range(args.steps):
-        vals.append(cpu_baseline(n, rp, col, src_h, min_seconds=0.0, max_units=1, bfs_only=bfs_only))
+    te = sum(unit(args.warmup + k) for k in range(args.steps))
     el = time.time() - t0
-    v = float(np.mean([x["value"] for x in vals]))
-    sample = "per step: 1 BFS source" + ("" if bfs_only else " + 1 PageRank iteration") + " of the same graph"
-    out = {"impl": "reference", "metric": "GTEPS (BFS 16 sources + PageRank 20 iterations, Log(Graph) "
-                                          "compressed, full step incl. encode)",
+    v = te / el / 1e9
+    sample = ("per step, on the input CSR (no encode): " + ("" if big else f"BFS from {cores} sources at once, one "
+              "per thread, + ") + f"1 PageRank iteration on {cores} OpenMP threads")
+    out = {"impl": "reference", "metric": METRIC_LG,
            "value": v, "unit": "GTEPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64 ranks / u32 depths", "data": "synthetic (seeded generator)",
            "config": {"workload": desc, "n": n, "arcs": int(col.shape[0]), "bfs_sources": S, "pr_iters": T,
-                      "parallelism": "host cores"},
-           "cpu_baseline": {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": sample},
+                      "step": sample, "parallelism": f"host cores x{cores}"},
+           "cpu_baseline": {"value": v, "unit": "GTEPS", "cores": cores, "kind": "oracle", "sample": sample},
            "e2e": {"value": v, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     return out, rank
 
@@ -1081,6 +1281,8 @@ def main():
     ap.add_argument("--impl", choices=["lg", "reference"], default="lg")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="community")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="rmat27: skip the community 2^24 (local-gap IDs, DM relabel) section of detail")
     ap.add_argument("--profile", choices=["lg", "csr32", "both"], default=None,
                     help="run one untimed pass of the hot path (for ncu) and exit")
     ap.add_argument("--pr-iters", type=int, default=None, help="PageRank iterations in --profile mode")

@@ -217,7 +217,10 @@ lg_status lg_sssp(const lg_graph *g, uint32_t source, uint64_t delta, uint64_t *
  *   personalize_source  host pointer to one u32 original ID s, or NULL for global
  *   ranks               device, n floats indexed by original ID
  * Asynchronous: returns once the work is enqueued (argument errors return
- * before any GPU work).
+ * before any GPU work).  Exception: a personalized call on a relabeled graph
+ * first reads the source's stored label back from the device, which waits for
+ * `stream`; such a call cannot be captured into a CUDA graph.  iters = 0
+ * writes r_0.
  */
 lg_status lg_pagerank(const lg_graph *g, float damping, uint32_t iters,
                       const uint32_t *personalize_source, float *ranks, void *stream);
@@ -233,9 +236,14 @@ lg_status lg_pagerank(const lg_graph *g, float damping, uint32_t iters,
  * the library, until the process exits) and calls no allocator.
  *   Limit: graphs of at most 1,048,576 vertices (and at most 262,144 schedule
  *   items for vertices split by the heavy-vertex schedule); larger graphs give
- *   LG_ERANGE with a message naming both limits.  iters must be >= 1.
+ *   LG_ERANGE with a message naming both limits.  iters = 0 writes r_0, as
+ *   lg_pagerank does, and touches no scratch.
  *   The first call on each device looks the array's device address up once
- *   (with that device current); make that first call before any stream capture.
+ *   (with that device current); make that first call before any stream
+ *   capture.  If the lookup fails, the call returns LG_ECUDA and
+ *   lg_last_error() says so (and names the capture when one is in progress).
+ *   A personalized call on a relabeled graph waits for `stream` (it reads the
+ *   source's stored label back from the device, as lg_pagerank does).
  *   All calls in the process share the one array and it keeps the last call's
  *   contents: calls whose GPU work overlaps (other streams, other threads) race
  *   and must be ordered by the caller.  Every scratch element is written before
@@ -507,6 +515,18 @@ lg_status lg_server_engine_time(lg_server *s, uint32_t graph, uint32_t kind, uin
 /* lg_server_destroy -- stop the engines (work in flight finishes, waiting
    requests are dropped), free the arenas and every undelivered result.  NULL-safe. */
 void lg_server_destroy(lg_server *s);
+
+/* lg_probe_gather -- a measurement aid with no counterpart in the paper: the
+   contribution gathers of a pull sweep (Section 7.1.2, PageRank reads
+   r[u] / d_u at every arc's u) without the decode, to give the rate at which
+   this GPU serves scattered 4-byte reads.  Thread i reads idx[i] (device,
+   count u32, each < table_len; a coalesced stream) and gathers table[idx[i]]
+   (device, table_len floats) with the pull kernels' load and L2 policy.
+   out (device) receives one partial sum per thread: it must hold
+   min(count, 311,296) floats.  Indices are not checked against table_len:
+   the caller guarantees them.  Asynchronous on `stream`. */
+lg_status lg_probe_gather(const uint32_t *idx, uint64_t count, const float *table, uint64_t table_len,
+                          float *out, void *stream);
 
 /* lg_kernel_launches -- number of CUDA kernels this library has launched in
    this process so far (all threads, all devices).  For instrumentation: the

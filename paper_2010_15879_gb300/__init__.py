@@ -30,9 +30,10 @@ from ._build import LIB, build, is_stale
 __all__ = [
     "LG_ID_GLOBAL", "LG_ID_LOCAL", "LG_ID_LOCAL_GAP", "LG_ID_CSR32", "LG_OFF_PACKED", "LG_OFF_EF",
     "LG_RELABEL_NONE", "LG_RELABEL_DM", "LG_RELABEL_GREEDY",
-    "LgError", "LogGraph", "build", "load", "lg_encode", "lg_stats_get", "lg_arrays_get", "lg_neighbors",
+    "LgError", "LogGraph", "build", "load", "lg_encode", "lg_stats_get", "lg_arrays_get", "lg_arrays_device",
+    "lg_neighbors",
     "lg_bfs", "lg_sssp", "lg_pagerank", "lg_pagerank_noalloc", "lg_free", "lg_last_error", "lg_kernel_launches",
-    "lg_decode", "lg_free_async", "lg_pool_trim", "lg_pool_usage",
+    "lg_decode", "lg_free_async", "lg_pool_trim", "lg_pool_usage", "lg_probe_gather",
     "LgBatch", "lg_batch_create", "lg_batch_run", "lg_batch_status", "lg_batch_info_get", "lg_batch_free",
     "LG_BATCH_FLAG_DROP_MEMBER",
     "LG_REQ_NEIGHBORS", "LG_REQ_BFS", "LG_REQ_PPR", "LgServer", "lg_server_create", "lg_server_submit",
@@ -152,6 +153,8 @@ def load(auto_build: bool = False):
         h.lg_pool_usage.restype = ctypes.c_int
         h.lg_free.restype = None
         h.lg_last_error.restype = ctypes.c_char_p
+        h.lg_probe_gather.argtypes = [_vp, _u64, _vp, _u64, _vp, _vp]
+        h.lg_probe_gather.restype = _i32
         h.lg_kernel_launches.argtypes = []
         h.lg_kernel_launches.restype = _u64
         h.lg_batch_create.argtypes = [_vp, _vp, _vp, _u32, _u64, _u64, ctypes.POINTER(_BatchOpts), _vp,
@@ -187,6 +190,23 @@ def lg_last_error() -> str:
 def lg_kernel_launches() -> int:
     """Kernels launched by liblg.so in this process so far."""
     return int(load().lg_kernel_launches())
+
+
+PROBE_THREADS = 152 * 8 * 256  # threads of one lg_probe_gather launch (at most)
+
+
+def lg_probe_gather(idx: torch.Tensor, table: torch.Tensor, out: Optional[torch.Tensor] = None,
+                    stream=None) -> torch.Tensor:
+    """lg_probe_gather: table[idx[i]] gathered for every i (idx int32 holding
+    uint32 values < table.numel(), table float32, both on the device); returns
+    the per-thread partial sums."""
+    if idx.dtype != torch.int32 or table.dtype != torch.float32 or not (idx.is_cuda and table.is_cuda):
+        raise TypeError("lg_probe_gather: idx must be int32 and table float32, on the device")
+    if out is None:
+        out = torch.empty(max(1, min(idx.numel(), PROBE_THREADS)), dtype=torch.float32, device=idx.device)
+    _check(load().lg_probe_gather(idx.data_ptr(), idx.numel(), table.data_ptr(), table.numel(), out.data_ptr(),
+                                  _stream(stream)), "lg_probe_gather")
+    return out
 
 
 def lg_pool_trim(device: int = 0, keep_bytes: int = 0) -> None:
@@ -348,6 +368,26 @@ def lg_arrays_get(g: LogGraph) -> dict:
     return out
 
 
+def lg_arrays_device(g: LogGraph) -> dict:
+    """Device views of the encoded arrays, without copies: int64 tensors over
+    the uint64 word streams (with padding and guard words) and int32 tensors
+    over the permutation if relabeled.  The memory belongs to the library: read
+    only, valid until g is freed."""
+    a = _Arrays()
+    _check(load().lg_arrays_get(g.handle, ctypes.byref(a)), "lg_arrays_get")
+    n = lg_stats_get(g)["n"]
+    out = {}
+    for name in ("A", "O", "ef_low", "ef_high", "ef_samples"):
+        ptr, cnt = getattr(a, name), getattr(a, "words_" + name)
+        out[name] = (torch.as_tensor(_DevView(ptr, cnt, "<i8"), device="cuda") if ptr and cnt
+                     else torch.zeros(0, dtype=torch.int64, device="cuda"))
+    for name in ("perm", "inv_perm"):
+        ptr = getattr(a, name)
+        out[name] = (torch.as_tensor(_DevView(ptr, n, "<i4"), device="cuda") if ptr
+                     else torch.zeros(0, dtype=torch.int32, device="cuda"))
+    return out
+
+
 @_on_stream
 def lg_decode(g: LogGraph, with_weights: bool = False, stream=None):
     """lg_decode: the whole graph as a CSR in stored order: (row_ptr int64[n+1],
@@ -417,6 +457,14 @@ def lg_pagerank_noalloc(g: LogGraph, damping: float, iters: int, out: torch.Tens
     """lg_pagerank_noalloc: PageRank into ``out`` (n float32, on the device) for
     callers that cannot allocate device memory -- the library uses a fixed
     internal scratch array instead (graphs up to 2^20 vertices)."""
+    n = lg_stats_get(g)["n"]
+    if not isinstance(out, torch.Tensor) or not out.is_cuda or out.dtype != torch.float32:
+        raise TypeError("lg_pagerank_noalloc: out must be a float32 CUDA tensor")
+    if out.numel() < n or not out.is_contiguous():
+        raise ValueError(f"lg_pagerank_noalloc: out must be contiguous with at least n = {n} elements")
+    dev = torch.cuda.current_device() if stream is None else stream.device.index
+    if out.device.index != dev:
+        raise ValueError(f"lg_pagerank_noalloc: out is on cuda:{out.device.index}, the call runs on cuda:{dev}")
     ps = None if personalize is None else ctypes.byref(_u32(personalize))
     _check(load().lg_pagerank_noalloc(g.handle, damping, iters, ps, out.data_ptr(), _stream(stream)),
            "lg_pagerank_noalloc")

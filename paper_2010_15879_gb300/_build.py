@@ -31,6 +31,7 @@ SOURCES = [
     "lg_batch.cu",
     "lg_serve.cu",
     "lg_sssp.cu",
+    "lg_probe.cu",
 ]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]

@@ -370,6 +370,23 @@ __global__ void k_pr_fill0(float* ranks, uint64_t n, float r0, int64_t personal_
     ranks[v] = personal_orig < 0 ? r0 : ((int64_t)v == personal_orig ? 1.0f : 0.0f);
 }
 
+uint32_t hot_rows(const lg_graph* g, uint32_t elem_bytes) {
+  const uint64_t all = g->n < 0xffffffffull ? g->n : 0xffffffffull;
+  if (g->relabel != 1 || elem_bytes == 0) return (uint32_t)all;
+  static const uint64_t bytes = [] {
+    const char* e = getenv("LG_HOT_BYTES");
+    return (e && *e) ? (uint64_t)strtoull(e, nullptr, 10) : (64ull << 20);
+  }();
+  const uint64_t rows = bytes / elem_bytes;
+  return (uint32_t)(rows < all ? rows : all);
+}
+
+cudaError_t pr_fill0(float* ranks, uint64_t n, int64_t personal_orig, cudaStream_t st) {
+  k_pr_fill0<<<grid_for(n, 256, 152 * 32), 256, 0, st>>>(ranks, n, 1.0f / (float)n, personal_orig);
+  count_launch();
+  return cudaGetLastError();
+}
+
 }  // namespace lg
 
 using namespace lg;
@@ -409,20 +426,41 @@ extern "C" lg_status lg_decode(const lg_graph* g, uint64_t* row_ptr, uint32_t* c
     LG_TRY(cudaMemsetAsync(row_ptr, 0, sizeof(uint64_t), st));
     return LG_OK;
   }
-  Tmp t_deg(st), t_stmp(st);
-  LG_TRY(t_deg.alloc(n * sizeof(uint64_t)));
-  LG_TRY(t_stmp.alloc(scan_tmp_words(n) * sizeof(uint64_t)));
   const GView v = make_view(g);
   const TravOps* ops = trav_ops((int)g->id_mode, (int)g->off_mode);
   DecArgs a;
   memset(&a, 0, sizeof(a));
-  a.degrees = t_deg.as<uint64_t>();
   a.row_ptr = row_ptr;
   a.ids = col;
   a.weights = weights;
-  LG_TRY(ops->dec_degrees(v, a, st));
-  LG_TRY(scan_excl_u64(t_deg.as<uint64_t>(), n, row_ptr, t_stmp.as<uint64_t>(), st));
-  if (g->arcs) LG_TRY(ops->dec_all(v, a, st));
+  if (g->id_mode == ID_GLOBAL || g->id_mode == ID_CSR32) {
+    // records are in arc order: the offsets are the row offsets
+    a.row_out = row_ptr;
+    LG_TRY(ops->dec_rows(v, a, st));
+    if (g->arcs) LG_TRY(ops->dec_all(v, a, st));
+    return LG_OK;
+  }
+  // local IDs: one launch (row offsets by a single-pass look-back over the
+  // tiles, then the rows); its small state is zeroed first
+  const uint64_t ntiles = (n + LG_TILE_V - 1) / LG_TILE_V;
+  Tmp t_state(st);
+  const size_t bytes = ntiles * (sizeof(unsigned long long) + sizeof(uint32_t)) + 16;
+  LG_TRY(t_state.alloc(bytes));
+  LG_TRY(cudaMemsetAsync(t_state.p, 0, bytes, st));
+  a.tile_status = t_state.as<unsigned long long>();
+  a.tile_ready = reinterpret_cast<uint32_t*>(a.tile_status + ntiles);
+  a.ticket = a.tile_ready + ntiles;
+  a.err = reinterpret_cast<int*>(a.ticket + 1);
+  a.row_out = row_ptr;
+  a.wait_ns = 200ull * 1000 * 1000;
+  LG_TRY(ops->dec_all(v, a, st));
+  int err = 0;
+  LG_TRY(cudaMemcpyAsync(&err, a.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  LG_TRY(cudaStreamSynchronize(st));
+  if (err) {
+    set_errf("lg_decode: a wait between the decode's blocks ran out (row offsets incomplete)");
+    return LG_ETIMEOUT;
+  }
   return LG_OK;
 }
 
@@ -809,6 +847,7 @@ extern "C" lg_status lg_bfs(const lg_graph* g, const uint32_t* sources, uint32_t
     a.counters = counters;
     a.hacc = t_hacc.p;
     a.err = d_err;
+    a.hot = hot_rows(g, mb);
     for (uint32_t level = 0; nq > 0; level++) {
       LG_TRY(cudaMemsetAsync(counters, 0, 8, st));
       a.front_in = cur; a.front_out = nxt; a.level = level;
@@ -853,9 +892,7 @@ extern "C" lg_status lg_pagerank(const lg_graph* g, float damping, uint32_t iter
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const uint64_t n = g->n;
   if (iters == 0) {
-    k_pr_fill0<<<grid_for(n, 256, 152 * 32), 256, 0, st>>>(ranks, n, 1.0f / (float)n, personal_orig);
-    count_launch();
-    LG_TRY(cudaGetLastError());
+    LG_TRY(pr_fill0(ranks, n, personal_orig, st));
     return LG_OK;
   }
   if (personal_orig >= 0) {
@@ -883,6 +920,7 @@ extern "C" lg_status lg_pagerank(const lg_graph* g, float damping, uint32_t iter
   a.part = tpart.as<float>();
   a.ranks_out = ranks;
   a.contrib_out = ca.as<float>();
+  a.hot = hot_rows(g, sizeof(float));
   LG_TRY(ops->pr_init(v, a, st));
   float* cur = ca.as<float>();
   float* nxt = cb.as<float>();

@@ -153,10 +153,21 @@ __device__ __forceinline__ float4 ldg_gather4(const float* p, uint64_t pol) {
       : "l"(p), "l"(pol));
   return v;
 }
-__device__ __forceinline__ uint16_t ldg_gather(const uint16_t* p, uint64_t) { return __ldg(p); }
-__device__ __forceinline__ uint32_t ldg_gather(const uint32_t* p, uint64_t) { return __ldg(p); }
-__device__ __forceinline__ uint64_t ldg_gather(const uint64_t* p, uint64_t) {
-  return (uint64_t)__ldg(reinterpret_cast<const unsigned long long*>(p));
+// BFS frontier masks (2, 4 or 8 bytes per vertex), same policy argument
+__device__ __forceinline__ uint16_t ldg_gather(const uint16_t* p, uint64_t pol) {
+  uint16_t v;
+  asm("ld.global.nc.L2::cache_hint.u16 %0, [%1], %2;" : "=h"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ uint32_t ldg_gather(const uint32_t* p, uint64_t pol) {
+  uint32_t v;
+  asm("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ uint64_t ldg_gather(const uint64_t* p, uint64_t pol) {
+  uint64_t v;
+  asm("ld.global.nc.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol));
+  return v;
 }
 
 // ---------------------------------------------------------------------------

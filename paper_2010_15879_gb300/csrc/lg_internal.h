@@ -80,8 +80,10 @@ cudaError_t radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, u
                            uint64_t n, uint32_t key_bits, void* tmp, cudaStream_t st);
 // Sort each row [off[i], off[i+1]) of keys ascending, moving vals (nullable) along.
 // Rows of <= 32 keys are skipped when `small_done` (their producer sorted them).
+// Every key is below 2^key_bits.
 cudaError_t segmented_sort(uint32_t* keys, uint32_t* vals, const uint64_t* off, uint64_t rows,
-                           uint64_t total, uint64_t max_row, cudaStream_t st, bool small_done = false);
+                           uint64_t total, uint64_t max_row, cudaStream_t st, bool small_done = false,
+                           uint32_t key_bits = 32);
 
 // ------------------------------------------------------------------ encoder
 cudaError_t enc_validate(const uint64_t* rp, const uint32_t* col, const uint32_t* w, uint64_t n,
@@ -127,6 +129,8 @@ struct PrArgs {
   int64_t personal;          // stored label of the personalization source, -1 = global
   float r0_all;              // 1/n (initial rank, global)
   float* part;               // per heavy item partial sums (split vertices)
+  uint32_t hot;              // gathers of contributions u < hot keep their L2 lines (evict-last), the
+                             // others are evict-first (DM order puts the most gathered vertices first)
 };
 
 struct BfsArgs {
@@ -147,6 +151,7 @@ struct BfsArgs {
   uint32_t* counters;        // [0] next queue length, [1] new (vertex, source) pairs
   void* hacc;                // per split vertex: OR of its items' frontier masks
   int* err;
+  uint32_t hot;              // pull gathers of masks u < hot are evict-last in L2, the others evict-first
 };
 
 // Personalized PageRank for up to PPR_K requests at once (the serving
@@ -176,11 +181,21 @@ struct NbrArgs {
 };
 
 // whole-graph decode into a CSR in stored order (lg_decode)
+// Global-ID and CSR-32 graphs hold their records in arc order, so their
+// offsets are the row offsets: the row pass writes row_out[0..n] directly and
+// the decode pass maps record j to col[j].  Local-ID graphs: one launch
+// writes both (row offsets by a look-back over the tiles).
 struct DecArgs {
-  uint64_t* degrees;         // n (degree pass output)
-  const uint64_t* row_ptr;   // n+1 arc offsets (decode pass input)
+  uint64_t* row_out;         // n+1 row offsets, written by the decode
+  const uint64_t* row_ptr;   // the same array, read back by the heavy items (local modes)
   uint32_t* ids;             // arcs
   uint32_t* weights;         // arcs, or null
+  // local modes: single-pass row offsets (zeroed before the launch)
+  unsigned long long* tile_status;  // per tile: 0, aggregate (flag 1) or inclusive prefix (flag 2) in bits 62-63
+  uint32_t* tile_ready;      // per tile: 1 once its row offsets are written
+  uint32_t* ticket;          // next block to start (blocks take tiles in start order)
+  int* err;                  // DERR_INTERNAL if a wait for another block ran out
+  uint64_t wait_ns;          // limit of each such wait
 };
 
 struct TravOps {
@@ -195,7 +210,7 @@ struct TravOps {
   cudaError_t (*plan_carry)(const GView&, const PlanArgs&, cudaStream_t);
   cudaError_t (*ppr_pull)(const GView&, const PprArgs&, cudaStream_t);
   cudaError_t (*ppr_join)(const GView&, float* cin, uint32_t slot, uint32_t src, cudaStream_t);
-  cudaError_t (*dec_degrees)(const GView&, const DecArgs&, cudaStream_t);
+  cudaError_t (*dec_rows)(const GView&, const DecArgs&, cudaStream_t);
   cudaError_t (*dec_all)(const GView&, const DecArgs&, cudaStream_t);
 };
 
@@ -214,6 +229,15 @@ const TravOps* trav_ops_local_ef();
 const TravOps* trav_ops_gap_packed();
 const TravOps* trav_ops_gap_ef();
 const TravOps* trav_ops_csr32();
+
+// Stored labels below which pull gathers of an array of `elem_bytes` per
+// vertex keep their L2 lines: on a DM-relabeled graph (hubs first) the first
+// LG_HOT_BYTES (default 64 MiB) of the array, else every vertex.
+uint32_t hot_rows(const lg_graph* g, uint32_t elem_bytes);
+
+// ranks = r_0 (1/n, or the indicator of personal_orig >= 0): PageRank after zero
+// iterations (lg_api.cu)
+cudaError_t pr_fill0(float* ranks, uint64_t n, int64_t personal_orig, cudaStream_t st);
 
 // BFS helpers (lg_api.cu); vmajor: depth[v * S + s] instead of depth[s * n + v]
 cudaError_t bfs_seed(void* vis, void* front, uint32_t* depth, uint64_t n, const uint32_t* sources_stored,

@@ -433,6 +433,7 @@ struct BfsEngine : Engine {
     a.counters = counters;
     a.hacc = hacc;
     a.err = err;
+    a.hot = hot_rows(g, 8);
     if ((uint64_t)nq > n / 64) {
       ECHK(ops->bfs_pull(view, a, 8, st));
       ECHK(bfs_finish_multi(view, a, 8, st));

@@ -35,47 +35,74 @@ __global__ void __launch_bounds__(RS_NT) k_rs_hist(const K* __restrict__ keys, u
   hist[(uint64_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];  // digit-major
 }
 
+// Scatter of one tile of RS_TILE keys: the tile is first ranked stably by digit
+// into shared memory (per round of RS_NT keys: a match among the warp's lanes,
+// the counts of the warps before, the tile's keys of this digit in earlier
+// rounds), then written out in that order, so the keys of one digit -- about
+// RS_TILE / 256 of them -- go to consecutive addresses (coalesced writes).
+template <typename K>
+struct RsSmem {
+  K keys[RS_TILE];
+  uint32_t vals[RS_TILE];
+  uint32_t wcnt[RS_NW][256];
+  uint32_t loc[256];        // first position of each digit in the tile
+  uint32_t seen[256];       // keys of each digit placed so far
+  uint64_t glob[256];       // first global position of each digit for this tile
+  uint32_t red[RS_NW];
+};
+
 template <typename K>
 __global__ void __launch_bounds__(RS_NT) k_rs_scatter(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
                                                       K* __restrict__ kout, uint32_t* __restrict__ vout, uint64_t n,
                                                       uint32_t shift, const uint64_t* __restrict__ off,
-                                                      uint64_t ntiles) {
-  __shared__ uint32_t wcnt[RS_NW][256];
-  __shared__ uint64_t run[256];
+                                                      const uint32_t* __restrict__ hist, uint64_t ntiles) {
+  extern __shared__ __align__(16) unsigned char rs_raw[];
+  RsSmem<K>& sm = *reinterpret_cast<RsSmem<K>*>(rs_raw);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  run[threadIdx.x] = off[(uint64_t)threadIdx.x * ntiles + blockIdx.x];
+  const uint64_t cell = (uint64_t)threadIdx.x * ntiles + blockIdx.x;
+  {
+    uint32_t total;
+    sm.loc[threadIdx.x] = block_excl_scan<uint32_t, RS_NT>(hist[cell], total, sm.red);
+    sm.glob[threadIdx.x] = off[cell];
+    sm.seen[threadIdx.x] = 0;
+  }
   const uint64_t base = (uint64_t)blockIdx.x * RS_TILE;
+  const uint32_t tn = (uint32_t)min((uint64_t)RS_TILE, n - base);
   for (int r = 0; r < RS_ROUNDS; r++) {
-    for (int k = 0; k < RS_NW; k++) wcnt[k][threadIdx.x] = 0;
+    for (int k = 0; k < RS_NW; k++) sm.wcnt[k][threadIdx.x] = 0;
     __syncthreads();
-    const uint64_t i = base + (uint64_t)r * RS_NT + threadIdx.x;
-    const bool ok = i < n;
-    K key = ok ? kin[i] : K(0);
-    const uint32_t val = (ok && vin) ? vin[i] : 0u;
+    const uint32_t li = (uint32_t)r * RS_NT + threadIdx.x;
+    const bool ok = li < tn;
+    const K key = ok ? kin[base + li] : K(0);
+    const uint32_t val = (ok && vin) ? vin[base + li] : 0u;
     const uint32_t dig = ok ? ((uint32_t)(key >> shift) & 255u) : 256u;
     const uint32_t peers = __match_any_sync(LG_FULL_MASK, dig);
     const uint32_t rank = __popc(peers & lanemask_lt());
-    if (ok && rank == 0) wcnt[w][dig] = __popc(peers);
+    if (ok && rank == 0) sm.wcnt[w][dig] = __popc(peers);
     __syncthreads();
-    // thread t owns digit t: exclusive prefix over warps, then advance the run
-    {
-      uint32_t acc = 0;
-      for (int k = 0; k < RS_NW; k++) {
-        const uint32_t c = wcnt[k][threadIdx.x];
-        wcnt[k][threadIdx.x] = acc;
-        acc += c;
-      }
-      // read run before updating: positions use the old value
-      __syncthreads();
-      if (ok) {
-        const uint64_t pos = run[dig] + wcnt[w][dig] + rank;
-        kout[pos] = key;
-        if (vin) vout[pos] = val;
-      }
-      __syncthreads();
-      run[threadIdx.x] += acc;
+    // thread t owns digit t: exclusive prefix over the warps of this round
+    uint32_t acc = 0;
+    for (int k = 0; k < RS_NW; k++) {
+      const uint32_t c = sm.wcnt[k][threadIdx.x];
+      sm.wcnt[k][threadIdx.x] = acc;
+      acc += c;
     }
     __syncthreads();
+    if (ok) {
+      const uint32_t pos = sm.loc[dig] + sm.seen[dig] + sm.wcnt[w][dig] + rank;
+      sm.keys[pos] = key;
+      sm.vals[pos] = val;
+    }
+    __syncthreads();
+    sm.seen[threadIdx.x] += acc;
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < tn; i += RS_NT) {
+    const K key = sm.keys[i];
+    const uint32_t dig = (uint32_t)(key >> shift) & 255u;
+    const uint64_t pos = sm.glob[dig] + (i - sm.loc[dig]);
+    kout[pos] = key;
+    if (vin) vout[pos] = sm.vals[i];
   }
   (void)lane;
 }
@@ -98,13 +125,18 @@ static cudaError_t radix_impl(K* keys, uint32_t* vals, K* keys_alt, uint32_t* va
   K* ka = keys; K* kb = keys_alt;
   uint32_t* va = vals; uint32_t* vb = vals_alt;
   const uint32_t passes = (key_bits + 7) / 8;
+  {
+    const cudaError_t e = cudaFuncSetAttribute(k_rs_scatter<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)sizeof(RsSmem<K>));
+    if (e != cudaSuccess) return e;
+  }
   for (uint32_t p = 0; p < passes; p++) {
     const uint32_t shift = 8 * p;
     k_rs_hist<K><<<(unsigned)ntiles, RS_NT, 0, st>>>(ka, n, shift, hist, ntiles);
     count_launch();
     cudaError_t e = scan_excl_u32(hist, cells, off, stmp, st);
     if (e != cudaSuccess) return e;
-    k_rs_scatter<K><<<(unsigned)ntiles, RS_NT, 0, st>>>(ka, va, kb, vb, n, shift, off, ntiles);
+    k_rs_scatter<K><<<(unsigned)ntiles, RS_NT, sizeof(RsSmem<K>), st>>>(ka, va, kb, vb, n, shift, off, hist, ntiles);
     count_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -446,24 +478,25 @@ __global__ void __launch_bounds__(256) k_seg_fill(const uint64_t* __restrict__ o
 // large rows: gather (row rank, key) composite keys, radix sort, scatter back
 __global__ void k_seg_big_gather(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
                                  const uint64_t* __restrict__ off, const uint32_t* __restrict__ big,
-                                 const uint64_t* __restrict__ boff, uint32_t nbig, uint64_t* __restrict__ ck,
-                                 uint32_t* __restrict__ cv) {
+                                 const uint64_t* __restrict__ boff, uint32_t nbig, uint32_t key_bits,
+                                 uint64_t* __restrict__ ck, uint32_t* __restrict__ cv) {
   for (uint32_t b = blockIdx.x; b < nbig; b += gridDim.x) {
     const uint64_t lo = off[big[b]], d = off[big[b] + 1] - lo, o = boff[b];
     for (uint64_t i = threadIdx.x; i < d; i += blockDim.x) {
-      ck[o + i] = ((uint64_t)b << 32) | keys[lo + i];
+      ck[o + i] = ((uint64_t)b << key_bits) | keys[lo + i];
       cv[o + i] = vals ? vals[lo + i] : 0u;
     }
   }
 }
 __global__ void k_seg_big_scatter(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                                   const uint64_t* __restrict__ off, const uint32_t* __restrict__ big,
-                                  const uint64_t* __restrict__ boff, uint32_t nbig, const uint64_t* __restrict__ ck,
-                                  const uint32_t* __restrict__ cv) {
+                                  const uint64_t* __restrict__ boff, uint32_t nbig, uint32_t key_bits,
+                                  const uint64_t* __restrict__ ck, const uint32_t* __restrict__ cv) {
+  const uint64_t kmask = key_bits >= 64 ? ~0ull : (1ull << key_bits) - 1ull;
   for (uint32_t b = blockIdx.x; b < nbig; b += gridDim.x) {
     const uint64_t lo = off[big[b]], d = off[big[b] + 1] - lo, o = boff[b];
     for (uint64_t i = threadIdx.x; i < d; i += blockDim.x) {
-      keys[lo + i] = (uint32_t)ck[o + i];
+      keys[lo + i] = (uint32_t)(ck[o + i] & kmask);
       if (vals) vals[lo + i] = cv[o + i];
     }
   }
@@ -475,7 +508,7 @@ __global__ void k_seg_big_sizes(const uint64_t* __restrict__ off, const uint32_t
 }
 
 static cudaError_t seg_sort_big(uint32_t* keys, uint32_t* vals, const uint64_t* off, const uint32_t* big,
-                                uint32_t nbig, cudaStream_t st) {
+                                uint32_t nbig, uint32_t key_bits, cudaStream_t st) {
   uint64_t *sizes = nullptr, *boff = nullptr, *ck = nullptr, *ck2 = nullptr, *stmp = nullptr;
   uint32_t *cv = nullptr, *cv2 = nullptr;
   void* rtmp = nullptr;
@@ -496,12 +529,13 @@ static cudaError_t seg_sort_big(uint32_t* keys, uint32_t* vals, const uint64_t* 
   if (e == cudaSuccess) e = lg::pool_alloc((void**)&cv2, nb_total * sizeof(uint32_t), st);
   if (e == cudaSuccess) e = lg::pool_alloc(&rtmp, radix_tmp_bytes(nb_total), st);
   if (e == cudaSuccess) {
-    k_seg_big_gather<<<grid_for(nbig, 1, 4096), 256, 0, st>>>(keys, vals, off, big, boff, nbig, ck, cv);
+    k_seg_big_gather<<<grid_for(nbig, 1, 4096), 256, 0, st>>>(keys, vals, off, big, boff, nbig, key_bits, ck, cv);
     count_launch();
-    e = radix_sort_u64(ck, cv, ck2, cv2, nb_total, 32 + host_bits(nbig), rtmp, st);
+    e = radix_sort_u64(ck, cv, ck2, cv2, nb_total, key_bits + host_bits(nbig), rtmp, st);
   }
   if (e == cudaSuccess) {
-    k_seg_big_scatter<<<grid_for(nbig, 1, 4096), 256, 0, st>>>(keys, vals, off, big, boff, nbig, ck, cv);
+    k_seg_big_scatter<<<grid_for(nbig, 1, 4096), 256, 0, st>>>(keys, vals, off, big, boff, nbig, key_bits, ck,
+                                                                cv);
     count_launch();
     e = cudaGetLastError();
   }
@@ -552,7 +586,7 @@ static cudaError_t seg_small_launch(uint32_t* keys, uint32_t* vals, const uint64
 }
 
 cudaError_t segmented_sort(uint32_t* keys, uint32_t* vals, const uint64_t* off, uint64_t rows, uint64_t total,
-                           uint64_t max_row, cudaStream_t st, bool small_done) {
+                           uint64_t max_row, cudaStream_t st, bool small_done, uint32_t key_bits) {
   if (rows == 0 || total == 0 || max_row <= 1) return cudaSuccess;
   cudaError_t e;
   if (!small_done && (e = seg_small_launch(keys, vals, off, rows, st)) != cudaSuccess) return e;
@@ -579,7 +613,7 @@ cudaError_t segmented_sort(uint32_t* keys, uint32_t* vals, const uint64_t* off, 
   for (int k = 1; k <= 7 && e == cudaSuccess; k++)
     if (cnt[k]) e = vals ? seg_blk_class<true>(k, keys, vals, off, list + base[k], cnt[k], st)
                          : seg_blk_class<false>(k, keys, vals, off, list + base[k], cnt[k], st);
-  if (e == cudaSuccess && cnt[9]) e = seg_sort_big(keys, vals, off, list + base[9], cnt[9], st);
+  if (e == cudaSuccess && cnt[9]) e = seg_sort_big(keys, vals, off, list + base[9], cnt[9], key_bits, st);
   cudaFreeAsync(list, st);
   cudaFreeAsync(meta, st);
   return e == cudaSuccess ? cudaGetLastError() : e;
@@ -679,7 +713,21 @@ __global__ void __launch_bounds__(256) k_dm_rows(const uint64_t* __restrict__ rp
       const uint64_t lq = __shfl_sync(LG_FULL_MASK, lo, q);
       const uint64_t oq = __shfl_sync(LG_FULL_MASK, o, q);
       const uint32_t dq = __shfl_sync(LG_FULL_MASK, d, q);
-      for (uint32_t k = lane; k < dq; k += 32) {
+      // four arcs per lane in flight: their col loads, then their perm gathers
+      uint32_t k = lane;
+      for (; k + 96 < dq; k += 128) {
+        uint32_t cc[4], pv[4];
+#pragma unroll
+        for (int z = 0; z < 4; z++) cc[z] = ldg_hint(col + lq + k + 32 * z, pstream);
+#pragma unroll
+        for (int z = 0; z < 4; z++) pv[z] = ldg_hint(perm + cc[z], pkeep);
+#pragma unroll
+        for (int z = 0; z < 4; z++) {
+          __stcs(ncol + oq + k + 32 * z, pv[z]);
+          if (VALS) __stcs(nw + oq + k + 32 * z, ldg_hint(w + lq + k + 32 * z, pstream));
+        }
+      }
+      for (; k < dq; k += 32) {
         const uint32_t cc = ldg_hint(col + lq + k, pstream);
         __stcs(ncol + oq + k, ldg_hint(perm + cc, pkeep));
         if (VALS) __stcs(nw + oq + k, ldg_hint(w + lq + k, pstream));
@@ -798,7 +846,7 @@ cudaError_t enc_dm_relabel(const uint64_t* rp, const uint32_t* col, const uint32
     if (e == cudaSuccess) e = cudaGetLastError();
   }
   // rows of <= 32 arcs left k_dm_rows sorted
-  if (e == cudaSuccess) e = segmented_sort(ncol, w ? nw : nullptr, nrp, n, arcs, max_deg, st, true);
+  if (e == cudaSuccess) e = segmented_sort(ncol, w ? nw : nullptr, nrp, n, arcs, max_deg, st, true, host_bits(n - 1));
   cudaFreeAsync(keys, st); cudaFreeAsync(k2, st); cudaFreeAsync(v2, st); cudaFreeAsync(newdeg, st);
   cudaFreeAsync(stmp, st); cudaFreeAsync(rtmp, st);
   return e;

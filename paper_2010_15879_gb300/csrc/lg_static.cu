@@ -85,14 +85,37 @@ extern "C" lg_status lg_pagerank_noalloc(const lg_graph* g, float damping, uint3
   lg_status status = LG_OK;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   float* scratch = nullptr;
-  cudaError_t e = scratch_on_device(g->device, &scratch);
-  if (e == cudaSuccess && personal >= 0 && g->perm) {
+  cudaError_t e = cudaSuccess;
+  if (iters == 0) {
+    // PageRank after zero iterations is r_0 itself: no scratch is needed
+    e = pr_fill0(ranks, g->n, personal, st);
+    if (e != cudaSuccess) {
+      snprintf(g_msg, sizeof g_msg, "lg_pagerank_noalloc: %s", cudaGetErrorString(e));
+      set_error_message(g_msg);
+      status = LG_ECUDA;
+    }
+    if (prev != g->device) cudaSetDevice(prev);
+    return status;
+  }
+  e = scratch_on_device(g->device, &scratch);
+  if (e != cudaSuccess) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const bool capturing = cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+    snprintf(g_msg, sizeof g_msg,
+             "lg_pagerank_noalloc: looking up the scratch array on device %d failed (%s)%s", g->device,
+             cudaGetErrorString(e),
+             capturing ? "; the first call on a device must come before any stream capture" : "");
+    set_error_message(g_msg);
+    if (prev != g->device) cudaSetDevice(prev);
+    return LG_ECUDA;
+  }
+  if (personal >= 0 && g->perm) {
     uint32_t ps = 0;
     e = cudaMemcpyAsync(&ps, g->perm + personal, sizeof(ps), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     personal = ps;
   }
-  if (e == cudaSuccess && iters > 0) {
+  if (e == cudaSuccess) {
     // scratch layout: contributions A [n], contributions B [n], item partial sums;
     // every element is written before it is read, so nothing needs clearing
     float* ca = scratch;
@@ -107,6 +130,7 @@ extern "C" lg_status lg_pagerank_noalloc(const lg_graph* g, float damping, uint3
     a.base_all = personal < 0 ? (1.0f - damping) / (float)g->n : (1.0f - damping);
     a.r0_all = 1.0f / (float)g->n;
     a.part = part;
+    a.hot = hot_rows(g, sizeof(float));
     a.ranks_out = ranks;
     a.contrib_out = ca;
     e = ops->pr_init(v, a, st);
@@ -120,9 +144,6 @@ extern "C" lg_status lg_pagerank_noalloc(const lg_graph* g, float damping, uint3
       if (e == cudaSuccess) e = pr_finish_multi(v, a, st);
       float* tt = cur; cur = nxt; nxt = tt;
     }
-  } else if (e == cudaSuccess) {
-    set_error_message("lg_pagerank_noalloc: iters must be >= 1");
-    status = LG_EINVAL;
   }
   if (e != cudaSuccess) {
     snprintf(g_msg, sizeof g_msg, "lg_pagerank_noalloc: %s", cudaGetErrorString(e));

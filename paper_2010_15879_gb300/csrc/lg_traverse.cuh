@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(TNT, (IDM == ID_LOCAL || IDM == ID_CSR32) ? 5 
       warp_ids<IDM, HEAVY_U>(g, h.bit, h.w, base, f1, carry, id);
       float x[HEAVY_U];
 #pragma unroll
-      for (int u = 0; u < HEAVY_U; u++) x[u] = (base + 32u * u + lane < f1) ? ldg_gather(c + id[u], pkeep) : 0.f;
+      for (int u = 0; u < HEAVY_U; u++) x[u] = (base + 32u * u + lane < f1) ? ldg_gather(c + id[u], id[u] < a.hot ? pkeep : pstream) : 0.f;
 #pragma unroll
       for (int u = 0; u < HEAVY_U; u++) {  // compensated (Kahan) lane sums
         const float y = x[u] - comp;
@@ -443,12 +443,15 @@ __global__ void __launch_bounds__(TNT, (IDM == ID_LOCAL || IDM == ID_CSR32) ? 5 
       uint32_t k = 0;
       for (; k + 4 <= d; k += 4) {
         const uint32_t u0 = dec.next(), u1 = dec.next(), u2 = dec.next(), u3 = dec.next();
-        const float f0 = ldg_gather(c + u0, pkeep), f1 = ldg_gather(c + u1, pkeep);
-        const float f2 = ldg_gather(c + u2, pkeep), f3 = ldg_gather(c + u3, pkeep);
+        const float f0 = ldg_gather(c + u0, u0 < a.hot ? pkeep : pstream), f1 = ldg_gather(c + u1, u1 < a.hot ? pkeep : pstream);
+        const float f2 = ldg_gather(c + u2, u2 < a.hot ? pkeep : pstream), f3 = ldg_gather(c + u3, u3 < a.hot ? pkeep : pstream);
         s0 += f0 + f1;
         s1 += f2 + f3;
       }
-      for (; k < d; k++) s0 += ldg_gather(c + dec.next(), pkeep);
+      for (; k < d; k++) {
+        const uint32_t u = dec.next();
+        s0 += ldg_gather(c + u, u < a.hot ? pkeep : pstream);
+      }
       pr_finish(g, a, v0 + i, d, s0 + s1);
     }
     return;
@@ -484,12 +487,15 @@ __global__ void __launch_bounds__(TNT, (IDM == ID_LOCAL || IDM == ID_CSR32) ? 5 
       uint32_t k = 0;
       for (; k + 4 <= d; k += 4) {  // four gathers in flight
         const uint32_t u0 = dec.next(), u1 = dec.next(), u2 = dec.next(), u3 = dec.next();
-        const float f0 = ldg_gather(c + u0, pkeep), f1 = ldg_gather(c + u1, pkeep);
-        const float f2 = ldg_gather(c + u2, pkeep), f3 = ldg_gather(c + u3, pkeep);
+        const float f0 = ldg_gather(c + u0, u0 < a.hot ? pkeep : pstream), f1 = ldg_gather(c + u1, u1 < a.hot ? pkeep : pstream);
+        const float f2 = ldg_gather(c + u2, u2 < a.hot ? pkeep : pstream), f3 = ldg_gather(c + u3, u3 < a.hot ? pkeep : pstream);
         s0 += f0 + f1;
         s1 += f2 + f3;
       }
-      for (; k < d; k++) s0 += ldg_gather(c + dec.next(), pkeep);
+      for (; k < d; k++) {
+        const uint32_t u = dec.next();
+        s0 += ldg_gather(c + u, u < a.hot ? pkeep : pstream);
+      }
       *ps = s0 + s1;
       f = vend;
       j++;
@@ -800,7 +806,7 @@ __global__ void __launch_bounds__(TNT, IDM == ID_LOCAL_GAP ? 6 : 5) k_bfs_pull(G
       warp_ids<IDM, HEAVY_U>(g, h.bit, h.w, base, f1, carry, id);
       M x[HEAVY_U];
 #pragma unroll
-      for (int u = 0; u < HEAVY_U; u++) x[u] = (base + 32u * u + lane < f1) ? ldg_gather(fin + id[u], pkeep) : (M)0;
+      for (int u = 0; u < HEAVY_U; u++) x[u] = (base + 32u * u + lane < f1) ? ldg_gather(fin + id[u], id[u] < a.hot ? pkeep : pstream) : (M)0;
 #pragma unroll
       for (int u = 0; u < HEAVY_U; u++) acc |= x[u];
       acc = warp_or<M>(acc);
@@ -837,12 +843,15 @@ __global__ void __launch_bounds__(TNT, IDM == ID_LOCAL_GAP ? 6 : 5) k_bfs_pull(G
       uint32_t k = 0;
       for (; k + 4 <= d; k += 4) {  // early exit once every unvisited source is found
         const uint32_t u0 = dec.next(), u1 = dec.next(), u2 = dec.next(), u3 = dec.next();
-        acc |= (M)(ldg_gather(fin + u0, pkeep) | ldg_gather(fin + u1, pkeep) | ldg_gather(fin + u2, pkeep) |
-                   ldg_gather(fin + u3, pkeep));
+        acc |= (M)(ldg_gather(fin + u0, u0 < a.hot ? pkeep : pstream) | ldg_gather(fin + u1, u1 < a.hot ? pkeep : pstream) | ldg_gather(fin + u2, u2 < a.hot ? pkeep : pstream) |
+                   ldg_gather(fin + u3, u3 < a.hot ? pkeep : pstream));
         if ((M)(acc & need) == need) break;
       }
       if ((M)(acc & need) != need)
-        for (; k < d; k++) acc |= ldg_gather(fin + dec.next(), pkeep);
+        for (; k < d; k++) {
+          const uint32_t u = dec.next();
+          acc |= ldg_gather(fin + u, u < a.hot ? pkeep : pstream);
+        }
       bfs_finish<M>(g, a, v0 + i, need, acc, qbuf, &qn, &newpairs);
     }
   } else {
@@ -874,12 +883,15 @@ __global__ void __launch_bounds__(TNT, IDM == ID_LOCAL_GAP ? 6 : 5) k_bfs_pull(G
         uint32_t k = 0;
         for (; k + 4 <= d; k += 4) {
           const uint32_t u0 = dec.next(), u1 = dec.next(), u2 = dec.next(), u3 = dec.next();
-          acc |= (M)(ldg_gather(fin + u0, pkeep) | ldg_gather(fin + u1, pkeep) | ldg_gather(fin + u2, pkeep) |
-                     ldg_gather(fin + u3, pkeep));
+          acc |= (M)(ldg_gather(fin + u0, u0 < a.hot ? pkeep : pstream) | ldg_gather(fin + u1, u1 < a.hot ? pkeep : pstream) | ldg_gather(fin + u2, u2 < a.hot ? pkeep : pstream) |
+                     ldg_gather(fin + u3, u3 < a.hot ? pkeep : pstream));
           if ((M)(acc & need) == need) break;
         }
         if ((M)(acc & need) != need)
-          for (; k < d; k++) acc |= ldg_gather(fin + dec.next(), pkeep);
+          for (; k < d; k++) {
+          const uint32_t u = dec.next();
+          acc |= ldg_gather(fin + u, u < a.hot ? pkeep : pstream);
+        }
         *ps = acc;
         f = vend;
         j++;
@@ -1018,27 +1030,38 @@ __global__ void __launch_bounds__(256) k_nbr_decode(GView g, NbrArgs a) {
 }
 
 // ===========================================================================
-// Whole-graph decode (lg_decode): the degree of every vertex, then every
-// neighborhood written to its CSR row in stored order.  Tiles of TV vertices
-// decode their offsets once; each warp takes a run of the tile's light
-// vertices balanced by fields and decodes a vertex 32 fields per step, a lane
-// per field (coalesced writes; gaps prefix-summed across the warp).  Heavy
-// vertices come from the heavy schedule, a warp per item.
+// Whole-graph decode (lg_decode): every neighborhood (Section 3.7.2's access
+// applied to all vertices) written to a CSR in stored order.
+//
+// Global IDs (and CSR-32) keep their records in arc order, so record j is
+// col[j] and the offsets x_v are the row offsets: a row pass writes row_ptr
+// from the offsets (one tile decode per 512 vertices) and a flat pass maps
+// records to IDs, consecutive threads on consecutive records (coalesced
+// stream reads and coalesced writes, no vertex lookup).  Local IDs: one
+// kernel, described above k_dec_local.
+//
+// Local IDs: a degree pass and a scan give the row offsets, then tiles of TV
+// vertices decode their offsets once and split the tile's light fields into
+// rounds of DEC_C fields.  In a round every thread decodes a contiguous run of
+// fields sequentially (bit reader, one shift and mask per field, a running sum
+// for gaps), entering its first neighborhood mid-way if need be, into a
+// shared-memory stage; the stage is then written out coalesced.  A run that
+// starts inside a gap-coded neighborhood sums its gaps from 0; a segmented
+// scan over the threads' last values (absolute once the neighborhood's first
+// field has been read) supplies the missing prefix.  Heavy vertices come from
+// the heavy schedule, a warp per item, a lane per field.
 // ===========================================================================
-template <int IDM, int OFF>
-__global__ void __launch_bounds__(TNT) k_dec_degrees(GView g, DecArgs a) {
+// row pass of global-ID / CSR-32 graphs: the offsets are the row offsets
+template <int OFF>
+__global__ void __launch_bounds__(TNT) k_dec_rows(GView g, DecArgs a) {
   __shared__ uint64_t xs[TV + 1];
   __shared__ TileScratch ts;
   const uint64_t v0 = (uint64_t)blockIdx.x * TV;
   const int cnt = (int)min((uint64_t)TV, g.n - v0);
   tile_offsets<OFF>(g, v0, cnt, xs, ts);
   __syncthreads();
-  for (int i = threadIdx.x; i < cnt; i += TNT) {
-    uint64_t start;
-    uint32_t d, w;
-    vgeo<IDM>(g, xs[i], xs[i + 1], start, d, w);
-    a.degrees[v0 + i] = d;
-  }
+  for (int i = threadIdx.x; i < cnt; i += TNT) a.row_out[v0 + i] = xs[i];
+  if (v0 + (uint64_t)cnt == g.n && threadIdx.x == 0) a.row_out[g.n] = xs[cnt];
 }
 
 template <int IDM, int U>
@@ -1051,109 +1074,394 @@ __device__ __forceinline__ void dec_fields(const GView& g, const DecArgs& a, uin
 #pragma unroll
     for (int u = 0; u < U; u++) {
       const uint32_t idx = base + 32u * u + lane;
-      if (idx < f1) {
-        __stcs(a.ids + o + idx, id[u]);
-        if (a.weights) {
-          uint32_t wt = 0;
-          if (IDM == ID_GLOBAL && g.omega) wt = weight_at(g, start, idx);
-          if (IDM == ID_CSR32 && g.W32) wt = __ldg(g.W32 + (start >> 5) + idx);
-          __stcs(a.weights + o + idx, wt);
+      if (idx < f1) __stcs(a.ids + o + idx, id[u]);
+    }
+  }
+}
+
+constexpr int DEC_FLAT_U = 4;  // records per thread in flight (flat decode)
+
+// Flat decode of global-ID records (or CSR-32 IDs): thread t of the grid takes
+// records j = base + t + k * blockDim.x for k < DEC_FLAT_U.
+template <int IDM>
+__global__ void __launch_bounds__(256) k_dec_flat(GView g, DecArgs a) {
+  const uint64_t arcs = g.arcs;
+  const uint64_t step = (uint64_t)gridDim.x * blockDim.x * DEC_FLAT_U;
+  const uint32_t r = IDM == ID_CSR32 ? 32u : g.r;
+  const uint32_t s = IDM == ID_CSR32 ? 32u : g.s;
+  const uint32_t ms = mask_lo(s), mw = mask_lo(g.omega);
+  const bool want_w = a.weights != nullptr;
+  for (uint64_t j0 = (uint64_t)blockIdx.x * blockDim.x * DEC_FLAT_U + threadIdx.x; j0 < arcs; j0 += step) {
+    uint32_t id[DEC_FLAT_U], wt[DEC_FLAT_U];
+#pragma unroll
+    for (int k = 0; k < DEC_FLAT_U; k++) {
+      const uint64_t j = j0 + (uint64_t)k * blockDim.x;
+      id[k] = 0; wt[k] = 0;
+      if (j < arcs) {
+        if (IDM == ID_CSR32) {
+          id[k] = __ldcs(g.A32 + j);
+          if (want_w && g.W32) wt[k] = __ldcs(g.W32 + j);
+        } else {
+          const uint64_t p = j * r;
+          const uint64_t wi = p >> 5;
+          const uint32_t sh = (uint32_t)p & 31u;
+          const uint32_t x0 = __ldg(g.A32 + wi), x1 = __ldg(g.A32 + wi + 1);
+          id[k] = __funnelshift_r(x0, x1, sh) & ms;
+          if (want_w && g.omega) {
+            const uint32_t q = sh + s;  // < 64
+            const uint32_t y0 = q < 32 ? x0 : x1;
+            const uint32_t y1 = q < 32 ? x1 : __ldg(g.A32 + wi + 2);
+            wt[k] = __funnelshift_r(y0, y1, q & 31u) & mw;
+          }
         }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < DEC_FLAT_U; k++) {
+      const uint64_t j = j0 + (uint64_t)k * blockDim.x;
+      if (j < arcs) {
+        __stcs(a.ids + j, id[k]);
+        if (want_w) __stcs(a.weights + j, wt[k]);
       }
     }
   }
 }
 
+// ---------------------------------------------------------------------------
+// Local-ID decode: one launch writes row_ptr and every row.
+//
+// Blocks take a ticket when they start: tickets below the tile count are tile
+// CTAs (tiles in start order), the rest are heavy-schedule CTAs.  A tile CTA
+// decodes its offsets and geometry, publishes its arc count, and finds the
+// arcs of all earlier tiles by a decoupled look-back over their published
+// counts (a tile waits only on tiles that started before it).  It writes its
+// row offsets, flags them ready (heavy items read their row start there), and
+// then decodes its light vertices window by window: a window is up to DEC_C
+// light fields of one run of light vertices with no heavy vertex between them,
+// so its stream bits are contiguous; they are staged in shared memory with
+// 16-byte loads, every thread decodes DEC_C / TNT consecutive fields from
+// there (a shift and a mask per field, a running sum for gaps), a segmented
+// scan over the threads supplies the prefix of gap runs entered mid-way, and
+// the window is written out coalesced.
+// ---------------------------------------------------------------------------
+constexpr int DEC_C = 3328;           // light fields per window (13 per thread: odd, so the
+                                      // threads' stage stores fall in distinct banks)
+// Stream words per window: DEC_C fields of at most 32 bits, the header and
+// first ID (H + s <= 38 bits) of each of at most TV vertices, the headers of
+// zero-degree vertices in between (<= TV * H bits), 3 words of alignment and
+// one word read past the last field.
+constexpr int DEC_WW = (DEC_C * 32 + TV * 38 + TV * 6) / 32 + 8;
+constexpr uint64_t DEC_AGG = 1ull << 62, DEC_INCL = 2ull << 62, DEC_VAL = (1ull << 62) - 1;
+
+struct DecSmem {
+  TileSmem t;                  // offsets (xs, reused for the all-degree prefix), geometry, light list
+  __align__(16) uint32_t words[DEC_WW];  // stream words of the current window
+  uint32_t stage[DEC_C];       // decoded IDs of the current window
+  uint64_t rdelta[TV];         // per run of light vertices: output index - light field index
+  uint16_t rfirst[TV + 1];     // per run: its first light index
+  uint64_t base;               // arcs of all earlier tiles
+  uint32_t nruns, rcarry, ticket, ok;
+  uint32_t wsf[TNT / 32], wsv[TNT / 32];
+};
+
+static_assert(sizeof(DecSmem) <= 56 * 1024, "four decode CTAs per SM");
+
+__device__ __forceinline__ uint64_t ld_acquire_u64(const unsigned long long* p) {
+  uint64_t v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, uint64_t v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t dec_clock_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// bit of light field k of a vertex starting at bit st with field width w
+template <int IDM>
+__device__ __forceinline__ uint64_t dec_pos(uint64_t st, uint32_t k, uint32_t w, uint32_t s) {
+  if (IDM == ID_LOCAL_GAP) return k == 0 ? st : st + s + (uint64_t)(k - 1) * w;
+  return st + (uint64_t)k * w;
+}
+template <int IDM>
+__device__ __forceinline__ uint32_t dec_width(uint32_t k, uint32_t w, uint32_t s) {
+  return (IDM == ID_LOCAL_GAP && k == 0) ? s : w;
+}
+
+// segmented combine of (absolute?, value) pairs: x = e then x
+__device__ __forceinline__ void seg_after(uint32_t& xf, uint32_t& xv, uint32_t ef, uint32_t ev) {
+  if (!xf) { xv += ev; xf = ef; }
+}
+
+// Arcs of all tiles before tile b (warp 0 of the tile CTA; the result in lane 0).
+// Returns false if a wait ran out.
+__device__ __forceinline__ bool dec_lookback(const DecArgs& a, uint64_t b, uint64_t& base) {
+  const uint32_t lane = threadIdx.x & 31u;
+  base = 0;
+  int64_t p = (int64_t)b - 1 - (int64_t)lane;  // lane 0 reads the nearest predecessor
+  const uint64_t t0 = dec_clock_ns();
+  uint64_t spins = 0;
+  while (true) {
+    const uint64_t v = p >= 0 ? ld_acquire_u64(a.tile_status + p) : DEC_INCL;  // nothing before tile 0
+    const uint64_t flag = v >> 62;
+    const uint32_t incl = __ballot_sync(LG_FULL_MASK, flag == 2);
+    const uint32_t stop = incl ? (uint32_t)(__ffs(incl) - 1) : 31u;  // nearest inclusive prefix
+    const uint32_t unready = __ballot_sync(LG_FULL_MASK, flag == 0 && lane <= stop);
+    if (unready) {
+      if (++spins > (a.wait_ns >> 5) + 1024 || ((spins & 63u) == 0 && dec_clock_ns() - t0 > a.wait_ns)) return false;
+      __nanosleep(32);
+      continue;
+    }
+    base += warp_sum<uint64_t>(lane <= stop ? (v & DEC_VAL) : 0ull);
+    if (incl) return true;
+    p -= 32;
+  }
+}
+
 template <int IDM, int OFF>
-__global__ void __launch_bounds__(TNT) k_dec_all(GView g, DecArgs a) {
-  __shared__ TileSmem sm;
-  const unsigned hb = heavy_blocks(g.n_items);
-  if (blockIdx.x < hb) {
-    const uint64_t it = (uint64_t)blockIdx.x * (TNT / 32) + (threadIdx.x >> 5);
+__global__ void __launch_bounds__(TNT, 4) k_dec_local(GView g, DecArgs a) {
+  extern __shared__ __align__(16) unsigned char dec_smem_raw[];
+  DecSmem& sm = *reinterpret_cast<DecSmem*>(dec_smem_raw);
+  TileSmem& ts = sm.t;
+  const uint64_t ntiles = (g.n + TV - 1) / TV;
+  if (threadIdx.x == 0) sm.ticket = atomicAdd(a.ticket, 1u);
+  __syncthreads();
+  const uint64_t b = sm.ticket;
+  const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+  if (b >= ntiles) {
+    // heavy items, a warp each; the row start comes from the tile that owns the vertex
+    const uint64_t it = (b - ntiles) * (TNT / 32) + wid;
     if (it >= g.n_items) return;
     const HeavyItem h = g.items[it];
-    dec_fields<IDM, HEAVY_U>(g, a, h.bit, h.w, h.f0, h.f0 + h.nf, h.carry, a.row_ptr[h.v]);
+    uint64_t o = 0;
+    bool ok = true;
+    if (lane == 0) {
+      const uint64_t t0 = dec_clock_ns();
+      uint64_t spins = 0;
+      while (ld_acquire_u32(a.tile_ready + h.v / TV) == 0) {
+        if (++spins > (a.wait_ns >> 5) + 1024 || ((spins & 63u) == 0 && dec_clock_ns() - t0 > a.wait_ns)) {
+          ok = false;
+          break;
+        }
+        __nanosleep(64);
+      }
+      if (ok) o = __ldcg(a.row_ptr + h.v);
+      else atomicOr(a.err, DERR_INTERNAL);
+    }
+    if (!__shfl_sync(LG_FULL_MASK, ok ? 1u : 0u, 0)) return;
+    o = __shfl_sync(LG_FULL_MASK, o, 0);
+    dec_fields<IDM, HEAVY_U>(g, a, h.bit, h.w, h.f0, h.f0 + h.nf, h.carry, o);
     return;
   }
-  const uint64_t v0 = (uint64_t)(blockIdx.x - hb) * TV;
+  // ---- tile: offsets and geometry
+  const uint64_t v0 = b * TV;
   const int cnt = (int)min((uint64_t)TV, g.n - v0);
-  tile_offsets<OFF>(g, v0, cnt, sm.xs, sm.ts);
+  tile_offsets<OFF>(g, v0, cnt, ts.xs, ts.ts);
   __syncthreads();
-  tile_classify<IDM>(g, sm, cnt, [](int) { return true; });
-  __shared__ uint64_t orow[TV];  // output row of each light vertex
-  for (uint32_t j = threadIdx.x; j < sm.nlight; j += TNT) orow[j] = a.row_ptr[v0 + sm.clist[j]];
-  __syncthreads();
-  // warp k takes the light vertices whose first field falls in [F k / 8, F (k+1) / 8)
-  constexpr uint32_t NW = TNT / 32;
-  const uint32_t wk = threadIdx.x >> 5;
-  const uint64_t F = sm.nfields;
-  const uint32_t flo = (uint32_t)(F * wk / NW), fhi = (uint32_t)(F * (wk + 1) / NW);
-  uint32_t jb = 0, je = sm.nlight;
-  {
-    uint32_t lo = 0, hi = sm.nlight;
-    while (lo < hi) { const uint32_t m = (lo + hi) >> 1; if (sm.fpre[m] < flo) lo = m + 1; else hi = m; }
-    jb = lo;
-    hi = sm.nlight;
-    while (lo < hi) { const uint32_t m = (lo + hi) >> 1; if (sm.fpre[m] < fhi) lo = m + 1; else hi = m; }
-    je = lo;
+  uint32_t lc = 0, lf = 0;
+  uint64_t all = 0;
+  bool light[TV / TNT];
+  uint32_t dq[TV / TNT];
+#pragma unroll
+  for (int q = 0; q < TV / TNT; q++) {
+    const int i = threadIdx.x * (TV / TNT) + q;
+    light[q] = false;
+    dq[q] = 0;
+    if (i < cnt) {
+      uint64_t start; uint32_t d, w;
+      vgeo<IDM>(g, ts.xs[i], ts.xs[i + 1], start, d, w);
+      ts.st[i] = start; ts.deg[i] = d; ts.wid[i] = (uint8_t)w;
+      dq[q] = d;
+      all += d;
+      if (d > 0 && d <= g.heavy_min) { light[q] = true; lc++; lf += d; }
+    }
   }
-  if (jb >= je) return;
-  // The warp walks the fields of its vertices [jb, je), contiguous in the
-  // compacted light list, 32 per chunk and DEC_U chunks per step, a lane per
-  // field.  A chunk's vertex starts come from the next 32 entries of fpre (one
-  // per lane), OR-reduced into a mask of the lanes where a vertex begins; a
-  // lane's vertex is the current one plus the starts at or below it.
-  constexpr int DEC_U = 4;
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t fend = sm.fpre[je];
-  uint32_t jcur = jb, carry = 0;
-  for (uint32_t b = sm.fpre[jb]; b < fend; b += 32u * DEC_U) {
-    uint32_t vj[DEC_U], vk[DEC_U], val[DEC_U];
+  uint64_t ltot, atot;
+  const uint64_t lpre = block_excl_scan<uint64_t, TNT>(((uint64_t)lc << 32) | lf, ltot, ts.red64);
+  const uint64_t apre = block_excl_scan<uint64_t, TNT>(all, atot, ts.red64);  // xs reads are done
+  uint64_t* pre_all = ts.xs;  // reused: in-tile exclusive prefix of all degrees
+  {
+    uint32_t ci = (uint32_t)(lpre >> 32), cf = (uint32_t)lpre;
+    uint64_t ca = apre;
 #pragma unroll
-    for (int u = 0; u < DEC_U; u++) {
-      const uint32_t cb = b + 32u * u;
-      const uint32_t nx = jcur + 1 + lane;
-      const uint32_t rel = nx < je ? sm.fpre[nx] - cb : 0xffffffffu;
-      const uint32_t starts = __reduce_or_sync(LG_FULL_MASK, rel < 32u ? (1u << rel) : 0u);
-      const uint32_t upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
-      const uint32_t j = min(jcur + (uint32_t)__popc(starts & upto), je - 1);
-      vj[u] = j;
-      vk[u] = cb + lane - sm.fpre[j];
-      jcur = __shfl_sync(LG_FULL_MASK, j, 31);
+    for (int q = 0; q < TV / TNT; q++) {
+      const int i = threadIdx.x * (TV / TNT) + q;
+      if (i < cnt) pre_all[i] = ca;
+      ca += dq[q];
+      if (light[q]) {
+        ts.clist[ci] = (uint16_t)i;
+        ts.fpre[ci] = cf;
+        ci++;
+        cf += dq[q];
+      }
     }
-#pragma unroll
-    for (int u = 0; u < DEC_U; u++) {
-      const uint32_t f = b + 32u * u + lane;
-      const int i = sm.clist[vj[u]];
-      val[u] = f < fend ? field_at<IDM>(g, sm.st[i], sm.wid[i], vk[u]) : 0u;
+  }
+  if (threadIdx.x == 0) {
+    ts.nlight = (uint32_t)(ltot >> 32);
+    ts.nfields = (uint32_t)ltot;
+    ts.fpre[ts.nlight] = (uint32_t)ltot;
+    sm.ok = 1;
+  }
+  // ---- arcs before this tile (decoupled look-back), then the row offsets
+  if (wid == 0) {
+    if (lane == 0) {
+      if (b == 0) st_release_u64(a.tile_status, DEC_INCL | atot);
+      else st_release_u64(a.tile_status + b, DEC_AGG | atot);
     }
+    uint64_t base = 0;
+    bool ok = true;
+    if (b > 0) ok = dec_lookback(a, b, base);
+    if (lane == 0) {
+      if (!ok) { atomicOr(a.err, DERR_INTERNAL); sm.ok = 0; }
+      if (b > 0) st_release_u64(a.tile_status + b, DEC_INCL | (base + atot));
+      sm.base = base;
+    }
+  }
+  __syncthreads();
+  if (!sm.ok) return;
+  const uint64_t base = sm.base;
+  for (int i = threadIdx.x; i < cnt; i += TNT) a.row_out[v0 + i] = base + pre_all[i];
+  if (v0 + (uint64_t)cnt == g.n && threadIdx.x == 0) a.row_out[g.n] = base + atot;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    st_release_u32(a.tile_ready + b, 1u);
+  }
+  const uint32_t nl = ts.nlight;
+  if (nl == 0) return;
+  // ---- runs of light vertices with contiguous output rows (a heavy vertex breaks a run)
+  {
+    uint32_t fl[TV / TNT], c = 0;
+    uint64_t dl[TV / TNT];
 #pragma unroll
-    for (int u = 0; u < DEC_U; u++) {
-      const uint32_t f = b + 32u * u + lane;
-      uint32_t x = val[u];
+    for (int q = 0; q < TV / TNT; q++) {
+      const uint32_t j = threadIdx.x * (TV / TNT) + q;
+      fl[q] = 0;
+      dl[q] = 0;
+      if (j < nl) {
+        // output index of light field f is row_ptr[v] + (f - fpre[j]): constant offset
+        // along light vertices with only zero-degree vertices between them
+        dl[q] = base + pre_all[ts.clist[j]] - (uint64_t)ts.fpre[j];
+        fl[q] = j == 0 || dl[q] != base + pre_all[ts.clist[j - 1]] - (uint64_t)ts.fpre[j - 1];
+        c += fl[q];
+      }
+    }
+    uint32_t total;
+    uint32_t pos = block_excl_scan<uint32_t, TNT>(c, total, ts.ts.red);
+#pragma unroll
+    for (int q = 0; q < TV / TNT; q++) {
+      const uint32_t j = threadIdx.x * (TV / TNT) + q;
+      if (fl[q]) { sm.rfirst[pos] = (uint16_t)j; sm.rdelta[pos] = dl[q]; pos++; }
+    }
+    if (threadIdx.x == 0) { sm.nruns = total; sm.rfirst[total] = (uint16_t)nl; }
+  }
+  __syncthreads();
+  // ---- windows
+  const uint32_t s = g.s;
+  const uint32_t nruns = sm.nruns;
+  for (uint32_t q = 0; q < nruns; q++) {
+    const uint32_t F0 = ts.fpre[sm.rfirst[q]], F1 = ts.fpre[sm.rfirst[q + 1]];
+    const uint64_t delta = sm.rdelta[q];
+    for (uint32_t W0 = F0; W0 < F1; W0 += DEC_C) {
+      const uint32_t W1 = min(F1, W0 + (uint32_t)DEC_C), Fw = W1 - W0;
+      // the window's bits: from its first field to the end of its last one
+      uint32_t ja, jb;
+      {
+        uint32_t lo = 0, hi = nl - 1;
+        while (lo < hi) { const uint32_t m = (lo + hi + 1) >> 1; if (ts.fpre[m] <= W0) lo = m; else hi = m - 1; }
+        ja = lo;
+        hi = nl - 1;
+        while (lo < hi) { const uint32_t m = (lo + hi + 1) >> 1; if (ts.fpre[m] <= W1 - 1) lo = m; else hi = m - 1; }
+        jb = lo;
+      }
+      const int ia = ts.clist[ja], ib = ts.clist[jb];
+      const uint32_t kb = W1 - 1 - ts.fpre[jb];
+      const uint64_t bA = dec_pos<IDM>(ts.st[ia], W0 - ts.fpre[ja], ts.wid[ia], s);
+      const uint64_t bB = dec_pos<IDM>(ts.st[ib], kb, ts.wid[ib], s) + dec_width<IDM>(kb, ts.wid[ib], s);
+      const uint64_t wA = (bA >> 5) & ~3ull;
+      const uint32_t nw = (uint32_t)(((bB + 31) >> 5) + 1 - wA);  // <= DEC_WW - 4
+      const uint4* src = reinterpret_cast<const uint4*>(g.A32 + wA);
+      uint4* dst = reinterpret_cast<uint4*>(sm.words);
+      for (uint32_t x = threadIdx.x; x * 4 < nw; x += TNT) dst[x] = __ldcs(src + x);
+      const uint32_t carry_in = sm.rcarry;
+      __syncthreads();
+      // this thread's fields [fa, fb) of the window
+      const uint32_t fa = W0 + (uint32_t)((uint64_t)Fw * threadIdx.x / TNT);
+      const uint32_t fb = W0 + (uint32_t)((uint64_t)Fw * (threadIdx.x + 1) / TNT);
+      uint32_t lastf = 0, lastv = 0, pend = fa;
+      if (fa < fb) {
+        uint32_t lo = ja, hi = jb;
+        while (lo < hi) { const uint32_t m = (lo + hi + 1) >> 1; if (ts.fpre[m] <= fa) lo = m; else hi = m - 1; }
+        uint32_t j = lo, f = fa, k = fa - ts.fpre[lo];
+        pend = k ? min(fb, ts.fpre[j + 1]) : fa;  // fields of a neighborhood entered mid-way
+        const uint64_t wbase = wA * 32;
+        while (f < fb) {
+          const int i = ts.clist[j];
+          const uint32_t w = ts.wid[i], mw = mask_lo(w);
+          uint32_t m = min(ts.deg[i] - k, fb - f);
+          uint32_t* out = sm.stage + (f - W0);
+          f += m;
+          uint32_t p = (uint32_t)(dec_pos<IDM>(ts.st[i], k, w, s) - wbase);
+          uint32_t run = 0;
+          if (IDM == ID_LOCAL_GAP && k == 0) {
+            run = __funnelshift_r(sm.words[p >> 5], sm.words[(p >> 5) + 1], p & 31u) & mask_lo(s);
+            *out++ = run;
+            p += s;
+            m--;
+          }
+          for (; m; m--) {
+            const uint32_t x = __funnelshift_r(sm.words[p >> 5], sm.words[(p >> 5) + 1], p & 31u) & mw;
+            p += w;
+            if (IDM == ID_LOCAL_GAP) { run += x; *out++ = run; }
+            else *out++ = x;
+          }
+          lastf = k == 0;
+          lastv = run;
+          j++;
+          k = 0;
+        }
+      }
       if (IDM == ID_LOCAL_GAP) {
-        // segmented inclusive sum: a segment starts at a vertex's first field;
-        // lane 0 continues the previous chunk's vertex with its running ID
-        if (lane == 0 && vk[u] != 0) x += carry;
-        const uint32_t seg0 = vk[u] <= lane ? lane - vk[u] : 0u;  // first lane of this vertex here
+        // inclusive segmented scan of (lastf, lastv) over the threads, after the
+        // window's carry (the absolute ID of field W0 - 1 when the window starts mid-vertex)
+        uint32_t xf = lastf, xv = lastv;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t y = __shfl_up_sync(LG_FULL_MASK, x, o);
-          if (lane >= seg0 + o) x += y;
+          const uint32_t ef = __shfl_up_sync(LG_FULL_MASK, xf, o), ev = __shfl_up_sync(LG_FULL_MASK, xv, o);
+          if (lane >= (uint32_t)o) seg_after(xf, xv, ef, ev);
         }
-        carry = __shfl_sync(LG_FULL_MASK, x, 31);
-      }
-      if (f < fend) {
-        const int i = sm.clist[vj[u]];
-        const uint64_t o = orow[vj[u]] + vk[u];
-        __stcs(a.ids + o, x);
-        if (a.weights) {
-          uint32_t wt = 0;
-          if (IDM == ID_GLOBAL && g.omega) wt = weight_at(g, sm.st[i], vk[u]);
-          if (IDM == ID_CSR32 && g.W32) wt = __ldg(g.W32 + (sm.st[i] >> 5) + vk[u]);
-          __stcs(a.weights + o, wt);
+        if (lane == 31) { sm.wsf[wid] = xf; sm.wsv[wid] = xv; }
+        __syncthreads();
+        uint32_t pf = W0 > F0 ? 1u : 0u, pv = W0 > F0 ? carry_in : 0u;
+        for (uint32_t ww = 0; ww < wid; ww++) {
+          uint32_t tf = sm.wsf[ww], tv = sm.wsv[ww];
+          seg_after(tf, tv, pf, pv);
+          pf = tf;
+          pv = tv;
+        }
+        uint32_t lf2 = __shfl_up_sync(LG_FULL_MASK, xf, 1), lv2 = __shfl_up_sync(LG_FULL_MASK, xv, 1);
+        if (lane == 0) { lf2 = 0; lv2 = 0; }
+        seg_after(lf2, lv2, pf, pv);
+        for (uint32_t f = fa; f < pend; f++) sm.stage[f - W0] += lv2;
+        if (threadIdx.x == TNT - 1) {
+          seg_after(xf, xv, pf, pv);
+          sm.rcarry = xv;  // the absolute ID of the window's last field
         }
       }
+      __syncthreads();
+      for (uint32_t f = threadIdx.x; f < Fw; f += TNT) __stcs(a.ids + delta + W0 + f, sm.stage[f]);
+      __syncthreads();
     }
   }
 }
@@ -1332,16 +1640,28 @@ cudaError_t launch_ppr_join(const GView& g, float* cin, uint32_t slot, uint32_t 
 }
 
 template <int IDM, int OFF>
-cudaError_t launch_dec_degrees(const GView& g, const DecArgs& a, cudaStream_t st) {
-  if (g.n == 0) return cudaSuccess;
-  k_dec_degrees<IDM, OFF><<<tiles_of(g.n), TNT, 0, st>>>(g, a);
-  count_launch();
-  return cudaGetLastError();
+cudaError_t launch_dec_rows(const GView& g, const DecArgs& a, cudaStream_t st) {
+  if constexpr (IDM == ID_GLOBAL || IDM == ID_CSR32) {
+    if (g.n == 0) return cudaSuccess;
+    k_dec_rows<OFF><<<tiles_of(g.n), TNT, 0, st>>>(g, a);
+    count_launch();
+    return cudaGetLastError();
+  } else {
+    return cudaErrorNotSupported;  // local IDs: k_dec_local writes the row offsets
+  }
 }
 template <int IDM, int OFF>
 cudaError_t launch_dec_all(const GView& g, const DecArgs& a, cudaStream_t st) {
-  if (g.n == 0) return cudaSuccess;
-  k_dec_all<IDM, OFF><<<heavy_blocks(g.n_items) + tiles_of(g.n), TNT, 0, st>>>(g, a);
+  if (g.n == 0 || ((IDM == ID_GLOBAL || IDM == ID_CSR32) && g.arcs == 0)) return cudaSuccess;
+  if constexpr (IDM == ID_GLOBAL || IDM == ID_CSR32) {
+    const uint64_t per_block = 256ull * DEC_FLAT_U;
+    k_dec_flat<IDM><<<grid_for(g.arcs, (unsigned)per_block, 152 * 16), 256, 0, st>>>(g, a);
+  } else {
+    const cudaError_t e = cudaFuncSetAttribute(k_dec_local<IDM, OFF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)sizeof(DecSmem));
+    if (e != cudaSuccess) return e;
+    k_dec_local<IDM, OFF><<<tiles_of(g.n) + heavy_blocks(g.n_items), TNT, sizeof(DecSmem), st>>>(g, a);
+  }
   count_launch();
   return cudaGetLastError();
 }
@@ -1352,7 +1672,7 @@ const TravOps* make_ops() {
       &launch_pr_init<IDM, OFF>,    &launch_pr_pull<IDM, OFF>,     &launch_bfs_pull<IDM, OFF>,
       &launch_bfs_push<IDM, OFF>,   &launch_nbr_degrees<IDM, OFF>, &launch_nbr_decode<IDM, OFF>,
       &launch_plan_count<IDM, OFF>, &launch_plan_fill<IDM, OFF>,   &launch_plan_carry<IDM, OFF>,
-      &launch_ppr_pull<IDM, OFF>,   &launch_ppr_join<IDM, OFF>,   &launch_dec_degrees<IDM, OFF>,
+      &launch_ppr_pull<IDM, OFF>,   &launch_ppr_join<IDM, OFF>,   &launch_dec_rows<IDM, OFF>,
       &launch_dec_all<IDM, OFF>,
   };
   return &ops;

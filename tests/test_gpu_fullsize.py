@@ -4,8 +4,9 @@ DM relabel + local-gap IDs + Elias-Fano offsets (select samples every 512),
 BFS from the same 16 seeded sources, 20 PageRank iterations (d = 0.85).
 
 Compared with the oracle: the whole A stream, the Elias-Fano arrays and the
-permutation byte for byte; 20,000 sampled neighborhoods; all 16 BFS depth rows;
-every PageRank value within 1e-4 relative.
+permutation byte for byte; the whole-graph decode (row offsets in full, 20,000
+stored rows); 20,000 sampled neighborhoods; all 16 BFS depth rows; every
+PageRank value within 1e-4 relative.
 """
 from concurrent.futures import ThreadPoolExecutor
 
@@ -39,10 +40,16 @@ def community():
     g.free()
 
 
-def test_fullsize_streams_byte_equal(community):
+@pytest.fixture(scope="module")
+def oracle_encoded(community):
+    g0, _ = community
+    return oracle.encode(g0.n, g0.row_ptr, g0.col, id_mode=oracle.ID_LOCAL_GAP, off_mode=oracle.OFF_EF,
+                         relabel=True, sample=512)
+
+
+def test_fullsize_streams_byte_equal(community, oracle_encoded):
     g0, g = community
-    e = oracle.encode(g0.n, g0.row_ptr, g0.col, id_mode=oracle.ID_LOCAL_GAP, off_mode=oracle.OFF_EF,
-                      relabel=True, sample=512)
+    e = oracle_encoded
     a = lg.lg_arrays_get(g)
     st = lg.lg_stats_get(g)
     assert st["bits_A"] == e.bits_A and st["ef_l"] == e.ef_l
@@ -53,6 +60,26 @@ def test_fullsize_streams_byte_equal(community):
     assert np.array_equal(a["A"], e.A)
     # bytes: compressed payload against the 32-bit CSR of the same graph
     assert (st["bits_A"] + st["bits_O"]) / 8 < 0.75 * (4 * g0.arcs + 8 * (g0.n + 1))
+
+
+def test_fullsize_whole_graph_decode(community, oracle_encoded):
+    """lg_decode of the whole graph (stored order, stored labels): row offsets
+    in full from the relabeled degrees, rows of 20,000 stored vertices (the
+    hub tiles first) against the oracle's bit-by-bit decode."""
+    g0, g = community
+    e = oracle_encoded
+    rp, col = lg.lg_decode(g)
+    rp = rp.cpu().numpy().view(np.uint64)
+    col = col.cpu().numpy().view(np.uint32)
+    sdeg = np.empty(g0.n, dtype=np.uint64)
+    sdeg[e.perm] = np.diff(g0.row_ptr)
+    want = np.zeros(g0.n + 1, dtype=np.uint64)
+    np.cumsum(sdeg, out=want[1:])
+    assert np.array_equal(rp, want)
+    rng = np.random.default_rng(13)
+    vs = np.concatenate([np.arange(2048), np.arange(g0.n - 1024, g0.n), rng.integers(0, g0.n, size=16928)])
+    for v in vs:
+        assert np.array_equal(col[rp[v]:rp[v + 1]], e.decode_raw(int(v))), f"stored vertex {v}"
 
 
 def test_fullsize_sampled_neighborhoods(community):

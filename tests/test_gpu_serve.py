@@ -254,3 +254,85 @@ def test_serve_all_modes(graphs, id_mode, off_mode, relabel):
         kind, src, vs = tickets[r["ticket"]]
         assert r["status"] == 0
         check_result(h, kind, src, vs, r["result"])
+
+
+@pytest.fixture(scope="module")
+def large_graphs():
+    """R-MAT scales 20 and 22 (edge factor 16, seed 4: the serving workload's
+    first two graphs), global IDs + Elias-Fano offsets with DM relabeling, so
+    the PageRank sweep keeps the hub rows in L2 (hot-row policy) as the
+    serving benchmark runs it."""
+    import torch
+
+    lg.load(auto_build=True)
+    out = []
+    for sc in (20, 22):
+        rp, col, _ = gen.rmat_gpu(sc, 16, seed=4)
+        g = lg.lg_encode(rp, col, id_mode=lg.LG_ID_GLOBAL, off_mode=lg.LG_OFF_EF, relabel=True)
+
+        class H:
+            pass
+
+        H.n, H.row_ptr, H.col = rp.numel() - 1, rp.cpu().numpy().view(np.uint64), col.cpu().numpy().view(np.uint32)
+        out.append((H, g))
+        del rp, col
+        torch.cuda.empty_cache()
+    return out
+
+
+def test_serve_large_graphs_mix_alone_and_oracle(large_graphs):
+    """A burst of 300 mixed requests over the 2^20 and 2^22 graphs: every
+    result equals the same request run alone; lookups equal the CSR rows;
+    BFS depths and personalized PageRank of a sample (hubs among the sources)
+    equal the oracle (PageRank within 1e-4 relative)."""
+    hs = [h for h, _ in large_graphs]
+    enc = [g for _, g in large_graphs]
+    tr = gen.serve_trace([h.row_ptr for h in hs], 300, seed=21)
+    # put the largest hub of each graph among the BFS and PPR sources
+    for gi, h in enumerate(hs):
+        hub = int(np.argmax(np.diff(h.row_ptr)))
+        for kind in (1, 2):
+            idx = np.flatnonzero((tr.kind == kind) & (tr.graph == gi))
+            if idx.size:
+                tr.source[idx[0]] = hub
+    s = lg.lg_server_create(enc, device_bytes=8 << 30, host_bytes=4 << 30)
+    alone = [run_alone(s, tr, i) for i in range(len(tr))]
+    s.destroy()
+    s = lg.lg_server_create(enc, device_bytes=8 << 30, host_bytes=4 << 30)
+    keep = keep_buffers(hs, tr)
+    lat, rs = lg.lg_server_replay(s, tr.kind, tr.graph, tr.source, tr.nbr_off, tr.nbr_vertices, tr.arrival_ns,
+                                  keep=keep)
+    st = lg.lg_server_stats_get(s)
+    s.destroy()
+    assert rs["completed"] == len(tr) and rs["failed"] == 0
+    for i in range(len(tr)):
+        k = int(tr.kind[i])
+        count = int(tr.nbr_off[i + 1] - tr.nbr_off[i]) if k == 0 else 0
+        mix = parse_kept(keep[i], k, count)
+        if k == 0:
+            assert np.array_equal(mix[0], alone[i][0]) and np.array_equal(mix[1], alone[i][1]), f"lookup {i}"
+        elif k == 1:
+            assert np.array_equal(mix, alone[i]), f"BFS {i}"
+        else:
+            a = alone[i].astype(np.float64)
+            m = mix.astype(np.float64)
+            nz = a > 0
+            assert np.all(m[~nz] == 0)
+            assert (np.abs(m[nz] - a[nz]) / a[nz]).max() <= PR_RTOL, f"PPR {i}"
+    assert st["bfs_joins_running"] > 0 and st["ppr_joins_running"] > 0 and st["nbr_max_batch"] > 1, st
+    # oracle: every lookup, the first BFS and PPR requests of each graph
+    checked = set()
+    for i in range(len(tr)):
+        k, gi = int(tr.kind[i]), int(tr.graph[i])
+        vs = tr.nbr_vertices[int(tr.nbr_off[i]):int(tr.nbr_off[i + 1])]
+        if k == 0 or (k, gi) not in checked:
+            h = hs[gi]
+            if k == 2:
+                want = oracle.pagerank(h.n, h.row_ptr, h.col, 0.85, ITERS, personalize=int(tr.source[i]), threads=16)
+                got = alone[i].astype(np.float64)
+                nz = want > 0
+                assert np.all(got[~nz] == 0)
+                assert (np.abs(got[nz] - want[nz]) / want[nz]).max() <= PR_RTOL, f"PPR {i} vs oracle"
+            else:
+                check_result(h, k, tr.source[i], vs, alone[i])
+            checked.add((k, gi))
