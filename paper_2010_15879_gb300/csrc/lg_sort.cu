@@ -713,21 +713,7 @@ __global__ void __launch_bounds__(256) k_dm_rows(const uint64_t* __restrict__ rp
       const uint64_t lq = __shfl_sync(LG_FULL_MASK, lo, q);
       const uint64_t oq = __shfl_sync(LG_FULL_MASK, o, q);
       const uint32_t dq = __shfl_sync(LG_FULL_MASK, d, q);
-      // four arcs per lane in flight: their col loads, then their perm gathers
-      uint32_t k = lane;
-      for (; k + 96 < dq; k += 128) {
-        uint32_t cc[4], pv[4];
-#pragma unroll
-        for (int z = 0; z < 4; z++) cc[z] = ldg_hint(col + lq + k + 32 * z, pstream);
-#pragma unroll
-        for (int z = 0; z < 4; z++) pv[z] = ldg_hint(perm + cc[z], pkeep);
-#pragma unroll
-        for (int z = 0; z < 4; z++) {
-          __stcs(ncol + oq + k + 32 * z, pv[z]);
-          if (VALS) __stcs(nw + oq + k + 32 * z, ldg_hint(w + lq + k + 32 * z, pstream));
-        }
-      }
-      for (; k < dq; k += 32) {
+      for (uint32_t k = lane; k < dq; k += 32) {
         const uint32_t cc = ldg_hint(col + lq + k, pstream);
         __stcs(ncol + oq + k, ldg_hint(perm + cc, pkeep));
         if (VALS) __stcs(nw + oq + k, ldg_hint(w + lq + k, pstream));

@@ -1144,24 +1144,24 @@ __global__ void __launch_bounds__(256) k_dec_flat(GView g, DecArgs a) {
 // scan over the threads supplies the prefix of gap runs entered mid-way, and
 // the window is written out coalesced.
 // ---------------------------------------------------------------------------
-constexpr int DEC_C = 3328;           // light fields per window (13 per thread: odd, so the
-                                      // threads' stage stores fall in distinct banks)
-// Stream words per window: DEC_C fields of at most 32 bits, the header and
-// first ID (H + s <= 38 bits) of each of at most TV vertices, the headers of
-// zero-degree vertices in between (<= TV * H bits), 3 words of alignment and
-// one word read past the last field.
-constexpr int DEC_WW = (DEC_C * 32 + TV * 38 + TV * 6) / 32 + 8;
+constexpr int DEC_P = 13;                  // light fields per lane and window (odd: the lanes' stage
+                                           // stores fall in distinct banks)
+constexpr int DEC_WF = 32 * DEC_P;         // light fields per warp window
+constexpr int DEC_WCAP = 576;              // stream words a warp window may stage (longer windows shrink)
 constexpr uint64_t DEC_AGG = 1ull << 62, DEC_INCL = 2ull << 62, DEC_VAL = (1ull << 62) - 1;
+
+struct DecWarp {
+  __align__(16) uint32_t words[DEC_WCAP + 8];  // stream words of the warp's current window
+  uint32_t stage[DEC_WF];                      // decoded IDs of the warp's current window
+};
 
 struct DecSmem {
   TileSmem t;                  // offsets (xs, reused for the all-degree prefix), geometry, light list
-  __align__(16) uint32_t words[DEC_WW];  // stream words of the current window
-  uint32_t stage[DEC_C];       // decoded IDs of the current window
+  DecWarp w[TNT / 32];
   uint64_t rdelta[TV];         // per run of light vertices: output index - light field index
   uint16_t rfirst[TV + 1];     // per run: its first light index
   uint64_t base;               // arcs of all earlier tiles
-  uint32_t nruns, rcarry, ticket, ok;
-  uint32_t wsf[TNT / 32], wsv[TNT / 32];
+  uint32_t nruns, ticket, ok;
 };
 
 static_assert(sizeof(DecSmem) <= 56 * 1024, "four decode CTAs per SM");
@@ -1367,61 +1367,74 @@ __global__ void __launch_bounds__(TNT, 4) k_dec_local(GView g, DecArgs a) {
     if (threadIdx.x == 0) { sm.nruns = total; sm.rfirst[total] = (uint16_t)nl; }
   }
   __syncthreads();
-  // ---- windows
-  const uint32_t s = g.s;
-  const uint32_t nruns = sm.nruns;
-  for (uint32_t q = 0; q < nruns; q++) {
-    const uint32_t F0 = ts.fpre[sm.rfirst[q]], F1 = ts.fpre[sm.rfirst[q + 1]];
-    const uint64_t delta = sm.rdelta[q];
-    for (uint32_t W0 = F0; W0 < F1; W0 += DEC_C) {
-      const uint32_t W1 = min(F1, W0 + (uint32_t)DEC_C), Fw = W1 - W0;
-      // the window's bits: from its first field to the end of its last one
-      uint32_t ja, jb;
-      {
-        uint32_t lo = 0, hi = nl - 1;
-        while (lo < hi) { const uint32_t m = (lo + hi + 1) >> 1; if (ts.fpre[m] <= W0) lo = m; else hi = m - 1; }
-        ja = lo;
-        hi = nl - 1;
-        while (lo < hi) { const uint32_t m = (lo + hi + 1) >> 1; if (ts.fpre[m] <= W1 - 1) lo = m; else hi = m - 1; }
-        jb = lo;
-      }
-      const int ia = ts.clist[ja], ib = ts.clist[jb];
-      const uint32_t kb = W1 - 1 - ts.fpre[jb];
-      const uint64_t bA = dec_pos<IDM>(ts.st[ia], W0 - ts.fpre[ja], ts.wid[ia], s);
-      const uint64_t bB = dec_pos<IDM>(ts.st[ib], kb, ts.wid[ib], s) + dec_width<IDM>(kb, ts.wid[ib], s);
+  // ---- warps: ranges of whole light vertices balanced by fields, decoded in
+  // windows of up to DEC_WF fields that never cross a run (contiguous stream
+  // bits, one output offset); lanes decode DEC_P consecutive fields each
+  {
+    const uint32_t s = g.s, F = ts.nfields;
+    const uint32_t* fpre = ts.fpre;
+    DecWarp& W = sm.w[wid];
+    // warp range: from the first light vertex starting at or after F * wid / 8
+    // to the one starting at or after F * (wid + 1) / 8
+    auto first_at_or_after = [&](uint32_t target) {
+      uint32_t lo = 0, hi = nl;
+      while (lo < hi) { const uint32_t m = (lo + hi) >> 1; if (fpre[m] < target) lo = m + 1; else hi = m; }
+      return lo;
+    };
+    const uint32_t jr0 = first_at_or_after((uint32_t)((uint64_t)F * wid / (TNT / 32)));
+    const uint32_t jr1 = wid + 1 == TNT / 32 ? nl : first_at_or_after((uint32_t)((uint64_t)F * (wid + 1) / (TNT / 32)));
+    const uint32_t Rend = fpre[jr1];
+    // the last light vertex holding field f, searched in [lo, hi]
+    auto vertex_of = [&](uint32_t f, uint32_t lo, uint32_t hi) {
+      while (lo < hi) { const uint32_t m = (lo + hi + 1) >> 1; if (fpre[m] <= f) lo = m; else hi = m - 1; }
+      return lo;
+    };
+    uint32_t q = 0;           // run holding W0
+    uint32_t wcarry = 0;      // absolute ID of the field before W0 (gap mode, W0 inside a vertex)
+    for (uint32_t W0 = fpre[jr0]; W0 < Rend;) {
+      while (q + 1 < sm.nruns && fpre[sm.rfirst[q + 1]] <= W0) q++;
+      const uint32_t RE = min(Rend, fpre[sm.rfirst[q + 1]]);
+      uint32_t Fw = min((uint32_t)DEC_WF, RE - W0);
+      const uint32_t ja = vertex_of(W0, jr0, jr1 - 1);
+      const int ia = ts.clist[ja];
+      const uint64_t bA = dec_pos<IDM>(ts.st[ia], W0 - fpre[ja], ts.wid[ia], s);
       const uint64_t wA = (bA >> 5) & ~3ull;
-      const uint32_t nw = (uint32_t)(((bB + 31) >> 5) + 1 - wA);  // <= DEC_WW - 4
+      uint32_t jb, nw;
+      while (true) {  // shrink the window until its stream words fit
+        jb = vertex_of(W0 + Fw - 1, ja, jr1 - 1);
+        const int ib = ts.clist[jb];
+        const uint32_t kb = W0 + Fw - 1 - fpre[jb];
+        const uint64_t bB = dec_pos<IDM>(ts.st[ib], kb, ts.wid[ib], s) + dec_width<IDM>(kb, ts.wid[ib], s);
+        nw = (uint32_t)(((bB + 31) >> 5) + 1 - wA);
+        if (nw <= DEC_WCAP || Fw == 1) break;
+        Fw = (Fw + 1) >> 1;
+      }
       const uint4* src = reinterpret_cast<const uint4*>(g.A32 + wA);
-      uint4* dst = reinterpret_cast<uint4*>(sm.words);
-      for (uint32_t x = threadIdx.x; x * 4 < nw; x += TNT) dst[x] = __ldcs(src + x);
-      const uint32_t carry_in = sm.rcarry;
-      __syncthreads();
-      // this thread's fields [fa, fb) of the window
-      const uint32_t fa = W0 + (uint32_t)((uint64_t)Fw * threadIdx.x / TNT);
-      const uint32_t fb = W0 + (uint32_t)((uint64_t)Fw * (threadIdx.x + 1) / TNT);
+      uint4* dst = reinterpret_cast<uint4*>(W.words);
+      for (uint32_t x = lane; x * 4 < nw; x += 32) dst[x] = __ldcs(src + x);
+      __syncwarp();
+      const uint32_t fa = W0 + Fw * lane / 32, fb = W0 + Fw * (lane + 1) / 32;
       uint32_t lastf = 0, lastv = 0, pend = fa;
       if (fa < fb) {
-        uint32_t lo = ja, hi = jb;
-        while (lo < hi) { const uint32_t m = (lo + hi + 1) >> 1; if (ts.fpre[m] <= fa) lo = m; else hi = m - 1; }
-        uint32_t j = lo, f = fa, k = fa - ts.fpre[lo];
-        pend = k ? min(fb, ts.fpre[j + 1]) : fa;  // fields of a neighborhood entered mid-way
+        uint32_t j = vertex_of(fa, ja, jb), f = fa, k = fa - fpre[j];
+        pend = k ? min(fb, fpre[j + 1]) : fa;  // fields of a neighborhood entered mid-way
         const uint64_t wbase = wA * 32;
         while (f < fb) {
           const int i = ts.clist[j];
           const uint32_t w = ts.wid[i], mw = mask_lo(w);
           uint32_t m = min(ts.deg[i] - k, fb - f);
-          uint32_t* out = sm.stage + (f - W0);
+          uint32_t* out = W.stage + (f - W0);
           f += m;
           uint32_t p = (uint32_t)(dec_pos<IDM>(ts.st[i], k, w, s) - wbase);
           uint32_t run = 0;
           if (IDM == ID_LOCAL_GAP && k == 0) {
-            run = __funnelshift_r(sm.words[p >> 5], sm.words[(p >> 5) + 1], p & 31u) & mask_lo(s);
+            run = __funnelshift_r(W.words[p >> 5], W.words[(p >> 5) + 1], p & 31u) & mask_lo(s);
             *out++ = run;
             p += s;
             m--;
           }
           for (; m; m--) {
-            const uint32_t x = __funnelshift_r(sm.words[p >> 5], sm.words[(p >> 5) + 1], p & 31u) & mw;
+            const uint32_t x = __funnelshift_r(W.words[p >> 5], W.words[(p >> 5) + 1], p & 31u) & mw;
             p += w;
             if (IDM == ID_LOCAL_GAP) { run += x; *out++ = run; }
             else *out++ = x;
@@ -1433,35 +1446,27 @@ __global__ void __launch_bounds__(TNT, 4) k_dec_local(GView g, DecArgs a) {
         }
       }
       if (IDM == ID_LOCAL_GAP) {
-        // inclusive segmented scan of (lastf, lastv) over the threads, after the
-        // window's carry (the absolute ID of field W0 - 1 when the window starts mid-vertex)
+        // inclusive segmented scan of (lastf, lastv) over the lanes, after the
+        // window's carry (the absolute ID of field W0 - 1 when W0 is inside a vertex)
+        const uint32_t cf = fpre[ja] < W0 ? 1u : 0u, cv = cf ? wcarry : 0u;
         uint32_t xf = lastf, xv = lastv;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
           const uint32_t ef = __shfl_up_sync(LG_FULL_MASK, xf, o), ev = __shfl_up_sync(LG_FULL_MASK, xv, o);
           if (lane >= (uint32_t)o) seg_after(xf, xv, ef, ev);
         }
-        if (lane == 31) { sm.wsf[wid] = xf; sm.wsv[wid] = xv; }
-        __syncthreads();
-        uint32_t pf = W0 > F0 ? 1u : 0u, pv = W0 > F0 ? carry_in : 0u;
-        for (uint32_t ww = 0; ww < wid; ww++) {
-          uint32_t tf = sm.wsf[ww], tv = sm.wsv[ww];
-          seg_after(tf, tv, pf, pv);
-          pf = tf;
-          pv = tv;
-        }
-        uint32_t lf2 = __shfl_up_sync(LG_FULL_MASK, xf, 1), lv2 = __shfl_up_sync(LG_FULL_MASK, xv, 1);
-        if (lane == 0) { lf2 = 0; lv2 = 0; }
-        seg_after(lf2, lv2, pf, pv);
-        for (uint32_t f = fa; f < pend; f++) sm.stage[f - W0] += lv2;
-        if (threadIdx.x == TNT - 1) {
-          seg_after(xf, xv, pf, pv);
-          sm.rcarry = xv;  // the absolute ID of the window's last field
-        }
+        uint32_t lf = __shfl_up_sync(LG_FULL_MASK, xf, 1), lv = __shfl_up_sync(LG_FULL_MASK, xv, 1);
+        if (lane == 0) { lf = 0; lv = 0; }
+        seg_after(lf, lv, cf, cv);
+        for (uint32_t f = fa; f < pend; f++) W.stage[f - W0] += lv;
+        seg_after(xf, xv, cf, cv);
+        wcarry = __shfl_sync(LG_FULL_MASK, xv, 31);  // the absolute ID of the window's last field
       }
-      __syncthreads();
-      for (uint32_t f = threadIdx.x; f < Fw; f += TNT) __stcs(a.ids + delta + W0 + f, sm.stage[f]);
-      __syncthreads();
+      __syncwarp();
+      const uint64_t dst0 = sm.rdelta[q] + W0;
+      for (uint32_t x = lane; x < Fw; x += 32) __stcs(a.ids + dst0 + x, W.stage[x]);
+      __syncwarp();
+      W0 += Fw;
     }
   }
 }
