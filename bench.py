@@ -63,10 +63,10 @@ WORKLOADS = {
     "rmat16": ("R-MAT scale 16, edge factor 16, (a,b,c)=(.57,.19,.19); global 16-bit IDs + packed offsets",
                lambda: gen.rmat_s16_ef16(seed=1),
                dict(id_mode=0, off_mode=0, relabel=False), 64, 20),
-    "rmat27": ("R-MAT scale 27, edge factor 16, weights in [1,255] at 8 bits; global 27-bit IDs + "
-               "Elias-Fano offsets",
+    "rmat27": ("R-MAT scale 27, edge factor 16, (a,b,c)=(.57,.19,.19), weights in [1,255] at 8 bits; DM relabel "
+               "(degree descending, Section 5.6) + global 27-bit IDs + Elias-Fano offsets",
                None,  # built on the device (gen.rmat_gpu)
-               dict(id_mode=0, off_mode=1, relabel=False, weight_bits=8), 16, 20),
+               dict(id_mode=0, off_mode=1, relabel=True, weight_bits=8), 16, 20),
     "batch": ("batch of 4,096 independent R-MAT graphs, (a,b,c)=(.57,.19,.19), scale floor(U[8,17)), edge "
               "factor uniform in [4,32], seeded; per-graph global IDs at bits(n-1) + packed offsets at "
               "bits(arcs); encode + BFS from vertex 0 + 10 PageRank iterations in one graph-captured "
@@ -81,28 +81,36 @@ WORKLOADS["serve"] = ("serving: 3 resident R-MAT graphs (scales 20, 22, 24, edge
                       None, None, 1, 10)
 SERVE_SCALES, SERVE_SEED, SERVE_RATES = (20, 22, 24), 4, (0.25, 0.5, 0.9)
 WORKLOADS["sssp"] = ("SSSP (delta-stepping, delta 32) from 4 sources on R-MAT scale 27, edge factor 16, weights in "
-                     "[1,255] at 8 bits; global 27-bit IDs + Elias-Fano offsets; CSR-32 with 32-bit weights beside it",
-                     None, dict(id_mode=0, off_mode=1, relabel=False, weight_bits=8), 4, 0)
+                     "[1,255] at 8 bits; DM relabel + global 27-bit IDs + Elias-Fano offsets; CSR-32 with 32-bit "
+                     "weights in the same order beside it",
+                     None, dict(id_mode=0, off_mode=1, relabel=True, weight_bits=8), 4, 0)
 SSSP_DELTA = 32
 
 
 class Workload:
     """The input graph on the device (and on the host, made on demand)."""
 
-    def __init__(self, name, dev, log2n=None):
+    def __init__(self, name, dev, log2n=None, relabel=None):
         import torch
 
         self.desc, make, self.opts, self.S, self.T = WORKLOADS[name]
+        if relabel is not None and self.opts is not None and bool(self.opts.get("relabel")) != relabel:
+            self.opts = dict(self.opts, relabel=relabel)
+            self.desc = self.desc + ("; DM relabel (Section 5.6)" if relabel else "; no relabel")
+        scale = 27
         if log2n is not None:
-            if name != "community":
-                raise SystemExit("--profile-log2n applies to the community workload only")
-            make = lambda: gen.community_2p24(seed=2, log2n=log2n)  # noqa: E731
+            if name == "community":
+                make = lambda: gen.community_2p24(seed=2, log2n=log2n)  # noqa: E731
+            elif name == "rmat27":
+                scale = log2n  # a smaller R-MAT of the same recipe (profiling captures)
+            else:
+                raise SystemExit("--profile-log2n applies to the community and rmat27 workloads")
         t0 = time.time()
         if make is None:
-            rp, col, w = gen.rmat_gpu(27, 16, seed=5, weighted=True)
+            rp, col, w = gen.rmat_gpu(scale, 16, seed=5, weighted=True)
             self.rp_d, self.col_d, self.w_d = rp, col, w
             self._host = None
-            self.name = "rmat_s27_ef16_seed5"
+            self.name = f"rmat_s{scale}_ef16_seed5"
         else:
             g0 = make()
             self._host = (g0.row_ptr, g0.col, g0.weights if "weight_bits" in self.opts else None)
@@ -342,8 +350,8 @@ def time_decode(lg, wl, dev, reps=5):
     peak, _ = peaks()
     t = float(np.median(ms))
     alg = (st["bits_A"] + st["bits_O"]) // 8 + 8 * (wl.n + 1) + 4 * wl.arcs
-    kern = ("k_dec_degrees (row pass) + k_dec_flat (records in arc order)" if wl.opts["id_mode"] == 0 else
-            "k_dec_degrees + scan + k_dec_local (tile rounds staged in shared memory)")
+    kern = ("k_dec_flat: row offsets from the offsets + records in arc order, one launch" if wl.opts["id_mode"] == 0
+            else "k_dec_local: row offsets by look-back + per-warp windows staged in shared memory, one launch")
     return {"kernel": f"lg_decode: whole graph to 32-bit CSR ({kern})", "ms": t, "algorithmic_bytes": alg,
             "achieved_gbs": alg / (t * 1e-3) / 1e9, "frac": alg / (t * 1e-3) / 1e9 / peak, "peak_gbs": peak}
 
@@ -535,7 +543,7 @@ def run_lg(args, rank, world):
             import torch.distributed as dist
             dist.barrier()
 
-    wl = Workload(args.workload, dev)
+    wl = Workload(args.workload, dev, relabel=args.relabel)
     arms = time_arms(lg, wl, args.steps, args.warmup, dev, barrier, rank)
     dec = time_decode(lg, wl, dev)
     e2e = time_e2e(lg, wl, args.steps, args.warmup, dev, barrier)
@@ -583,8 +591,12 @@ def run_lg(args, rank, world):
     out["detail"]["gather_ceiling"] = {
         "probe": "lg_probe_gather: uniformly random 4-byte gathers + a coalesced index stream",
         "contrib_size": ceil_full, "l2_resident_64MiB": ceil_l2, "pr_gathers_per_s": pr_rate,
-        "pr_frac_of_ceiling_at_contrib_size": pr_rate / ceil_full["g_gathers_per_s"]}
-    out["roofline"]["gather_ceiling_frac"] = pr_rate / ceil_full["g_gathers_per_s"]
+        "pr_vs_uniform_at_contrib_size": pr_rate / ceil_full["g_gathers_per_s"],
+        "pr_frac_of_l2_resident_ceiling": pr_rate / ceil_l2["g_gathers_per_s"],
+        "note": "PageRank gathers one 4-byte contribution per arc; the L2-resident rate is the ceiling when the "
+                "gathered rows stay in L2 (DM order keeps the hubs' rows there), the uniform rate at the full array "
+                "size is the rate without any locality"}
+    out["roofline"]["gather_ceiling_frac"] = pr_rate / ceil_l2["g_gathers_per_s"]
     out["clocks"] = res["clocks"]
     if args.workload == "rmat27" and not args.no_secondary:
         # the local-gap / DM workload beside the headline: the <= 75 % bytes
@@ -932,7 +944,7 @@ def run_sssp(args, rank, world):
     log(f"generated rmat_s27_ef16_seed5 weighted: n={n} arcs={arcs} in {time.time() - t0:.1f}s")
     stream = torch.cuda.current_stream(dev)
     arms = {}
-    for name, o in (("log(graph)", opts), ("csr32", dict(id_mode=3))):
+    for name, o in (("log(graph)", opts), ("csr32", dict(id_mode=3, relabel=opts.get("relabel", False)))):
         g = lg.lg_encode(rp, col, w, **o)
         st = g.stats()
         dist = torch.empty(n, dtype=torch.int64, device=dev)
@@ -1127,10 +1139,24 @@ def profile_pass(args):
     import paper_2010_15879_gb300 as lg
 
     lg.load(auto_build=True)
-    wl = Workload(args.workload, torch.device("cuda", 0), log2n=args.profile_log2n)
+    wl = Workload(args.workload, torch.device("cuda", 0), log2n=args.profile_log2n, relabel=args.relabel)
     opts, T = wl.opts, (args.pr_iters if args.pr_iters is not None else wl.T)
     rp, col, w = wl.rp_d, wl.col_d, wl.w_d
     src = torch.from_numpy(wl.sources().view(np.int32)).cuda()
+    if args.profile == "decode":
+        g = lg.lg_encode(rp, col, w, **opts)
+        for _ in range(3):
+            lg.lg_decode(g)
+        torch.cuda.synchronize()
+        log(f"profile pass decode: {g.stats()['arcs']} arcs")
+        g.free()
+        return
+    if args.profile == "encode":
+        g = lg.lg_encode(rp, col, w, **opts)
+        torch.cuda.synchronize()
+        log(f"profile pass encode: {g.stats()['bits_per_arc']:.2f} bits/arc")
+        g.free()
+        return
     arms = {"lg": opts, "csr32": dict(id_mode=3, relabel=False)}
     for name in (["lg", "csr32"] if args.profile == "both" else [args.profile]):
         g = lg.lg_encode(rp, col, w, **arms[name])
@@ -1323,13 +1349,17 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rmat27",
                     help="default: R-MAT scale 27 (the largest configuration that fits one GPU)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--relabel", type=int, choices=[0, 1], default=None,
+                    help="override the workload's DM relabeling (Section 5.6): 1 on, 0 off")
     ap.add_argument("--no-secondary", action="store_true",
                     help="rmat27: skip the community 2^24 (local-gap IDs, DM relabel) section of detail")
-    ap.add_argument("--profile", choices=["lg", "csr32", "both"], default=None,
-                    help="run one untimed pass of the hot path (for ncu) and exit")
+    ap.add_argument("--profile", choices=["lg", "csr32", "both", "decode", "encode"], default=None,
+                    help="run one untimed pass of the hot path (for ncu) and exit: lg / csr32 / both = encode + "
+                         "BFS + PageRank of that arm; decode = encode + 3 x lg_decode; encode = one encode")
     ap.add_argument("--pr-iters", type=int, default=None, help="PageRank iterations in --profile mode")
     ap.add_argument("--profile-log2n", type=int, default=None,
-                    help="--profile mode of the community workload on a 2^k-vertex graph (a small capture case)")
+                    help="--profile mode of the community / rmat27 workload on a 2^k-vertex graph (a small capture "
+                         "case)")
     ap.add_argument("--batch-count", type=int, default=None, help="graphs in --profile mode of the batch workload")
     ap.add_argument("--serve-requests", type=int, default=100000, help="requests per rate (serve workload)")
     ap.add_argument("--serve-probe-requests", type=int, default=30000,

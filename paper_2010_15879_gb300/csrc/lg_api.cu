@@ -434,10 +434,10 @@ extern "C" lg_status lg_decode(const lg_graph* g, uint64_t* row_ptr, uint32_t* c
   a.ids = col;
   a.weights = weights;
   if (g->id_mode == ID_GLOBAL || g->id_mode == ID_CSR32) {
-    // records are in arc order: the offsets are the row offsets
+    // records are in arc order: the offsets are the row offsets (one launch
+    // writes both)
     a.row_out = row_ptr;
-    LG_TRY(ops->dec_rows(v, a, st));
-    if (g->arcs) LG_TRY(ops->dec_all(v, a, st));
+    LG_TRY(ops->dec_all(v, a, st));
     return LG_OK;
   }
   // local IDs: one launch (row offsets by a single-pass look-back over the

@@ -285,6 +285,29 @@ __device__ __forceinline__ T block_excl_scan(T v, T& total, T* tmp) {
   return pre;
 }
 
+// Two exclusive scans over a block of NT threads in one pass (one tree, two
+// values); `tmp` holds 2 * NT/32 elements of shared memory.
+template <typename T, int NT>
+__device__ __forceinline__ void block_excl_scan2(T a, T b, T& pa, T& pb, T& ta, T& tb, T* tmp) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  constexpr int NW = NT / 32;
+  const T xa = warp_incl_scan(a), xb = warp_incl_scan(b);
+  if (lane == 31) { tmp[wid] = xa; tmp[NW + wid] = xb; }
+  __syncthreads();
+  if (wid == 0) {
+    T ya = lane < NW ? tmp[lane] : T(0), yb = lane < NW ? tmp[NW + lane] : T(0);
+    ya = warp_incl_scan(ya);
+    yb = warp_incl_scan(yb);
+    if (lane < NW) { tmp[lane] = ya; tmp[NW + lane] = yb; }
+  }
+  __syncthreads();
+  pa = (wid > 0 ? tmp[wid - 1] : T(0)) + xa - a;
+  pb = (wid > 0 ? tmp[NW + wid - 1] : T(0)) + xb - b;
+  ta = tmp[NW - 1];
+  tb = tmp[2 * NW - 1];
+  __syncthreads();
+}
+
 __device__ __forceinline__ void set_err(int* err, int bit) { atomicOr(err, bit); }
 
 // ---------------------------------------------------------------------------

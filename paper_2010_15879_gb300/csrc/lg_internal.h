@@ -210,7 +210,6 @@ struct TravOps {
   cudaError_t (*plan_carry)(const GView&, const PlanArgs&, cudaStream_t);
   cudaError_t (*ppr_pull)(const GView&, const PprArgs&, cudaStream_t);
   cudaError_t (*ppr_join)(const GView&, float* cin, uint32_t slot, uint32_t src, cudaStream_t);
-  cudaError_t (*dec_rows)(const GView&, const DecArgs&, cudaStream_t);
   cudaError_t (*dec_all)(const GView&, const DecArgs&, cudaStream_t);
 };
 

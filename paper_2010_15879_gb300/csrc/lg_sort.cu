@@ -653,7 +653,8 @@ template <bool VALS>
 __global__ void __launch_bounds__(256) k_dm_rows(const uint64_t* __restrict__ rp, const uint32_t* __restrict__ col,
                                                  const uint32_t* __restrict__ w, const uint32_t* __restrict__ inv,
                                                  const uint32_t* __restrict__ perm, const uint64_t* __restrict__ nrp,
-                                                 uint32_t* __restrict__ ncol, uint32_t* __restrict__ nw, uint64_t n) {
+                                                 uint32_t* __restrict__ ncol, uint32_t* __restrict__ nw, uint64_t n,
+                                                 int skip_big) {
   extern __shared__ uint32_t dsm[];  // 8 warps x 32 slots of keys, then of weights
   const int lane = threadIdx.x & 31;
   uint32_t* sk = dsm + (threadIdx.x >> 5) * 32 * SROW;
@@ -708,6 +709,7 @@ __global__ void __launch_bounds__(256) k_dm_rows(const uint64_t* __restrict__ rp
       }
     }
     __syncwarp();
+    if (skip_big) continue;  // k_dm_big copies the rows of more than SEG_SMALL arcs
     for (uint32_t t = __ballot_sync(LG_FULL_MASK, !small); t; t &= t - 1) {
       const int q = __ffs(t) - 1;
       const uint64_t lq = __shfl_sync(LG_FULL_MASK, lo, q);
@@ -717,6 +719,77 @@ __global__ void __launch_bounds__(256) k_dm_rows(const uint64_t* __restrict__ rp
         const uint32_t cc = ldg_hint(col + lq + k, pstream);
         __stcs(ncol + oq + k, ldg_hint(perm + cc, pkeep));
         if (VALS) __stcs(nw + oq + k, ldg_hint(w + lq + k, pstream));
+      }
+    }
+  }
+}
+
+// Rows of more than SEG_SMALL arcs in DM order.  Labels go by degree
+// descending, so these rows are the first K new rows and their arcs the prefix
+// [0, nrp[K]) of the new CSR: the prefix is cut into chunks of DM_CHUNK arcs
+// spread evenly over the grid (a hub no longer rests on one warp).  chunk_row[c]
+// is the row holding arc c * DM_CHUNK; a lane walks 8 arcs 32 apart, all their
+// loads and perm lookups in flight together.
+constexpr uint32_t DM_CHUNK = 256;
+
+// K = the number of rows of more than SEG_SMALL arcs (degrees are descending)
+__global__ void k_dm_count_big(const uint32_t* __restrict__ newdeg, uint64_t n, unsigned long long* __restrict__ K) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    if (newdeg[i] > SEG_SMALL && (i + 1 == n || newdeg[i + 1] <= SEG_SMALL)) *K = i + 1;
+}
+__global__ void k_dm_chunk_rows(const uint64_t* __restrict__ nrp, uint64_t n, const unsigned long long* __restrict__ K,
+                                uint32_t* __restrict__ chunk_row) {
+  const uint64_t k = *K;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k && i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t c0 = (nrp[i] + DM_CHUNK - 1) / DM_CHUNK, c1 = (nrp[i + 1] + DM_CHUNK - 1) / DM_CHUNK;
+    for (uint64_t c = c0; c < c1; c++) chunk_row[c] = (uint32_t)i;
+  }
+}
+template <bool VALS>
+__global__ void __launch_bounds__(256) k_dm_big(const uint64_t* __restrict__ rp, const uint32_t* __restrict__ col,
+                                                const uint32_t* __restrict__ w, const uint32_t* __restrict__ inv,
+                                                const uint32_t* __restrict__ perm, const uint64_t* __restrict__ nrp,
+                                                const unsigned long long* __restrict__ K,
+                                                const uint32_t* __restrict__ chunk_row, uint32_t* __restrict__ ncol,
+                                                uint32_t* __restrict__ nw) {
+  constexpr int T = DM_CHUNK / 32;
+  const int lane = threadIdx.x & 31;
+  const uint64_t E = nrp[*K];
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  const uint64_t pstream = policy_stream(), pkeep = policy_keep();
+  for (uint64_t c = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c * DM_CHUNK < E; c += warps) {
+    uint32_t i = chunk_row[c];
+    uint64_t rs = nrp[i], re = nrp[i + 1], old = rp[inv[i]];
+    uint32_t cc[T], wv[T];
+#pragma unroll
+    for (int t = 0; t < T; t++) {
+      const uint64_t p = c * DM_CHUNK + lane + 32u * t;
+      cc[t] = 0;
+      wv[t] = 0;
+      if (p < E) {
+        while (re <= p) {  // next row (each holds more than SEG_SMALL arcs)
+          i++;
+          rs = re;
+          re = nrp[i + 1];
+          old = rp[inv[i]];
+        }
+        cc[t] = ldg_hint(col + old + (p - rs), pstream);
+        if (VALS) wv[t] = ldg_hint(w + old + (p - rs), pstream);
+      }
+    }
+    uint32_t pv[T];
+#pragma unroll
+    for (int t = 0; t < T; t++) {
+      const uint64_t p = c * DM_CHUNK + lane + 32u * t;
+      pv[t] = p < E ? ldg_hint(perm + cc[t], pkeep) : 0u;
+    }
+#pragma unroll
+    for (int t = 0; t < T; t++) {
+      const uint64_t p = c * DM_CHUNK + lane + 32u * t;
+      if (p < E) {
+        __stcs(ncol + p, pv[t]);
+        if (VALS) __stcs(nw + p, wv[t]);
       }
     }
   }
@@ -819,18 +892,46 @@ cudaError_t enc_dm_relabel(const uint64_t* rp, const uint32_t* col, const uint32
     count_launch();
     e = scan_excl_u32(newdeg, n, nrp, stmp, st);
   }
+  // DM order (degree descending): the rows of more than SEG_SMALL arcs form a
+  // prefix and go to k_dm_big; the greedy order mixes sizes, so k_dm_rows
+  // copies its big rows itself
+  const int split_big = mode != 2;
+  unsigned long long* dK = nullptr;
+  uint32_t* chunk_row = nullptr;
+  if (e == cudaSuccess && split_big) {
+    e = lg::pool_alloc((void**)&dK, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = lg::pool_alloc((void**)&chunk_row, (arcs / DM_CHUNK + 2) * sizeof(uint32_t), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dK, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) {
+      k_dm_count_big<<<grid_for(n, 256, 152 * 32), 256, 0, st>>>(newdeg, n, dK);
+      count_launch();
+      k_dm_chunk_rows<<<grid_for(n, 256, 152 * 32), 256, 0, st>>>(nrp, n, dK, chunk_row);
+      count_launch();
+      e = cudaGetLastError();
+    }
+  }
   if (e == cudaSuccess) {
     const size_t smem = (size_t)8 * 32 * SROW * sizeof(uint32_t) * (w ? 2 : 1);
     if (w) {
       e = cudaFuncSetAttribute(k_dm_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e == cudaSuccess)
-        k_dm_rows<true><<<grid_for(n, 256, 152 * 16), 256, smem, st>>>(rp, col, w, inv_perm, perm, nrp, ncol, nw, n);
+        k_dm_rows<true><<<grid_for(n, 256, 152 * 16), 256, smem, st>>>(rp, col, w, inv_perm, perm, nrp, ncol, nw, n,
+                                                                       split_big);
     } else {
-      k_dm_rows<false><<<grid_for(n, 256, 152 * 16), 256, smem, st>>>(rp, col, w, inv_perm, perm, nrp, ncol, nw, n);
+      k_dm_rows<false><<<grid_for(n, 256, 152 * 16), 256, smem, st>>>(rp, col, w, inv_perm, perm, nrp, ncol, nw, n,
+                                                                      split_big);
     }
     count_launch();
     if (e == cudaSuccess) e = cudaGetLastError();
   }
+  if (e == cudaSuccess && split_big) {
+    if (w) k_dm_big<true><<<152 * 8, 256, 0, st>>>(rp, col, w, inv_perm, perm, nrp, dK, chunk_row, ncol, nw);
+    else k_dm_big<false><<<152 * 8, 256, 0, st>>>(rp, col, w, inv_perm, perm, nrp, dK, chunk_row, ncol, nw);
+    count_launch();
+    e = cudaGetLastError();
+  }
+  if (dK) cudaFreeAsync(dK, st);
+  if (chunk_row) cudaFreeAsync(chunk_row, st);
   // rows of <= 32 arcs left k_dm_rows sorted
   if (e == cudaSuccess) e = segmented_sort(ncol, w ? nw : nullptr, nrp, n, arcs, max_deg, st, true, host_bits(n - 1));
   cudaFreeAsync(keys, st); cudaFreeAsync(k2, st); cudaFreeAsync(v2, st); cudaFreeAsync(newdeg, st);

@@ -1034,10 +1034,10 @@ __global__ void __launch_bounds__(256) k_nbr_decode(GView g, NbrArgs a) {
 // applied to all vertices) written to a CSR in stored order.
 //
 // Global IDs (and CSR-32) keep their records in arc order, so record j is
-// col[j] and the offsets x_v are the row offsets: a row pass writes row_ptr
-// from the offsets (one tile decode per 512 vertices) and a flat pass maps
-// records to IDs, consecutive threads on consecutive records (coalesced
-// stream reads and coalesced writes, no vertex lookup).  Local IDs: one
+// col[j] and the offsets x_v are the row offsets: one launch writes row_ptr
+// from the offsets (a tile decode per 512 vertices) and maps records to IDs,
+// consecutive threads on consecutive records (coalesced stream reads and
+// coalesced writes, no vertex lookup).  Local IDs: one
 // kernel, described above k_dec_local.
 //
 // Local IDs: a degree pass and a scan give the row offsets, then tiles of TV
@@ -1051,19 +1051,6 @@ __global__ void __launch_bounds__(256) k_nbr_decode(GView g, NbrArgs a) {
 // field has been read) supplies the missing prefix.  Heavy vertices come from
 // the heavy schedule, a warp per item, a lane per field.
 // ===========================================================================
-// row pass of global-ID / CSR-32 graphs: the offsets are the row offsets
-template <int OFF>
-__global__ void __launch_bounds__(TNT) k_dec_rows(GView g, DecArgs a) {
-  __shared__ uint64_t xs[TV + 1];
-  __shared__ TileScratch ts;
-  const uint64_t v0 = (uint64_t)blockIdx.x * TV;
-  const int cnt = (int)min((uint64_t)TV, g.n - v0);
-  tile_offsets<OFF>(g, v0, cnt, xs, ts);
-  __syncthreads();
-  for (int i = threadIdx.x; i < cnt; i += TNT) a.row_out[v0 + i] = xs[i];
-  if (v0 + (uint64_t)cnt == g.n && threadIdx.x == 0) a.row_out[g.n] = xs[cnt];
-}
-
 template <int IDM, int U>
 __device__ __forceinline__ void dec_fields(const GView& g, const DecArgs& a, uint64_t start, uint32_t w, uint32_t f0,
                                            uint32_t f1, uint32_t carry, uint64_t o) {
@@ -1079,25 +1066,39 @@ __device__ __forceinline__ void dec_fields(const GView& g, const DecArgs& a, uin
   }
 }
 
-constexpr int DEC_FLAT_U = 4;  // records per thread in flight (flat decode)
+constexpr int DEC_FLAT_U = 8;  // records per thread in flight (flat decode)
 
-// Flat decode of global-ID records (or CSR-32 IDs): thread t of the grid takes
-// records j = base + t + k * blockDim.x for k < DEC_FLAT_U.
-template <int IDM>
-__global__ void __launch_bounds__(256) k_dec_flat(GView g, DecArgs a) {
+// Flat decode of global-ID records (or CSR-32 IDs), one launch, one block per
+// tile of TV vertices: the block writes the tile's row_ptr entries from the
+// offsets, then maps its share of the records (arcs / tiles, rounded up to
+// whole warps of DEC_FLAT_U) to IDs -- consecutive threads on consecutive
+// records, coalesced reads and writes -- so every block mixes the latency-bound
+// offset decode with streaming work.
+template <int IDM, int OFF>
+__global__ void __launch_bounds__(256) k_dec_flat(GView g, DecArgs a, uint64_t per_block) {
+  {
+    __shared__ uint64_t xs[TV + 1];
+    __shared__ TileScratch ts;
+    const uint64_t v0 = (uint64_t)blockIdx.x * TV;
+    const int cnt = (int)min((uint64_t)TV, g.n - v0);
+    tile_offsets<OFF>(g, v0, cnt, xs, ts);
+    __syncthreads();
+    for (int i = threadIdx.x; i < cnt; i += TNT) a.row_out[v0 + i] = xs[i];
+    if (v0 + (uint64_t)cnt == g.n && threadIdx.x == 0) a.row_out[g.n] = xs[cnt];
+  }
   const uint64_t arcs = g.arcs;
-  const uint64_t step = (uint64_t)gridDim.x * blockDim.x * DEC_FLAT_U;
+  const uint64_t jb = (uint64_t)blockIdx.x * per_block, je = min(arcs, jb + per_block);
   const uint32_t r = IDM == ID_CSR32 ? 32u : g.r;
   const uint32_t s = IDM == ID_CSR32 ? 32u : g.s;
   const uint32_t ms = mask_lo(s), mw = mask_lo(g.omega);
   const bool want_w = a.weights != nullptr;
-  for (uint64_t j0 = (uint64_t)blockIdx.x * blockDim.x * DEC_FLAT_U + threadIdx.x; j0 < arcs; j0 += step) {
+  for (uint64_t j0 = jb + threadIdx.x; j0 < je; j0 += (uint64_t)blockDim.x * DEC_FLAT_U) {
     uint32_t id[DEC_FLAT_U], wt[DEC_FLAT_U];
 #pragma unroll
     for (int k = 0; k < DEC_FLAT_U; k++) {
       const uint64_t j = j0 + (uint64_t)k * blockDim.x;
       id[k] = 0; wt[k] = 0;
-      if (j < arcs) {
+      if (j < je) {
         if (IDM == ID_CSR32) {
           id[k] = __ldcs(g.A32 + j);
           if (want_w && g.W32) wt[k] = __ldcs(g.W32 + j);
@@ -1119,7 +1120,7 @@ __global__ void __launch_bounds__(256) k_dec_flat(GView g, DecArgs a) {
 #pragma unroll
     for (int k = 0; k < DEC_FLAT_U; k++) {
       const uint64_t j = j0 + (uint64_t)k * blockDim.x;
-      if (j < arcs) {
+      if (j < je) {
         __stcs(a.ids + j, id[k]);
         if (want_w) __stcs(a.weights + j, wt[k]);
       }
@@ -1161,6 +1162,7 @@ struct DecSmem {
   uint64_t rdelta[TV];         // per run of light vertices: output index - light field index
   uint16_t rfirst[TV + 1];     // per run: its first light index
   uint64_t base;               // arcs of all earlier tiles
+  uint64_t scan2[2 * (TNT / 32)];
   uint32_t nruns, ticket, ok;
 };
 
@@ -1269,7 +1271,7 @@ __global__ void __launch_bounds__(TNT, 4) k_dec_local(GView g, DecArgs a) {
   const int cnt = (int)min((uint64_t)TV, g.n - v0);
   tile_offsets<OFF>(g, v0, cnt, ts.xs, ts.ts);
   __syncthreads();
-  uint32_t lc = 0, lf = 0;
+  uint32_t lc = 0, lf = 0, hc = 0;
   uint64_t all = 0;
   bool light[TV / TNT];
   uint32_t dq[TV / TNT];
@@ -1285,11 +1287,17 @@ __global__ void __launch_bounds__(TNT, 4) k_dec_local(GView g, DecArgs a) {
       dq[q] = d;
       all += d;
       if (d > 0 && d <= g.heavy_min) { light[q] = true; lc++; lf += d; }
+      hc += d > g.heavy_min;
     }
   }
-  uint64_t ltot, atot;
-  const uint64_t lpre = block_excl_scan<uint64_t, TNT>(((uint64_t)lc << 32) | lf, ltot, ts.red64);
-  const uint64_t apre = block_excl_scan<uint64_t, TNT>(all, atot, ts.red64);  // xs reads are done
+  // one pass over the block: (heavy count, light count, light fields) packed
+  // into 16 / 16 / 32 bits, and the sum of all degrees
+  uint64_t lpre, apre, ltot, atot;
+  block_excl_scan2<uint64_t, TNT>(((uint64_t)hc << 48) | ((uint64_t)lc << 32) | lf, all, lpre, apre, ltot, atot,
+                                  sm.scan2);  // xs reads are done
+  const bool no_heavy = (ltot >> 48) == 0;
+  ltot &= (1ull << 48) - 1;
+  lpre &= (1ull << 48) - 1;
   uint64_t* pre_all = ts.xs;  // reused: in-tile exclusive prefix of all degrees
   {
     uint32_t ci = (uint32_t)(lpre >> 32), cf = (uint32_t)lpre;
@@ -1341,7 +1349,14 @@ __global__ void __launch_bounds__(TNT, 4) k_dec_local(GView g, DecArgs a) {
   const uint32_t nl = ts.nlight;
   if (nl == 0) return;
   // ---- runs of light vertices with contiguous output rows (a heavy vertex breaks a run)
-  {
+  if (no_heavy) {  // one run
+    if (threadIdx.x == 0) {
+      sm.nruns = 1;
+      sm.rfirst[0] = 0;
+      sm.rfirst[1] = (uint16_t)nl;
+      sm.rdelta[0] = base + pre_all[ts.clist[0]];
+    }
+  } else {
     uint32_t fl[TV / TNT], c = 0;
     uint64_t dl[TV / TNT];
 #pragma unroll
@@ -1645,22 +1660,13 @@ cudaError_t launch_ppr_join(const GView& g, float* cin, uint32_t slot, uint32_t 
 }
 
 template <int IDM, int OFF>
-cudaError_t launch_dec_rows(const GView& g, const DecArgs& a, cudaStream_t st) {
-  if constexpr (IDM == ID_GLOBAL || IDM == ID_CSR32) {
-    if (g.n == 0) return cudaSuccess;
-    k_dec_rows<OFF><<<tiles_of(g.n), TNT, 0, st>>>(g, a);
-    count_launch();
-    return cudaGetLastError();
-  } else {
-    return cudaErrorNotSupported;  // local IDs: k_dec_local writes the row offsets
-  }
-}
-template <int IDM, int OFF>
 cudaError_t launch_dec_all(const GView& g, const DecArgs& a, cudaStream_t st) {
-  if (g.n == 0 || ((IDM == ID_GLOBAL || IDM == ID_CSR32) && g.arcs == 0)) return cudaSuccess;
+  if (g.n == 0) return cudaSuccess;
   if constexpr (IDM == ID_GLOBAL || IDM == ID_CSR32) {
-    const uint64_t per_block = 256ull * DEC_FLAT_U;
-    k_dec_flat<IDM><<<grid_for(g.arcs, (unsigned)per_block, 152 * 16), 256, 0, st>>>(g, a);
+    const uint64_t tiles = tiles_of(g.n);
+    const uint64_t unit = 256ull * DEC_FLAT_U;
+    const uint64_t per_block = (g.arcs + tiles - 1) / tiles;
+    k_dec_flat<IDM, OFF><<<(unsigned)tiles, 256, 0, st>>>(g, a, (per_block + unit - 1) / unit * unit);
   } else {
     const cudaError_t e = cudaFuncSetAttribute(k_dec_local<IDM, OFF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)sizeof(DecSmem));
@@ -1677,8 +1683,7 @@ const TravOps* make_ops() {
       &launch_pr_init<IDM, OFF>,    &launch_pr_pull<IDM, OFF>,     &launch_bfs_pull<IDM, OFF>,
       &launch_bfs_push<IDM, OFF>,   &launch_nbr_degrees<IDM, OFF>, &launch_nbr_decode<IDM, OFF>,
       &launch_plan_count<IDM, OFF>, &launch_plan_fill<IDM, OFF>,   &launch_plan_carry<IDM, OFF>,
-      &launch_ppr_pull<IDM, OFF>,   &launch_ppr_join<IDM, OFF>,   &launch_dec_rows<IDM, OFF>,
-      &launch_dec_all<IDM, OFF>,
+      &launch_ppr_pull<IDM, OFF>,   &launch_ppr_join<IDM, OFF>,   &launch_dec_all<IDM, OFF>,
   };
   return &ops;
 }
