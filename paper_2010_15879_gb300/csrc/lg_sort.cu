@@ -545,6 +545,102 @@ static cudaError_t seg_sort_big(uint32_t* keys, uint32_t* vals, const uint64_t* 
   return e;
 }
 
+// Rows of 513..4096 keys: a CTA per row, a stable LSD radix sort in shared
+// memory (8-bit digits, ceil(key_bits / 8) passes).  Per pass: a digit
+// histogram, its exclusive scan, then rounds of RS_NT keys ranked as in
+// k_rs_scatter (a match among the warp's lanes, the warps before, the keys of
+// the digit placed in earlier rounds).  About 4 compare-free steps per key and
+// pass instead of a bitonic network's log2(d) (log2(d) + 1) / 2 stages.
+constexpr uint32_t SEG_RADIX_MAX = 4096;
+
+template <bool VALS>
+struct SegRadixSmem {
+  uint32_t k[2][SEG_RADIX_MAX];
+  uint32_t v[VALS ? 2 : 1][VALS ? SEG_RADIX_MAX : 1];
+  uint32_t wcnt[RS_NW][256];
+  uint32_t base[256], seen[256], red[RS_NW];
+};
+
+template <bool VALS>
+__global__ void __launch_bounds__(RS_NT) k_seg_radix(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                                     const uint64_t* __restrict__ off,
+                                                     const uint32_t* __restrict__ list, uint32_t nlist,
+                                                     uint32_t passes) {
+  extern __shared__ __align__(16) unsigned char sr_raw[];
+  SegRadixSmem<VALS>& sm = *reinterpret_cast<SegRadixSmem<VALS>*>(sr_raw);
+  const int w = threadIdx.x >> 5;
+  for (uint32_t li = blockIdx.x; li < nlist; li += gridDim.x) {
+    const uint64_t lo = off[list[li]];
+    const uint32_t d = (uint32_t)(off[list[li] + 1] - lo);
+    for (uint32_t i = threadIdx.x; i < d; i += RS_NT) {
+      sm.k[0][i] = keys[lo + i];
+      if (VALS) sm.v[0][i] = vals[lo + i];
+    }
+    __syncthreads();
+    int cur = 0;
+    for (uint32_t p = 0; p < passes; p++) {
+      const uint32_t shift = 8 * p;
+      sm.seen[threadIdx.x] = 0;
+      sm.base[threadIdx.x] = 0;
+      __syncthreads();
+      for (uint32_t i = threadIdx.x; i < d; i += RS_NT) atomicAdd(&sm.base[(sm.k[cur][i] >> shift) & 255u], 1u);
+      __syncthreads();
+      {
+        uint32_t total;
+        const uint32_t c = sm.base[threadIdx.x];
+        const uint32_t pre = block_excl_scan<uint32_t, RS_NT>(c, total, sm.red);
+        sm.base[threadIdx.x] = pre;
+      }
+      for (uint32_t r0 = 0; r0 < d; r0 += RS_NT) {
+        for (int q = 0; q < RS_NW; q++) sm.wcnt[q][threadIdx.x] = 0;
+        __syncthreads();
+        const uint32_t i = r0 + threadIdx.x;
+        const bool ok = i < d;
+        const uint32_t key = ok ? sm.k[cur][i] : 0u;
+        const uint32_t val = (VALS && ok) ? sm.v[cur][i] : 0u;
+        const uint32_t dig = ok ? ((key >> shift) & 255u) : 256u;
+        const uint32_t peers = __match_any_sync(LG_FULL_MASK, dig);
+        const uint32_t rank = __popc(peers & lanemask_lt());
+        if (ok && rank == 0) sm.wcnt[w][dig] = __popc(peers);
+        __syncthreads();
+        uint32_t acc = 0;
+        for (int q = 0; q < RS_NW; q++) {
+          const uint32_t c = sm.wcnt[q][threadIdx.x];
+          sm.wcnt[q][threadIdx.x] = acc;
+          acc += c;
+        }
+        __syncthreads();
+        if (ok) {
+          const uint32_t pos = sm.base[dig] + sm.seen[dig] + sm.wcnt[w][dig] + rank;
+          sm.k[cur ^ 1][pos] = key;
+          if (VALS) sm.v[cur ^ 1][pos] = val;
+        }
+        __syncthreads();
+        sm.seen[threadIdx.x] += acc;
+      }
+      cur ^= 1;
+      __syncthreads();
+    }
+    for (uint32_t i = threadIdx.x; i < d; i += RS_NT) {
+      keys[lo + i] = sm.k[cur][i];
+      if (VALS) vals[lo + i] = sm.v[cur][i];
+    }
+    __syncthreads();
+  }
+}
+
+template <bool VALS>
+static cudaError_t seg_radix_launch(uint32_t* keys, uint32_t* vals, const uint64_t* off, const uint32_t* list,
+                                    uint32_t nlist, uint32_t key_bits, cudaStream_t st) {
+  const size_t smem = sizeof(SegRadixSmem<VALS>);
+  cudaError_t e = cudaFuncSetAttribute(k_seg_radix<VALS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_seg_radix<VALS><<<grid_for(nlist, 1, 152 * 8), RS_NT, smem, st>>>(keys, vals, off, list, nlist,
+                                                                      (key_bits + 7) / 8);
+  count_launch();
+  return cudaGetLastError();
+}
+
 template <int G, int W, bool VALS>
 static cudaError_t seg_blk_launch(uint32_t* keys, uint32_t* vals, const uint64_t* off, const uint32_t* list,
                                   uint32_t nlist, cudaStream_t st) {
@@ -610,9 +706,14 @@ cudaError_t segmented_sort(uint32_t* keys, uint32_t* vals, const uint64_t* off, 
   cudaMemcpyAsync(meta + SEG_NCLASS, base, sizeof(base), cudaMemcpyHostToDevice, st);
   k_seg_fill<<<grid_for(rows, 256, 152 * 16), 256, 0, st>>>(off, rows, meta + SEG_NCLASS, meta + 2 * SEG_NCLASS, list);
   count_launch();
-  for (int k = 1; k <= 7 && e == cudaSuccess; k++)
+  for (int k = 1; k <= 4 && e == cudaSuccess; k++)
     if (cnt[k]) e = vals ? seg_blk_class<true>(k, keys, vals, off, list + base[k], cnt[k], st)
                          : seg_blk_class<false>(k, keys, vals, off, list + base[k], cnt[k], st);
+  // rows of 513..4096 keys: one radix sort per row in shared memory
+  const uint32_t mid = cnt[5] + cnt[6] + cnt[7];  // classes 5..7 are adjacent in `list`
+  if (e == cudaSuccess && mid)
+    e = vals ? seg_radix_launch<true>(keys, vals, off, list + base[5], mid, key_bits, st)
+             : seg_radix_launch<false>(keys, vals, off, list + base[5], mid, key_bits, st);
   if (e == cudaSuccess && cnt[9]) e = seg_sort_big(keys, vals, off, list + base[9], cnt[9], key_bits, st);
   cudaFreeAsync(list, st);
   cudaFreeAsync(meta, st);

@@ -920,53 +920,76 @@ __global__ void __launch_bounds__(TNT, IDM == ID_LOCAL_GAP ? 6 : 5) k_bfs_pull(G
   for (uint32_t t = threadIdx.x; t < qn; t += TNT) a.queue_out[qbase + t] = qbuf[t];
 }
 
-// top-down step: one warp per frontier vertex
-template <int IDM, int OFF, typename M>
-__global__ void __launch_bounds__(256) k_bfs_push(GView g, BfsArgs a) {
+// top-down step over fields [f0, f1) of a frontier vertex with source mask m:
+// every neighbor not yet visited by some of m's sources joins the next
+// frontier for them (a warp, 32 * HEAVY_U fields per step)
+template <int IDM, typename M>
+__device__ __forceinline__ void push_fields(const GView& g, const BfsArgs& a, M m, uint64_t start, uint32_t w,
+                                            uint32_t f0, uint32_t f1, uint32_t carry, uint32_t& pairs) {
   M* vis = reinterpret_cast<M*>(a.vis);
-  const M* __restrict__ fin = reinterpret_cast<const M*>(a.front_in);
   M* fout = reinterpret_cast<M*>(a.front_out);
   const int lane = threadIdx.x & 31;
   const uint32_t nd = a.level + 1;
-  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-  uint32_t pairs = 0;
-  for (uint64_t q = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); q < a.queue_in_len; q += warps) {
-    const uint32_t v = a.queue_in[q];
-    const M m = fin[v];
-    uint64_t x0, x1, start;
-    uint32_t d, w;
-    offset_pair<OFF>(g, v, x0, x1);
-    vgeo<IDM>(g, x0, x1, start, d, w);
-    uint32_t carry = 0;
-    for (uint32_t base = 0; base < d; base += 32 * HEAVY_U) {
-      uint32_t id[HEAVY_U];
-      warp_ids<IDM, HEAVY_U>(g, start, w, base, d, carry, id);
-      M cur[HEAVY_U];
+  for (uint32_t base = f0; base < f1; base += 32 * HEAVY_U) {
+    uint32_t id[HEAVY_U];
+    warp_ids<IDM, HEAVY_U>(g, start, w, base, f1, carry, id);
+    M cur[HEAVY_U];
 #pragma unroll
-      for (int u = 0; u < HEAVY_U; u++) cur[u] = (base + 32u * u + lane < d) ? vis[id[u]] : (M)~(M)0;
+    for (int u = 0; u < HEAVY_U; u++) cur[u] = (base + 32u * u + lane < f1) ? vis[id[u]] : (M)~(M)0;
 #pragma unroll
-      for (int u = 0; u < HEAVY_U; u++) {
-        const uint32_t u_id = id[u];
-        bool app = false;
-        M nb = (M)(m & (M)~cur[u]);
+    for (int u = 0; u < HEAVY_U; u++) {
+      const uint32_t u_id = id[u];
+      bool app = false;
+      M nb = (M)(m & (M)~cur[u]);
+      if (nb) {
+        const M old = atomic_or_mask<M>(vis + u_id, nb);
+        nb = (M)(nb & (M)~old);
         if (nb) {
-          const M old = atomic_or_mask<M>(vis + u_id, nb);
-          nb = (M)(nb & (M)~old);
-          if (nb) {
-            const M oldf = atomic_or_mask<M>(fout + u_id, nb);
-            app = (oldf == 0);
-            write_depths<M>(a, g.n, u_id, nb, nd);
-            pairs += __popcll((unsigned long long)nb);
-          }
-        }
-        const uint32_t b = __ballot_sync(LG_FULL_MASK, app);
-        if (b) {
-          uint32_t basepos = 0;
-          if (lane == 0) basepos = atomicAdd(&a.counters[0], (uint32_t)__popc(b));
-          basepos = __shfl_sync(LG_FULL_MASK, basepos, 0);
-          if (app) a.queue_out[basepos + __popc(b & lane_lt_mask())] = u_id;
+          const M oldf = atomic_or_mask<M>(fout + u_id, nb);
+          app = (oldf == 0);
+          write_depths<M>(a, g.n, u_id, nb, nd);
+          pairs += __popcll((unsigned long long)nb);
         }
       }
+      const uint32_t bal = __ballot_sync(LG_FULL_MASK, app);
+      if (bal) {
+        uint32_t basepos = 0;
+        if (lane == 0) basepos = atomicAdd(&a.counters[0], (uint32_t)__popc(bal));
+        basepos = __shfl_sync(LG_FULL_MASK, basepos, 0);
+        if (app) a.queue_out[basepos + __popc(bal & lane_lt_mask())] = u_id;
+      }
+    }
+  }
+}
+
+// Top-down step.  Blocks [0, hb) take the heavy-vertex schedule, a warp per
+// item, working when the item's vertex is in the frontier (a hub's arcs are
+// spread over as many warps as it has items); the other blocks take the
+// frontier queue, a warp per vertex of degree <= heavy_min.
+template <int IDM, int OFF, typename M>
+__global__ void __launch_bounds__(256) k_bfs_push(GView g, BfsArgs a, unsigned hb) {
+  const M* __restrict__ fin = reinterpret_cast<const M*>(a.front_in);
+  const int lane = threadIdx.x & 31;
+  uint32_t pairs = 0;
+  if (blockIdx.x < hb) {
+    const uint64_t it = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (it < g.n_items) {
+      const HeavyItem h = g.items[it];
+      const M m = fin[h.v];
+      if (m) push_fields<IDM, M>(g, a, m, h.bit, h.w, h.f0, h.f0 + h.nf, h.carry, pairs);
+    }
+  } else {
+    const uint64_t warps = (uint64_t)(gridDim.x - hb) * (blockDim.x >> 5);
+    for (uint64_t q = (uint64_t)(blockIdx.x - hb) * (blockDim.x >> 5) + (threadIdx.x >> 5); q < a.queue_in_len;
+         q += warps) {
+      const uint32_t v = a.queue_in[q];
+      const M m = fin[v];
+      uint64_t x0, x1, start;
+      uint32_t d, w;
+      offset_pair<OFF>(g, v, x0, x1);
+      vgeo<IDM>(g, x0, x1, start, d, w);
+      if (d > g.heavy_min && g.n_items) continue;  // in the heavy schedule
+      push_fields<IDM, M>(g, a, m, start, w, 0, d, 0, pairs);
     }
   }
   pairs = warp_sum<uint32_t>(pairs);
@@ -1066,16 +1089,20 @@ __device__ __forceinline__ void dec_fields(const GView& g, const DecArgs& a, uin
   }
 }
 
-constexpr int DEC_FLAT_U = 8;  // records per thread in flight (flat decode)
+constexpr uint32_t DEC_FLAT_CH = 512;                      // records per warp chunk (flat decode)
+constexpr uint32_t DEC_FLAT_WORDS = DEC_FLAT_CH * 64 / 32 + 4;  // stream words of a chunk of <= 64-bit records
 
 // Flat decode of global-ID records (or CSR-32 IDs), one launch, one block per
 // tile of TV vertices: the block writes the tile's row_ptr entries from the
-// offsets, then maps its share of the records (arcs / tiles, rounded up to
-// whole warps of DEC_FLAT_U) to IDs -- consecutive threads on consecutive
-// records, coalesced reads and writes -- so every block mixes the latency-bound
-// offset decode with streaming work.
+// offsets, then decodes its share of the records (arcs / tiles, rounded up to
+// whole chunks) chunk by chunk, a warp per chunk of DEC_FLAT_CH records: the
+// chunk's stream words come into shared memory with 16-byte loads (a chunk
+// starts on a 16-byte boundary: DEC_FLAT_CH * r bits is a multiple of 128),
+// then lane l extracts records l, l + 32, ... with a funnel shift and writes
+// them coalesced.
 template <int IDM, int OFF>
 __global__ void __launch_bounds__(256) k_dec_flat(GView g, DecArgs a, uint64_t per_block) {
+  __shared__ __align__(16) uint32_t fw[TNT / 32][DEC_FLAT_WORDS];
   {
     __shared__ uint64_t xs[TV + 1];
     __shared__ TileScratch ts;
@@ -1088,42 +1115,38 @@ __global__ void __launch_bounds__(256) k_dec_flat(GView g, DecArgs a, uint64_t p
   }
   const uint64_t arcs = g.arcs;
   const uint64_t jb = (uint64_t)blockIdx.x * per_block, je = min(arcs, jb + per_block);
-  const uint32_t r = IDM == ID_CSR32 ? 32u : g.r;
-  const uint32_t s = IDM == ID_CSR32 ? 32u : g.s;
-  const uint32_t ms = mask_lo(s), mw = mask_lo(g.omega);
+  const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
   const bool want_w = a.weights != nullptr;
-  for (uint64_t j0 = jb + threadIdx.x; j0 < je; j0 += (uint64_t)blockDim.x * DEC_FLAT_U) {
-    uint32_t id[DEC_FLAT_U], wt[DEC_FLAT_U];
-#pragma unroll
-    for (int k = 0; k < DEC_FLAT_U; k++) {
-      const uint64_t j = j0 + (uint64_t)k * blockDim.x;
-      id[k] = 0; wt[k] = 0;
-      if (j < je) {
-        if (IDM == ID_CSR32) {
-          id[k] = __ldcs(g.A32 + j);
-          if (want_w && g.W32) wt[k] = __ldcs(g.W32 + j);
-        } else {
-          const uint64_t p = j * r;
-          const uint64_t wi = p >> 5;
-          const uint32_t sh = (uint32_t)p & 31u;
-          const uint32_t x0 = __ldg(g.A32 + wi), x1 = __ldg(g.A32 + wi + 1);
-          id[k] = __funnelshift_r(x0, x1, sh) & ms;
-          if (want_w && g.omega) {
-            const uint32_t q = sh + s;  // < 64
-            const uint32_t y0 = q < 32 ? x0 : x1;
-            const uint32_t y1 = q < 32 ? x1 : __ldg(g.A32 + wi + 2);
-            wt[k] = __funnelshift_r(y0, y1, q & 31u) & mw;
+  if constexpr (IDM == ID_CSR32) {
+    for (uint64_t j = jb + threadIdx.x; j < je; j += TNT) {
+      __stcs(a.ids + j, __ldcs(g.A32 + j));
+      if (want_w) __stcs(a.weights + j, g.W32 ? __ldcs(g.W32 + j) : 0u);
+    }
+  } else {
+    const uint32_t r = g.r, s = g.s;
+    const uint32_t ms = mask_lo(s), mw = mask_lo(g.omega);
+    uint32_t* sw = fw[wid];
+    for (uint64_t c = jb + (uint64_t)wid * DEC_FLAT_CH; c < je; c += (uint64_t)(TNT / 32) * DEC_FLAT_CH) {
+      const uint32_t nrec = (uint32_t)min((uint64_t)DEC_FLAT_CH, je - c);
+      const uint64_t w0 = c * r / 32;  // a multiple of 4: c is a multiple of DEC_FLAT_CH
+      const uint32_t nw = (nrec * r + 31) / 32 + 1;  // the chunk's words and the one after
+      const uint4* src = reinterpret_cast<const uint4*>(g.A32 + w0);
+      for (uint32_t q = lane; q * 4 < nw; q += 32) reinterpret_cast<uint4*>(sw)[q] = __ldcs(src + q);
+      __syncwarp();
+      for (uint32_t t = lane; t < nrec; t += 32) {
+        const uint32_t p = t * r;
+        const uint32_t x0 = sw[p >> 5], x1 = sw[(p >> 5) + 1];
+        __stcs(a.ids + c + t, __funnelshift_r(x0, x1, p & 31u) & ms);
+        if (want_w) {
+          uint32_t wt = 0;
+          if (g.omega) {
+            const uint32_t q = p + s;
+            wt = __funnelshift_r(sw[q >> 5], sw[(q >> 5) + 1], q & 31u) & mw;
           }
+          __stcs(a.weights + c + t, wt);
         }
       }
-    }
-#pragma unroll
-    for (int k = 0; k < DEC_FLAT_U; k++) {
-      const uint64_t j = j0 + (uint64_t)k * blockDim.x;
-      if (j < je) {
-        __stcs(a.ids + j, id[k]);
-        if (want_w) __stcs(a.weights + j, wt[k]);
-      }
+      __syncwarp();
     }
   }
 }
@@ -1606,10 +1629,11 @@ cudaError_t launch_bfs_pull(const GView& g, const BfsArgs& a, int mb, cudaStream
 template <int IDM, int OFF>
 cudaError_t launch_bfs_push(const GView& g, const BfsArgs& a, int mb, cudaStream_t st) {
   if (a.queue_in_len == 0) return cudaSuccess;
-  const unsigned grid = grid_for(a.queue_in_len, 8, 152 * 16);
-  if (mb == 2) { k_bfs_push<IDM, OFF, uint16_t><<<grid, 256, 0, st>>>(g, a); count_launch(); }
-  else if (mb == 4) { k_bfs_push<IDM, OFF, uint32_t><<<grid, 256, 0, st>>>(g, a); count_launch(); }
-  else { k_bfs_push<IDM, OFF, uint64_t><<<grid, 256, 0, st>>>(g, a); count_launch(); }
+  const unsigned hb = heavy_blocks(g.n_items);
+  const unsigned grid = hb + grid_for(a.queue_in_len, 8, 152 * 16);
+  if (mb == 2) { k_bfs_push<IDM, OFF, uint16_t><<<grid, 256, 0, st>>>(g, a, hb); count_launch(); }
+  else if (mb == 4) { k_bfs_push<IDM, OFF, uint32_t><<<grid, 256, 0, st>>>(g, a, hb); count_launch(); }
+  else { k_bfs_push<IDM, OFF, uint64_t><<<grid, 256, 0, st>>>(g, a, hb); count_launch(); }
   return cudaGetLastError();
 }
 template <int IDM, int OFF>
@@ -1664,7 +1688,7 @@ cudaError_t launch_dec_all(const GView& g, const DecArgs& a, cudaStream_t st) {
   if (g.n == 0) return cudaSuccess;
   if constexpr (IDM == ID_GLOBAL || IDM == ID_CSR32) {
     const uint64_t tiles = tiles_of(g.n);
-    const uint64_t unit = 256ull * DEC_FLAT_U;
+    const uint64_t unit = (uint64_t)(TNT / 32) * DEC_FLAT_CH;
     const uint64_t per_block = (g.arcs + tiles - 1) / tiles;
     k_dec_flat<IDM, OFF><<<(unsigned)tiles, 256, 0, st>>>(g, a, (per_block + unit - 1) / unit * unit);
   } else {
