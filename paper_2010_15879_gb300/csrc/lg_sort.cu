@@ -478,25 +478,24 @@ __global__ void __launch_bounds__(256) k_seg_fill(const uint64_t* __restrict__ o
 // large rows: gather (row rank, key) composite keys, radix sort, scatter back
 __global__ void k_seg_big_gather(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
                                  const uint64_t* __restrict__ off, const uint32_t* __restrict__ big,
-                                 const uint64_t* __restrict__ boff, uint32_t nbig, uint32_t key_bits,
-                                 uint64_t* __restrict__ ck, uint32_t* __restrict__ cv) {
+                                 const uint64_t* __restrict__ boff, uint32_t nbig, uint32_t* __restrict__ ck,
+                                 uint32_t* __restrict__ cv) {
   for (uint32_t b = blockIdx.x; b < nbig; b += gridDim.x) {
     const uint64_t lo = off[big[b]], d = off[big[b] + 1] - lo, o = boff[b];
     for (uint64_t i = threadIdx.x; i < d; i += blockDim.x) {
-      ck[o + i] = ((uint64_t)b << key_bits) | keys[lo + i];
+      ck[o + i] = keys[lo + i];
       cv[o + i] = vals ? vals[lo + i] : 0u;
     }
   }
 }
 __global__ void k_seg_big_scatter(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                                   const uint64_t* __restrict__ off, const uint32_t* __restrict__ big,
-                                  const uint64_t* __restrict__ boff, uint32_t nbig, uint32_t key_bits,
-                                  const uint64_t* __restrict__ ck, const uint32_t* __restrict__ cv) {
-  const uint64_t kmask = key_bits >= 64 ? ~0ull : (1ull << key_bits) - 1ull;
+                                  const uint64_t* __restrict__ boff, uint32_t nbig, const uint32_t* __restrict__ ck,
+                                  const uint32_t* __restrict__ cv) {
   for (uint32_t b = blockIdx.x; b < nbig; b += gridDim.x) {
     const uint64_t lo = off[big[b]], d = off[big[b] + 1] - lo, o = boff[b];
     for (uint64_t i = threadIdx.x; i < d; i += blockDim.x) {
-      keys[lo + i] = (uint32_t)(ck[o + i] & kmask);
+      keys[lo + i] = ck[o + i];
       if (vals) vals[lo + i] = cv[o + i];
     }
   }
@@ -507,41 +506,168 @@ __global__ void k_seg_big_sizes(const uint64_t* __restrict__ off, const uint32_t
     sizes[b] = off[big[b] + 1] - off[big[b]];
 }
 
+// Rows above SEG_MEDIUM keys: a segmented LSD radix sort of the rows gathered
+// into one buffer.  Tiles of RS_TILE keys never straddle two rows; the
+// histogram cells are laid out row by row, digit-major within a row, so one
+// exclusive scan over all cells gives every (row, digit, tile) its output
+// position inside its own row -- no row index in the keys, ceil(key_bits / 8)
+// passes over 4-byte keys.
+struct SrsTile {
+  uint64_t start;     // first key of the tile in the gathered buffer
+  uint64_t cellbase;  // first histogram cell of the tile's row
+  uint32_t len;       // keys in the tile (<= RS_TILE)
+  uint32_t stride;    // tiles in the row
+  uint32_t tl;        // index of the tile within its row
+  uint32_t pad;
+};
+
+__global__ void k_srs_tile_count(const uint64_t* __restrict__ boff, uint32_t nbig, uint32_t* __restrict__ nt) {
+  for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < nbig; b += gridDim.x * blockDim.x)
+    nt[b] = (uint32_t)((boff[b + 1] - boff[b] + RS_TILE - 1) / RS_TILE);
+}
+__global__ void k_srs_tile_fill(const uint64_t* __restrict__ boff, const uint64_t* __restrict__ tbase, uint32_t nbig,
+                                SrsTile* __restrict__ tiles) {
+  for (uint32_t b = blockIdx.x; b < nbig; b += gridDim.x) {
+    const uint64_t size = boff[b + 1] - boff[b], t0 = tbase[b];
+    const uint32_t nt = (uint32_t)(tbase[b + 1] - t0);
+    for (uint32_t tl = threadIdx.x; tl < nt; tl += blockDim.x) {
+      SrsTile d;
+      d.start = boff[b] + (uint64_t)tl * RS_TILE;
+      d.cellbase = 256ull * t0;
+      d.len = (uint32_t)min((uint64_t)RS_TILE, size - (uint64_t)tl * RS_TILE);
+      d.stride = nt;
+      d.tl = tl;
+      d.pad = 0;
+      tiles[t0 + tl] = d;
+    }
+  }
+}
+__global__ void __launch_bounds__(RS_NT) k_srs_hist(const uint32_t* __restrict__ keys, const SrsTile* __restrict__ tiles,
+                                                    uint32_t shift, uint32_t* __restrict__ hist) {
+  __shared__ uint32_t cnt[256];
+  const SrsTile d = tiles[blockIdx.x];
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < d.len; i += RS_NT) atomicAdd(&cnt[(keys[d.start + i] >> shift) & 255u], 1u);
+  __syncthreads();
+  hist[d.cellbase + (uint64_t)threadIdx.x * d.stride + d.tl] = cnt[threadIdx.x];
+}
+__global__ void __launch_bounds__(RS_NT) k_srs_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                                       uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                       const SrsTile* __restrict__ tiles, uint32_t shift,
+                                                       const uint64_t* __restrict__ off,
+                                                       const uint32_t* __restrict__ hist) {
+  extern __shared__ __align__(16) unsigned char srs_raw[];
+  RsSmem<uint32_t>& sm = *reinterpret_cast<RsSmem<uint32_t>*>(srs_raw);
+  const SrsTile d = tiles[blockIdx.x];
+  const int w = threadIdx.x >> 5;
+  const uint64_t cell = d.cellbase + (uint64_t)threadIdx.x * d.stride + d.tl;
+  {
+    uint32_t total;
+    sm.loc[threadIdx.x] = block_excl_scan<uint32_t, RS_NT>(hist[cell], total, sm.red);
+    sm.glob[threadIdx.x] = off[cell];
+    sm.seen[threadIdx.x] = 0;
+  }
+  for (uint32_t r0 = 0; r0 < d.len; r0 += RS_NT) {
+    for (int k = 0; k < RS_NW; k++) sm.wcnt[k][threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t li = r0 + threadIdx.x;
+    const bool ok = li < d.len;
+    const uint32_t key = ok ? kin[d.start + li] : 0u;
+    const uint32_t val = (ok && vin) ? vin[d.start + li] : 0u;
+    const uint32_t dig = ok ? ((key >> shift) & 255u) : 256u;
+    const uint32_t peers = __match_any_sync(LG_FULL_MASK, dig);
+    const uint32_t rank = __popc(peers & lanemask_lt());
+    if (ok && rank == 0) sm.wcnt[w][dig] = __popc(peers);
+    __syncthreads();
+    uint32_t acc = 0;
+    for (int k = 0; k < RS_NW; k++) {
+      const uint32_t c = sm.wcnt[k][threadIdx.x];
+      sm.wcnt[k][threadIdx.x] = acc;
+      acc += c;
+    }
+    __syncthreads();
+    if (ok) {
+      const uint32_t pos = sm.loc[dig] + sm.seen[dig] + sm.wcnt[w][dig] + rank;
+      sm.keys[pos] = key;
+      sm.vals[pos] = val;
+    }
+    __syncthreads();
+    sm.seen[threadIdx.x] += acc;
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < d.len; i += RS_NT) {
+    const uint32_t key = sm.keys[i];
+    const uint32_t dig = (key >> shift) & 255u;
+    const uint64_t pos = sm.glob[dig] + (i - sm.loc[dig]);
+    kout[pos] = key;
+    if (vin) vout[pos] = sm.vals[i];
+  }
+}
+
 static cudaError_t seg_sort_big(uint32_t* keys, uint32_t* vals, const uint64_t* off, const uint32_t* big,
                                 uint32_t nbig, uint32_t key_bits, cudaStream_t st) {
-  uint64_t *sizes = nullptr, *boff = nullptr, *ck = nullptr, *ck2 = nullptr, *stmp = nullptr;
-  uint32_t *cv = nullptr, *cv2 = nullptr;
-  void* rtmp = nullptr;
-  uint64_t nb_total = 0;
+  uint64_t *sizes = nullptr, *boff = nullptr, *stmp = nullptr, *tbase = nullptr, *coff = nullptr, *ctmp = nullptr;
+  uint32_t *ka = nullptr, *kb = nullptr, *va = nullptr, *vb = nullptr, *nt = nullptr, *hist = nullptr;
+  SrsTile* tiles = nullptr;
+  uint64_t hb[2] = {0, 0};  // keys, tiles
   cudaError_t e = lg::pool_alloc((void**)&sizes, nbig * sizeof(uint64_t), st);
   if (e == cudaSuccess) e = lg::pool_alloc((void**)&boff, (nbig + 1) * sizeof(uint64_t), st);
+  if (e == cudaSuccess) e = lg::pool_alloc((void**)&tbase, (nbig + 1) * sizeof(uint64_t), st);
+  if (e == cudaSuccess) e = lg::pool_alloc((void**)&nt, nbig * sizeof(uint32_t), st);
   if (e == cudaSuccess) e = lg::pool_alloc((void**)&stmp, scan_tmp_words(nbig) * sizeof(uint64_t), st);
   if (e == cudaSuccess) {
     k_seg_big_sizes<<<grid_for(nbig, 256, 1024), 256, 0, st>>>(off, big, nbig, sizes);
     count_launch();
     e = scan_excl_u64(sizes, nbig, boff, stmp, st);
   }
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&nb_total, boff + nbig, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e == cudaSuccess) e = lg::pool_alloc((void**)&ck, nb_total * sizeof(uint64_t), st);
-  if (e == cudaSuccess) e = lg::pool_alloc((void**)&ck2, nb_total * sizeof(uint64_t), st);
-  if (e == cudaSuccess) e = lg::pool_alloc((void**)&cv, nb_total * sizeof(uint32_t), st);
-  if (e == cudaSuccess) e = lg::pool_alloc((void**)&cv2, nb_total * sizeof(uint32_t), st);
-  if (e == cudaSuccess) e = lg::pool_alloc(&rtmp, radix_tmp_bytes(nb_total), st);
   if (e == cudaSuccess) {
-    k_seg_big_gather<<<grid_for(nbig, 1, 4096), 256, 0, st>>>(keys, vals, off, big, boff, nbig, key_bits, ck, cv);
+    k_srs_tile_count<<<grid_for(nbig, 256, 1024), 256, 0, st>>>(boff, nbig, nt);
     count_launch();
-    e = radix_sort_u64(ck, cv, ck2, cv2, nb_total, key_bits + host_bits(nbig), rtmp, st);
+    e = scan_excl_u32(nt, nbig, tbase, stmp, st);
   }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hb[0], boff + nbig, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hb[1], tbase + nbig, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  const uint64_t nb_total = hb[0], ntiles = hb[1], cells = 256 * ntiles;
+  if (e == cudaSuccess) e = lg::pool_alloc((void**)&ka, nb_total * sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = lg::pool_alloc((void**)&kb, nb_total * sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = lg::pool_alloc((void**)&va, nb_total * sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = lg::pool_alloc((void**)&vb, nb_total * sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = lg::pool_alloc((void**)&tiles, ntiles * sizeof(SrsTile), st);
+  if (e == cudaSuccess) e = lg::pool_alloc((void**)&hist, cells * sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = lg::pool_alloc((void**)&coff, (cells + 1) * sizeof(uint64_t), st);
+  if (e == cudaSuccess) e = lg::pool_alloc((void**)&ctmp, scan_tmp_words(cells) * sizeof(uint64_t), st);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_srs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)sizeof(RsSmem<uint32_t>));
   if (e == cudaSuccess) {
-    k_seg_big_scatter<<<grid_for(nbig, 1, 4096), 256, 0, st>>>(keys, vals, off, big, boff, nbig, key_bits, ck,
-                                                                cv);
+    k_srs_tile_fill<<<grid_for(nbig, 1, 4096), 256, 0, st>>>(boff, tbase, nbig, tiles);
+    count_launch();
+    k_seg_big_gather<<<grid_for(nbig, 1, 4096), 256, 0, st>>>(keys, vals, off, big, boff, nbig, ka, va);
     count_launch();
     e = cudaGetLastError();
   }
-  cudaFreeAsync(sizes, st); cudaFreeAsync(boff, st); cudaFreeAsync(stmp, st);
-  cudaFreeAsync(ck, st); cudaFreeAsync(ck2, st); cudaFreeAsync(cv, st); cudaFreeAsync(cv2, st);
-  cudaFreeAsync(rtmp, st);
+  const uint32_t passes = (key_bits + 7) / 8;
+  for (uint32_t p = 0; p < passes && e == cudaSuccess; p++) {
+    k_srs_hist<<<(unsigned)ntiles, RS_NT, 0, st>>>(ka, tiles, 8 * p, hist);
+    count_launch();
+    e = scan_excl_u32(hist, cells, coff, ctmp, st);
+    if (e != cudaSuccess) break;
+    k_srs_scatter<<<(unsigned)ntiles, RS_NT, sizeof(RsSmem<uint32_t>), st>>>(ka, vals ? va : nullptr, kb, vb, tiles,
+                                                                              8 * p, coff, hist);
+    count_launch();
+    e = cudaGetLastError();
+    uint32_t* t = ka; ka = kb; kb = t;
+    t = va; va = vb; vb = t;
+  }
+  if (e == cudaSuccess) {
+    k_seg_big_scatter<<<grid_for(nbig, 1, 4096), 256, 0, st>>>(keys, vals, off, big, boff, nbig, ka, va);
+    count_launch();
+    e = cudaGetLastError();
+  }
+  cudaFreeAsync(sizes, st); cudaFreeAsync(boff, st); cudaFreeAsync(tbase, st); cudaFreeAsync(nt, st);
+  cudaFreeAsync(stmp, st); cudaFreeAsync(ka, st); cudaFreeAsync(kb, st); cudaFreeAsync(va, st); cudaFreeAsync(vb, st);
+  cudaFreeAsync(tiles, st); cudaFreeAsync(hist, st); cudaFreeAsync(coff, st); cudaFreeAsync(ctmp, st);
   return e;
 }
 
