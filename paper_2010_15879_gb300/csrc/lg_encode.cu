@@ -310,15 +310,27 @@ cudaError_t enc_local_lengths(const uint64_t* rp, const uint32_t* col, uint64_t 
 // (Sections 3.2.1 and 3.3; the weight directly after the ID).  One thread
 // assembles one output word from the (at most 64/r + 2) records touching it.
 // =========================================================================
+// Word-owner packing of r-bit records: 64 records fill exactly r words, so
+// word k is word q = k mod r of chunk c = k / r; the records overlapping word q
+// of a chunk (the same for every chunk) come from a per-block table instead of
+// two 64-bit divisions per word.
 __global__ void __launch_bounds__(256) k_pack_global(const uint32_t* __restrict__ col, const uint32_t* __restrict__ w,
                                                      uint64_t arcs, uint32_t s, uint32_t omega,
                                                      uint64_t* __restrict__ out, uint64_t data_words) {
-  const uint32_t r = s + omega;
+  const uint32_t r = s + omega;  // 1..64
+  __shared__ uint8_t tj0[64], tj1[64];  // first and last record of word q within a chunk of 64 records
+  if (threadIdx.x < r) {
+    tj0[threadIdx.x] = (uint8_t)(threadIdx.x * 64u / r);
+    tj1[threadIdx.x] = (uint8_t)((threadIdx.x * 64u + 63u) / r);
+  }
+  __syncthreads();
   for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < data_words;
        k += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t c = (k >> 32) ? k / r : (uint64_t)((uint32_t)k / r);
+    const uint32_t q = (uint32_t)(k - c * r);
     const uint64_t b0 = k * 64;
-    const uint64_t j0 = b0 / r;
-    uint64_t j1 = (b0 + 63) / r;
+    const uint64_t j0 = c * 64 + tj0[q];
+    uint64_t j1 = c * 64 + tj1[q];
     if (j1 >= arcs) j1 = arcs - 1;
     uint64_t acc = 0;
     for (uint64_t j = j0; j <= j1; j++) {
