@@ -80,10 +80,11 @@ cudaError_t radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, u
                            uint64_t n, uint32_t key_bits, void* tmp, cudaStream_t st);
 // Sort each row [off[i], off[i+1]) of keys ascending, moving vals (nullable) along.
 // Rows of <= 32 keys are skipped when `small_done` (their producer sorted them).
-// Every key is below 2^key_bits.
+// Every key is below 2^key_bits.  `big_prefix`: the rows above 4,096 keys are
+// the first rows (degrees descending), so they are sorted where they lie.
 cudaError_t segmented_sort(uint32_t* keys, uint32_t* vals, const uint64_t* off, uint64_t rows,
                            uint64_t total, uint64_t max_row, cudaStream_t st, bool small_done = false,
-                           uint32_t key_bits = 32);
+                           uint32_t key_bits = 32, bool big_prefix = false);
 
 // ------------------------------------------------------------------ encoder
 cudaError_t enc_validate(const uint64_t* rp, const uint32_t* col, const uint32_t* w, uint64_t n,

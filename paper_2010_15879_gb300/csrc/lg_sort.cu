@@ -506,11 +506,111 @@ __global__ void k_seg_big_sizes(const uint64_t* __restrict__ off, const uint32_t
     sizes[b] = off[big[b] + 1] - off[big[b]];
 }
 
+// -------------------------------------------------------------------------
+// One stable split of a tile of up to RS_TILE keys by a 9-bit digit, for the
+// segmented radix sorts.  Warp w holds the consecutive chunk of keys
+// [c0, c0 + 32 G) with c0 = 32 G w, key c0 + 32 g + lane in x[g]: the warp
+// counts its chunk's digits into its own row of `wc` (one match per 32 keys,
+// the lowest lane of each digit adds its group's count), one block scan turns
+// the (digit, warp) counts into positions, and the warp writes its chunk in
+// order.  Three block barriers per pass, whatever the tile's length.
+// -------------------------------------------------------------------------
+constexpr int SPL_BITS = 9;
+constexpr uint32_t SPL_NB = 1u << SPL_BITS;  // digits per pass
+constexpr int SPL_G = RS_TILE / RS_NT;       // groups of 32 keys per warp, at most
+
+struct SplitSmem {
+  uint32_t wc[RS_NW][SPL_NB];  // per warp: its count, then its next position, of each digit
+  uint32_t dstart[SPL_NB];     // first position of each digit in the tile
+  uint32_t red[RS_NW];
+};
+
+__host__ __device__ constexpr uint32_t spl_passes(uint32_t key_bits) { return (key_bits + SPL_BITS - 1) / SPL_BITS; }
+
+template <bool VALS>
+__device__ __forceinline__ void split_pass(const uint32_t (&x)[SPL_G], const uint32_t (&y)[SPL_G], uint32_t c0,
+                                           uint32_t len, int G, uint32_t shift, uint32_t* __restrict__ dk,
+                                           uint32_t* __restrict__ dv, SplitSmem& sp) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t lt = lanemask_lt();
+  for (uint32_t b = lane; b < SPL_NB; b += 32) sp.wc[w][b] = 0;
+  __syncwarp();
+  uint32_t pm[SPL_G];
+#pragma unroll
+  for (int g = 0; g < SPL_G; g++) {
+    pm[g] = 0;
+    if (g < G) {
+      const bool ok = c0 + 32u * g + lane < len;
+      const uint32_t dig = ok ? (x[g] >> shift) & (SPL_NB - 1) : SPL_NB;
+      pm[g] = __match_any_sync(LG_FULL_MASK, dig);
+      if (ok && (pm[g] & lt) == 0) sp.wc[w][dig] += __popc(pm[g]);
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  constexpr int DPT = SPL_NB / RS_NT;  // digits per thread, consecutive
+  uint32_t tot[DPT], sum = 0;
+#pragma unroll
+  for (int q = 0; q < DPT; q++) {
+    const uint32_t b = threadIdx.x * DPT + q;
+    uint32_t acc = 0;
+#pragma unroll
+    for (int v = 0; v < RS_NW; v++) {
+      const uint32_t c = sp.wc[v][b];
+      sp.wc[v][b] = acc;
+      acc += c;
+    }
+    tot[q] = acc;
+    sum += acc;
+  }
+  uint32_t total;
+  uint32_t pre = block_excl_scan<uint32_t, RS_NT>(sum, total, sp.red);
+#pragma unroll
+  for (int q = 0; q < DPT; q++) {
+    const uint32_t b = threadIdx.x * DPT + q;
+    sp.dstart[b] = pre;
+#pragma unroll
+    for (int v = 0; v < RS_NW; v++) sp.wc[v][b] += pre;
+    pre += tot[q];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int g = 0; g < SPL_G; g++) {
+    if (g < G) {
+      const bool ok = c0 + 32u * g + lane < len;
+      const uint32_t dig = (x[g] >> shift) & (SPL_NB - 1);
+      if (ok) {
+        const uint32_t pos = sp.wc[w][dig] + __popc(pm[g] & lt);
+        dk[pos] = x[g];
+        if (VALS) dv[pos] = y[g];
+      }
+      __syncwarp();
+      if (ok && (pm[g] & lt) == 0) sp.wc[w][dig] += __popc(pm[g]);
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+}
+
+template <bool VALS>
+__device__ __forceinline__ void split_load(const uint32_t* __restrict__ k, const uint32_t* __restrict__ v,
+                                           uint32_t c0, uint32_t len, int G, uint32_t (&x)[SPL_G],
+                                           uint32_t (&y)[SPL_G]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int g = 0; g < SPL_G; g++) {
+    const uint32_t i = c0 + 32u * g + lane;
+    const bool ok = g < G && i < len;
+    x[g] = ok ? k[i] : 0u;
+    y[g] = (VALS && ok) ? v[i] : 0u;
+  }
+}
+
 // Rows above SEG_MEDIUM keys: a segmented LSD radix sort of the rows gathered
 // into one buffer.  Tiles of RS_TILE keys never straddle two rows; the
 // histogram cells are laid out row by row, digit-major within a row, so one
 // exclusive scan over all cells gives every (row, digit, tile) its output
-// position inside its own row -- no row index in the keys, ceil(key_bits / 8)
+// position inside its own row -- no row index in the keys, ceil(key_bits / 9)
 // passes over 4-byte keys.
 struct SrsTile {
   uint64_t start;     // first key of the tile in the gathered buffer
@@ -533,7 +633,7 @@ __global__ void k_srs_tile_fill(const uint64_t* __restrict__ boff, const uint64_
     for (uint32_t tl = threadIdx.x; tl < nt; tl += blockDim.x) {
       SrsTile d;
       d.start = boff[b] + (uint64_t)tl * RS_TILE;
-      d.cellbase = 256ull * t0;
+      d.cellbase = (uint64_t)SPL_NB * t0;
       d.len = (uint32_t)min((uint64_t)RS_TILE, size - (uint64_t)tl * RS_TILE);
       d.stride = nt;
       d.tl = tl;
@@ -544,149 +644,180 @@ __global__ void k_srs_tile_fill(const uint64_t* __restrict__ boff, const uint64_
 }
 __global__ void __launch_bounds__(RS_NT) k_srs_hist(const uint32_t* __restrict__ keys, const SrsTile* __restrict__ tiles,
                                                     uint32_t shift, uint32_t* __restrict__ hist) {
-  __shared__ uint32_t cnt[256];
+  __shared__ uint32_t cnt[SPL_NB];
   const SrsTile d = tiles[blockIdx.x];
-  cnt[threadIdx.x] = 0;
+  for (uint32_t b = threadIdx.x; b < SPL_NB; b += RS_NT) cnt[b] = 0;
   __syncthreads();
-  for (uint32_t i = threadIdx.x; i < d.len; i += RS_NT) atomicAdd(&cnt[(keys[d.start + i] >> shift) & 255u], 1u);
+  for (uint32_t i = threadIdx.x; i < d.len; i += RS_NT)
+    atomicAdd(&cnt[(keys[d.start + i] >> shift) & (SPL_NB - 1)], 1u);
   __syncthreads();
-  hist[d.cellbase + (uint64_t)threadIdx.x * d.stride + d.tl] = cnt[threadIdx.x];
+  for (uint32_t b = threadIdx.x; b < SPL_NB; b += RS_NT) hist[d.cellbase + (uint64_t)b * d.stride + d.tl] = cnt[b];
 }
+
+struct SrsSmem {
+  uint32_t k[RS_TILE];
+  uint32_t v[RS_TILE];
+  uint64_t glob[SPL_NB];  // first output position of each digit of this tile
+  SplitSmem sp;
+};
+
+// One pass: the tile is split by digit in shared memory, then each key goes to
+// its digit's run for this tile (runs of one digit are consecutive in kout).
+template <bool VALS>
 __global__ void __launch_bounds__(RS_NT) k_srs_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                                                        uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                        const SrsTile* __restrict__ tiles, uint32_t shift,
-                                                       const uint64_t* __restrict__ off,
-                                                       const uint32_t* __restrict__ hist) {
+                                                       const uint64_t* __restrict__ off) {
   extern __shared__ __align__(16) unsigned char srs_raw[];
-  RsSmem<uint32_t>& sm = *reinterpret_cast<RsSmem<uint32_t>*>(srs_raw);
+  SrsSmem& sm = *reinterpret_cast<SrsSmem*>(srs_raw);
   const SrsTile d = tiles[blockIdx.x];
-  const int w = threadIdx.x >> 5;
-  const uint64_t cell = d.cellbase + (uint64_t)threadIdx.x * d.stride + d.tl;
-  {
-    uint32_t total;
-    sm.loc[threadIdx.x] = block_excl_scan<uint32_t, RS_NT>(hist[cell], total, sm.red);
-    sm.glob[threadIdx.x] = off[cell];
-    sm.seen[threadIdx.x] = 0;
-  }
-  for (uint32_t r0 = 0; r0 < d.len; r0 += RS_NT) {
-    for (int k = 0; k < RS_NW; k++) sm.wcnt[k][threadIdx.x] = 0;
-    __syncthreads();
-    const uint32_t li = r0 + threadIdx.x;
-    const bool ok = li < d.len;
-    const uint32_t key = ok ? kin[d.start + li] : 0u;
-    const uint32_t val = (ok && vin) ? vin[d.start + li] : 0u;
-    const uint32_t dig = ok ? ((key >> shift) & 255u) : 256u;
-    const uint32_t peers = __match_any_sync(LG_FULL_MASK, dig);
-    const uint32_t rank = __popc(peers & lanemask_lt());
-    if (ok && rank == 0) sm.wcnt[w][dig] = __popc(peers);
-    __syncthreads();
-    uint32_t acc = 0;
-    for (int k = 0; k < RS_NW; k++) {
-      const uint32_t c = sm.wcnt[k][threadIdx.x];
-      sm.wcnt[k][threadIdx.x] = acc;
-      acc += c;
-    }
-    __syncthreads();
-    if (ok) {
-      const uint32_t pos = sm.loc[dig] + sm.seen[dig] + sm.wcnt[w][dig] + rank;
-      sm.keys[pos] = key;
-      sm.vals[pos] = val;
-    }
-    __syncthreads();
-    sm.seen[threadIdx.x] += acc;
-  }
-  __syncthreads();
+  for (uint32_t b = threadIdx.x; b < SPL_NB; b += RS_NT) sm.glob[b] = off[d.cellbase + (uint64_t)b * d.stride + d.tl];
+  const int G = (int)((d.len + RS_NT - 1) / RS_NT);
+  const uint32_t c0 = 32u * G * (threadIdx.x >> 5);
+  uint32_t x[SPL_G], y[SPL_G];
+  split_load<VALS>(kin + d.start, vin + (VALS ? d.start : 0), c0, d.len, G, x, y);
+  split_pass<VALS>(x, y, c0, d.len, G, shift, sm.k, sm.v, sm.sp);
   for (uint32_t i = threadIdx.x; i < d.len; i += RS_NT) {
-    const uint32_t key = sm.keys[i];
-    const uint32_t dig = (key >> shift) & 255u;
-    const uint64_t pos = sm.glob[dig] + (i - sm.loc[dig]);
+    const uint32_t key = sm.k[i];
+    const uint32_t dig = (key >> shift) & (SPL_NB - 1);
+    const uint64_t pos = sm.glob[dig] + (i - sm.sp.dstart[dig]);
     kout[pos] = key;
-    if (vin) vout[pos] = sm.vals[i];
+    if (VALS) vout[pos] = sm.v[i];
   }
 }
 
+// The segmented radix passes over rows held back to back in (ka, va), row b at
+// [boff[b], boff[b+1]) with boff on the device; kb, vb hold as much.  On
+// return *result_in_b says whether the sorted rows ended in (kb, vb).
+static cudaError_t srs_sort(uint32_t* ka, uint32_t* va, uint32_t* kb, uint32_t* vb, const uint64_t* boff,
+                            uint32_t nbig, uint32_t key_bits, bool* result_in_b, cudaStream_t st) {
+  uint64_t *tbase = nullptr, *stmp = nullptr, *coff = nullptr, *ctmp = nullptr;
+  uint32_t *nt = nullptr, *hist = nullptr;
+  SrsTile* tiles = nullptr;
+  uint64_t ntiles = 0;
+  *result_in_b = false;
+  cudaError_t e = lg::pool_alloc((void**)&tbase, (nbig + 1) * sizeof(uint64_t), st);
+  if (e == cudaSuccess) e = lg::pool_alloc((void**)&nt, nbig * sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = lg::pool_alloc((void**)&stmp, scan_tmp_words(nbig) * sizeof(uint64_t), st);
+  if (e == cudaSuccess) {
+    k_srs_tile_count<<<grid_for(nbig, 256, 1024), 256, 0, st>>>(boff, nbig, nt);
+    count_launch();
+    e = scan_excl_u32(nt, nbig, tbase, stmp, st);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&ntiles, tbase + nbig, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  const uint64_t cells = (uint64_t)SPL_NB * ntiles;
+  if (e == cudaSuccess) e = lg::pool_alloc((void**)&tiles, (ntiles ? ntiles : 1) * sizeof(SrsTile), st);
+  if (e == cudaSuccess) e = lg::pool_alloc((void**)&hist, (cells ? cells : 1) * sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = lg::pool_alloc((void**)&coff, (cells + 1) * sizeof(uint64_t), st);
+  if (e == cudaSuccess) e = lg::pool_alloc((void**)&ctmp, scan_tmp_words(cells) * sizeof(uint64_t), st);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(va ? k_srs_scatter<true> : k_srs_scatter<false>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SrsSmem));
+  if (e == cudaSuccess) {
+    k_srs_tile_fill<<<grid_for(nbig, 1, 4096), 256, 0, st>>>(boff, tbase, nbig, tiles);
+    count_launch();
+    e = cudaGetLastError();
+  }
+  const uint32_t passes = spl_passes(key_bits);
+  for (uint32_t p = 0; p < passes && e == cudaSuccess && ntiles; p++) {
+    const uint32_t shift = SPL_BITS * p;
+    k_srs_hist<<<(unsigned)ntiles, RS_NT, 0, st>>>(ka, tiles, shift, hist);
+    count_launch();
+    e = scan_excl_u32(hist, cells, coff, ctmp, st);
+    if (e != cudaSuccess) break;
+    if (va)
+      k_srs_scatter<true><<<(unsigned)ntiles, RS_NT, sizeof(SrsSmem), st>>>(ka, va, kb, vb, tiles, shift, coff);
+    else
+      k_srs_scatter<false><<<(unsigned)ntiles, RS_NT, sizeof(SrsSmem), st>>>(ka, va, kb, vb, tiles, shift, coff);
+    count_launch();
+    e = cudaGetLastError();
+    uint32_t* t = ka; ka = kb; kb = t;
+    t = va; va = vb; vb = t;
+    *result_in_b = !*result_in_b;
+  }
+  cudaFreeAsync(tbase, st); cudaFreeAsync(nt, st); cudaFreeAsync(stmp, st);
+  cudaFreeAsync(tiles, st); cudaFreeAsync(hist, st); cudaFreeAsync(coff, st); cudaFreeAsync(ctmp, st);
+  return e;
+}
+
+// Rows above SEG_MEDIUM keys listed in `big`: gathered back to back, sorted,
+// scattered back.
 static cudaError_t seg_sort_big(uint32_t* keys, uint32_t* vals, const uint64_t* off, const uint32_t* big,
                                 uint32_t nbig, uint32_t key_bits, cudaStream_t st) {
-  uint64_t *sizes = nullptr, *boff = nullptr, *stmp = nullptr, *tbase = nullptr, *coff = nullptr, *ctmp = nullptr;
-  uint32_t *ka = nullptr, *kb = nullptr, *va = nullptr, *vb = nullptr, *nt = nullptr, *hist = nullptr;
-  SrsTile* tiles = nullptr;
-  uint64_t hb[2] = {0, 0};  // keys, tiles
+  uint64_t *sizes = nullptr, *boff = nullptr, *stmp = nullptr;
+  uint32_t *ka = nullptr, *kb = nullptr, *va = nullptr, *vb = nullptr;
+  uint64_t nb_total = 0;
   cudaError_t e = lg::pool_alloc((void**)&sizes, nbig * sizeof(uint64_t), st);
   if (e == cudaSuccess) e = lg::pool_alloc((void**)&boff, (nbig + 1) * sizeof(uint64_t), st);
-  if (e == cudaSuccess) e = lg::pool_alloc((void**)&tbase, (nbig + 1) * sizeof(uint64_t), st);
-  if (e == cudaSuccess) e = lg::pool_alloc((void**)&nt, nbig * sizeof(uint32_t), st);
   if (e == cudaSuccess) e = lg::pool_alloc((void**)&stmp, scan_tmp_words(nbig) * sizeof(uint64_t), st);
   if (e == cudaSuccess) {
     k_seg_big_sizes<<<grid_for(nbig, 256, 1024), 256, 0, st>>>(off, big, nbig, sizes);
     count_launch();
     e = scan_excl_u64(sizes, nbig, boff, stmp, st);
   }
-  if (e == cudaSuccess) {
-    k_srs_tile_count<<<grid_for(nbig, 256, 1024), 256, 0, st>>>(boff, nbig, nt);
-    count_launch();
-    e = scan_excl_u32(nt, nbig, tbase, stmp, st);
-  }
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&hb[0], boff + nbig, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&hb[1], tbase + nbig, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&nb_total, boff + nbig, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  const uint64_t nb_total = hb[0], ntiles = hb[1], cells = 256 * ntiles;
   if (e == cudaSuccess) e = lg::pool_alloc((void**)&ka, nb_total * sizeof(uint32_t), st);
   if (e == cudaSuccess) e = lg::pool_alloc((void**)&kb, nb_total * sizeof(uint32_t), st);
   if (e == cudaSuccess) e = lg::pool_alloc((void**)&va, nb_total * sizeof(uint32_t), st);
   if (e == cudaSuccess) e = lg::pool_alloc((void**)&vb, nb_total * sizeof(uint32_t), st);
-  if (e == cudaSuccess) e = lg::pool_alloc((void**)&tiles, ntiles * sizeof(SrsTile), st);
-  if (e == cudaSuccess) e = lg::pool_alloc((void**)&hist, cells * sizeof(uint32_t), st);
-  if (e == cudaSuccess) e = lg::pool_alloc((void**)&coff, (cells + 1) * sizeof(uint64_t), st);
-  if (e == cudaSuccess) e = lg::pool_alloc((void**)&ctmp, scan_tmp_words(cells) * sizeof(uint64_t), st);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_srs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)sizeof(RsSmem<uint32_t>));
   if (e == cudaSuccess) {
-    k_srs_tile_fill<<<grid_for(nbig, 1, 4096), 256, 0, st>>>(boff, tbase, nbig, tiles);
-    count_launch();
     k_seg_big_gather<<<grid_for(nbig, 1, 4096), 256, 0, st>>>(keys, vals, off, big, boff, nbig, ka, va);
     count_launch();
     e = cudaGetLastError();
   }
-  const uint32_t passes = (key_bits + 7) / 8;
-  for (uint32_t p = 0; p < passes && e == cudaSuccess; p++) {
-    k_srs_hist<<<(unsigned)ntiles, RS_NT, 0, st>>>(ka, tiles, 8 * p, hist);
-    count_launch();
-    e = scan_excl_u32(hist, cells, coff, ctmp, st);
-    if (e != cudaSuccess) break;
-    k_srs_scatter<<<(unsigned)ntiles, RS_NT, sizeof(RsSmem<uint32_t>), st>>>(ka, vals ? va : nullptr, kb, vb, tiles,
-                                                                              8 * p, coff, hist);
-    count_launch();
-    e = cudaGetLastError();
-    uint32_t* t = ka; ka = kb; kb = t;
-    t = va; va = vb; vb = t;
-  }
+  bool in_b = false;
+  if (e == cudaSuccess) e = srs_sort(ka, vals ? va : nullptr, kb, vals ? vb : nullptr, boff, nbig, key_bits, &in_b, st);
   if (e == cudaSuccess) {
-    k_seg_big_scatter<<<grid_for(nbig, 1, 4096), 256, 0, st>>>(keys, vals, off, big, boff, nbig, ka, va);
+    k_seg_big_scatter<<<grid_for(nbig, 1, 4096), 256, 0, st>>>(keys, vals, off, big, boff, nbig, in_b ? kb : ka,
+                                                                in_b ? vb : va);
     count_launch();
     e = cudaGetLastError();
   }
-  cudaFreeAsync(sizes, st); cudaFreeAsync(boff, st); cudaFreeAsync(tbase, st); cudaFreeAsync(nt, st);
-  cudaFreeAsync(stmp, st); cudaFreeAsync(ka, st); cudaFreeAsync(kb, st); cudaFreeAsync(va, st); cudaFreeAsync(vb, st);
-  cudaFreeAsync(tiles, st); cudaFreeAsync(hist, st); cudaFreeAsync(coff, st); cudaFreeAsync(ctmp, st);
+  cudaFreeAsync(sizes, st); cudaFreeAsync(boff, st); cudaFreeAsync(stmp, st);
+  cudaFreeAsync(ka, st); cudaFreeAsync(kb, st); cudaFreeAsync(va, st); cudaFreeAsync(vb, st);
   return e;
 }
 
-// Rows of 513..4096 keys: a CTA per row, a stable LSD radix sort in shared
-// memory (8-bit digits, ceil(key_bits / 8) passes).  Per pass: a digit
-// histogram, its exclusive scan, then rounds of RS_NT keys ranked as in
-// k_rs_scatter (a match among the warp's lanes, the warps before, the keys of
-// the digit placed in earlier rounds).  About 4 compare-free steps per key and
-// pass instead of a bitonic network's log2(d) (log2(d) + 1) / 2 stages.
+// The first nbig rows are the rows above SEG_MEDIUM keys (degree-descending
+// order) and lie back to back from off[0] = 0: sorted in place, with one
+// buffer of the same size beside them.
+static cudaError_t seg_sort_big_prefix(uint32_t* keys, uint32_t* vals, const uint64_t* off, uint32_t nbig,
+                                       uint32_t key_bits, cudaStream_t st) {
+  uint64_t nb_total = 0;
+  cudaError_t e = cudaMemcpyAsync(&nb_total, off + nbig, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  uint32_t *kb = nullptr, *vb = nullptr;
+  if (e == cudaSuccess) e = lg::pool_alloc((void**)&kb, nb_total * sizeof(uint32_t), st);
+  if (e == cudaSuccess && vals) e = lg::pool_alloc((void**)&vb, nb_total * sizeof(uint32_t), st);
+  bool in_b = false;
+  if (e == cudaSuccess) e = srs_sort(keys, vals, kb, vb, off, nbig, key_bits, &in_b, st);
+  if (e == cudaSuccess && in_b) {
+    e = cudaMemcpyAsync(keys, kb, nb_total * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && vals) e = cudaMemcpyAsync(vals, vb, nb_total * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st);
+  }
+  if (kb) cudaFreeAsync(kb, st);
+  if (vb) cudaFreeAsync(vb, st);
+  return e;
+}
+
+// Rows of 513..4096 keys: a CTA per row, a stable LSD radix sort with 9-bit
+// digits (ceil(key_bits / 9) passes of split_pass) -- a few compare-free steps
+// per key and pass instead of a bitonic network's log2(d) (log2(d) + 1) / 2
+// stages.
 constexpr uint32_t SEG_RADIX_MAX = 4096;
+static_assert(SEG_RADIX_MAX <= (uint32_t)RS_TILE, "a row must fit one split tile");
 
 template <bool VALS>
 struct SegRadixSmem {
-  uint32_t k[2][SEG_RADIX_MAX];
-  uint32_t v[VALS ? 2 : 1][VALS ? SEG_RADIX_MAX : 1];
-  uint32_t wcnt[RS_NW][256];
-  uint32_t base[256], seen[256], red[RS_NW];
+  uint32_t k[SEG_RADIX_MAX];
+  uint32_t v[VALS ? SEG_RADIX_MAX : 1];
+  SplitSmem sp;
 };
 
+// Rows of SEG_SMALL < d <= SEG_RADIX_MAX keys, one row per block: the keys
+// stay in registers (warp chunks), each pass splits them into shared memory
+// and reads them back; the last pass's order is written out coalesced.
 template <bool VALS>
 __global__ void __launch_bounds__(RS_NT) k_seg_radix(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                                                      const uint64_t* __restrict__ off,
@@ -694,62 +825,20 @@ __global__ void __launch_bounds__(RS_NT) k_seg_radix(uint32_t* __restrict__ keys
                                                      uint32_t passes) {
   extern __shared__ __align__(16) unsigned char sr_raw[];
   SegRadixSmem<VALS>& sm = *reinterpret_cast<SegRadixSmem<VALS>*>(sr_raw);
-  const int w = threadIdx.x >> 5;
   for (uint32_t li = blockIdx.x; li < nlist; li += gridDim.x) {
     const uint64_t lo = off[list[li]];
     const uint32_t d = (uint32_t)(off[list[li] + 1] - lo);
-    for (uint32_t i = threadIdx.x; i < d; i += RS_NT) {
-      sm.k[0][i] = keys[lo + i];
-      if (VALS) sm.v[0][i] = vals[lo + i];
-    }
-    __syncthreads();
-    int cur = 0;
+    const int G = (int)((d + RS_NT - 1) / RS_NT);
+    const uint32_t c0 = 32u * G * (threadIdx.x >> 5);
+    uint32_t x[SPL_G], y[SPL_G];
+    split_load<VALS>(keys + lo, vals + (VALS ? lo : 0), c0, d, G, x, y);
     for (uint32_t p = 0; p < passes; p++) {
-      const uint32_t shift = 8 * p;
-      sm.seen[threadIdx.x] = 0;
-      sm.base[threadIdx.x] = 0;
-      __syncthreads();
-      for (uint32_t i = threadIdx.x; i < d; i += RS_NT) atomicAdd(&sm.base[(sm.k[cur][i] >> shift) & 255u], 1u);
-      __syncthreads();
-      {
-        uint32_t total;
-        const uint32_t c = sm.base[threadIdx.x];
-        const uint32_t pre = block_excl_scan<uint32_t, RS_NT>(c, total, sm.red);
-        sm.base[threadIdx.x] = pre;
-      }
-      for (uint32_t r0 = 0; r0 < d; r0 += RS_NT) {
-        for (int q = 0; q < RS_NW; q++) sm.wcnt[q][threadIdx.x] = 0;
-        __syncthreads();
-        const uint32_t i = r0 + threadIdx.x;
-        const bool ok = i < d;
-        const uint32_t key = ok ? sm.k[cur][i] : 0u;
-        const uint32_t val = (VALS && ok) ? sm.v[cur][i] : 0u;
-        const uint32_t dig = ok ? ((key >> shift) & 255u) : 256u;
-        const uint32_t peers = __match_any_sync(LG_FULL_MASK, dig);
-        const uint32_t rank = __popc(peers & lanemask_lt());
-        if (ok && rank == 0) sm.wcnt[w][dig] = __popc(peers);
-        __syncthreads();
-        uint32_t acc = 0;
-        for (int q = 0; q < RS_NW; q++) {
-          const uint32_t c = sm.wcnt[q][threadIdx.x];
-          sm.wcnt[q][threadIdx.x] = acc;
-          acc += c;
-        }
-        __syncthreads();
-        if (ok) {
-          const uint32_t pos = sm.base[dig] + sm.seen[dig] + sm.wcnt[w][dig] + rank;
-          sm.k[cur ^ 1][pos] = key;
-          if (VALS) sm.v[cur ^ 1][pos] = val;
-        }
-        __syncthreads();
-        sm.seen[threadIdx.x] += acc;
-      }
-      cur ^= 1;
-      __syncthreads();
+      if (p) split_load<VALS>(sm.k, sm.v, c0, d, G, x, y);
+      split_pass<VALS>(x, y, c0, d, G, SPL_BITS * p, sm.k, sm.v, sm.sp);
     }
     for (uint32_t i = threadIdx.x; i < d; i += RS_NT) {
-      keys[lo + i] = sm.k[cur][i];
-      if (VALS) vals[lo + i] = sm.v[cur][i];
+      keys[lo + i] = sm.k[i];
+      if (VALS) vals[lo + i] = sm.v[i];
     }
     __syncthreads();
   }
@@ -762,7 +851,7 @@ static cudaError_t seg_radix_launch(uint32_t* keys, uint32_t* vals, const uint64
   cudaError_t e = cudaFuncSetAttribute(k_seg_radix<VALS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_seg_radix<VALS><<<grid_for(nlist, 1, 152 * 8), RS_NT, smem, st>>>(keys, vals, off, list, nlist,
-                                                                      (key_bits + 7) / 8);
+                                                                      spl_passes(key_bits));
   count_launch();
   return cudaGetLastError();
 }
@@ -808,7 +897,7 @@ static cudaError_t seg_small_launch(uint32_t* keys, uint32_t* vals, const uint64
 }
 
 cudaError_t segmented_sort(uint32_t* keys, uint32_t* vals, const uint64_t* off, uint64_t rows, uint64_t total,
-                           uint64_t max_row, cudaStream_t st, bool small_done, uint32_t key_bits) {
+                           uint64_t max_row, cudaStream_t st, bool small_done, uint32_t key_bits, bool big_prefix) {
   if (rows == 0 || total == 0 || max_row <= 1) return cudaSuccess;
   cudaError_t e;
   if (!small_done && (e = seg_small_launch(keys, vals, off, rows, st)) != cudaSuccess) return e;
@@ -840,7 +929,9 @@ cudaError_t segmented_sort(uint32_t* keys, uint32_t* vals, const uint64_t* off, 
   if (e == cudaSuccess && mid)
     e = vals ? seg_radix_launch<true>(keys, vals, off, list + base[5], mid, key_bits, st)
              : seg_radix_launch<false>(keys, vals, off, list + base[5], mid, key_bits, st);
-  if (e == cudaSuccess && cnt[9]) e = seg_sort_big(keys, vals, off, list + base[9], cnt[9], key_bits, st);
+  if (e == cudaSuccess && cnt[9])
+    e = big_prefix ? seg_sort_big_prefix(keys, vals, off, cnt[9], key_bits, st)
+                   : seg_sort_big(keys, vals, off, list + base[9], cnt[9], key_bits, st);
   cudaFreeAsync(list, st);
   cudaFreeAsync(meta, st);
   return e == cudaSuccess ? cudaGetLastError() : e;
@@ -1160,7 +1251,9 @@ cudaError_t enc_dm_relabel(const uint64_t* rp, const uint32_t* col, const uint32
   if (dK) cudaFreeAsync(dK, st);
   if (chunk_row) cudaFreeAsync(chunk_row, st);
   // rows of <= 32 arcs left k_dm_rows sorted
-  if (e == cudaSuccess) e = segmented_sort(ncol, w ? nw : nullptr, nrp, n, arcs, max_deg, st, true, host_bits(n - 1));
+  // DM order is degree-descending, so its rows above SEG_MEDIUM keys are the first rows
+  if (e == cudaSuccess)
+    e = segmented_sort(ncol, w ? nw : nullptr, nrp, n, arcs, max_deg, st, true, host_bits(n - 1), split_big != 0);
   cudaFreeAsync(keys, st); cudaFreeAsync(k2, st); cudaFreeAsync(v2, st); cudaFreeAsync(newdeg, st);
   cudaFreeAsync(stmp, st); cudaFreeAsync(rtmp, st);
   return e;

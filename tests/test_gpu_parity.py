@@ -262,13 +262,16 @@ def test_weighted_relabel_and_35_bit_records():
     assert_neighbors(g, g0.row_ptr, g0.col, g0.n, w=g0.weights)
 
 
+@pytest.mark.parametrize("relabel", [True, lg.LG_RELABEL_GREEDY])
 @pytest.mark.parametrize("weighted", [False, True])
-def test_relabel_every_row_size_class(weighted):
+def test_relabel_every_row_size_class(weighted, relabel):
     """Relabeling re-sorts every row: degrees on both sides of each sort size
-    class boundary (sub-warp, warp, register networks of 1..8 warps, radix)."""
+    class boundary (sub-warp, warp, register networks of 1..8 warps, radix).
+    DM order puts the rows above 4,096 keys first (sorted where they lie); the
+    greedy order scatters them (gathered, sorted, scattered back)."""
     rng = np.random.default_rng(11)
     degs = [0, 1, 2, 3, 7, 8, 9, 15, 16, 17, 31, 32, 33, 63, 64, 65, 127, 128, 129, 255, 256, 257, 511, 512,
-            513, 1023, 1024, 1025, 2047, 2048, 2049, 4095, 4096, 4097, 6000]
+            513, 1023, 1024, 1025, 2047, 2048, 2049, 4095, 4096, 4097, 6000, 8191, 8192, 8193]
     n = 9000
     deg = np.zeros(n, dtype=np.int64)
     rows = rng.permutation(n)[:5 * len(degs)]
@@ -279,7 +282,7 @@ def test_relabel_every_row_size_class(weighted):
     col = np.concatenate([np.sort(rng.choice(n, int(d), replace=False)) for d in deg]).astype(np.uint32)
     w = rng.integers(0, 1 << 20, size=len(col)).astype(np.uint32) if weighted else None
     for mode in (0, 2):
-        g, e = encode_both(n, rp, col, w, mode=mode, off=1, relabel=True,
+        g, e = encode_both(n, rp, col, w, mode=mode, off=1, relabel=relabel,
                            weight_bits=20 if weighted and mode == 0 else 0)
         assert_arrays_equal(g, e)
         assert_neighbors(g, rp, col, n, w=w if weighted and mode == 0 else None)
