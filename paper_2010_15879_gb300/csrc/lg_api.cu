@@ -373,10 +373,8 @@ __global__ void k_pr_fill0(float* ranks, uint64_t n, float r0, int64_t personal_
 uint32_t hot_rows(const lg_graph* g, uint32_t elem_bytes) {
   const uint64_t all = g->n < 0xffffffffull ? g->n : 0xffffffffull;
   if (g->relabel != 1 || elem_bytes == 0) return (uint32_t)all;
-  static const uint64_t bytes = [] {
-    const char* e = getenv("LG_HOT_BYTES");
-    return (e && *e) ? (uint64_t)strtoull(e, nullptr, 10) : (64ull << 20);
-  }();
+  const char* e = getenv("LG_HOT_BYTES");  // read per traversal: a few ns
+  const uint64_t bytes = (e && *e) ? (uint64_t)strtoull(e, nullptr, 10) : (64ull << 20);
   const uint64_t rows = bytes / elem_bytes;
   return (uint32_t)(rows < all ? rows : all);
 }
