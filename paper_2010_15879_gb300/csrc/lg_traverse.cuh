@@ -1168,10 +1168,10 @@ __global__ void __launch_bounds__(256) k_dec_flat(GView g, DecArgs a, uint64_t p
 // scan over the threads supplies the prefix of gap runs entered mid-way, and
 // the window is written out coalesced.
 // ---------------------------------------------------------------------------
-constexpr int DEC_P = 13;                  // light fields per lane and window (odd: the lanes' stage
+constexpr int DEC_P = 9;                   // light fields per lane and window (odd: the lanes' stage
                                            // stores fall in distinct banks)
 constexpr int DEC_WF = 32 * DEC_P;         // light fields per warp window
-constexpr int DEC_WCAP = 576;              // stream words a warp window may stage (longer windows shrink)
+constexpr int DEC_WCAP = 400;              // stream words a warp window may stage (longer windows shrink)
 constexpr uint64_t DEC_AGG = 1ull << 62, DEC_INCL = 2ull << 62, DEC_VAL = (1ull << 62) - 1;
 
 struct DecWarp {
@@ -1189,7 +1189,7 @@ struct DecSmem {
   uint32_t nruns, ticket, ok;
 };
 
-static_assert(sizeof(DecSmem) <= 56 * 1024, "four decode CTAs per SM");
+static_assert(sizeof(DecSmem) <= 44 * 1024, "five decode CTAs per SM");
 
 __device__ __forceinline__ uint64_t ld_acquire_u64(const unsigned long long* p) {
   uint64_t v;
@@ -1255,7 +1255,7 @@ __device__ __forceinline__ bool dec_lookback(const DecArgs& a, uint64_t b, uint6
 }
 
 template <int IDM, int OFF>
-__global__ void __launch_bounds__(TNT, 4) k_dec_local(GView g, DecArgs a) {
+__global__ void __launch_bounds__(TNT, 5) k_dec_local(GView g, DecArgs a) {
   extern __shared__ __align__(16) unsigned char dec_smem_raw[];
   DecSmem& sm = *reinterpret_cast<DecSmem*>(dec_smem_raw);
   TileSmem& ts = sm.t;
