@@ -23,7 +23,8 @@ BFS from each graph's vertex 0 and 10 PageRank iterations.
 The ``serve`` workload measures the serving engine: 3 resident compressed
 R-MAT graphs (scales 20, 22, 24, edge factor 16, global IDs + Elias-Fano
 offsets), 100,000 requests (60 % lookups of 1-256 vertices, 30 % BFS, 10 %
-personalized PageRank of 10 iterations): saturation throughput from a burst,
+personalized PageRank of 10 iterations): the highest Poisson arrival rate the
+engine sustains (bisection over rates; the burst rate is reported beside it),
 then p50 / p99 latency with Poisson arrivals at 0.25, 0.5 and 0.9 of it.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lg|reference]
