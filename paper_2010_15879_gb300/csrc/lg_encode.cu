@@ -310,43 +310,59 @@ cudaError_t enc_local_lengths(const uint64_t* rp, const uint32_t* col, uint64_t 
 // (Sections 3.2.1 and 3.3; the weight directly after the ID).  One thread
 // assembles one output word from the (at most 64/r + 2) records touching it.
 // =========================================================================
-// Word-owner packing of r-bit records: 64 records fill exactly r words, so
-// word k is word q = k mod r of chunk c = k / r; the records overlapping word q
-// of a chunk (the same for every chunk) come from a per-block table instead of
-// two 64-bit divisions per word.
-__global__ void __launch_bounds__(256) k_pack_global(const uint32_t* __restrict__ col, const uint32_t* __restrict__ w,
-                                                     uint64_t arcs, uint32_t s, uint32_t omega,
-                                                     uint64_t* __restrict__ out, uint64_t data_words) {
+// 64 records fill exactly r words: a warp takes one such chunk at a time,
+// loads its 64 records coalesced into shared memory (ID | weight << s), then
+// each lane assembles whole output words q = lane, lane + 32, ... of the chunk
+// from the records overlapping them (the same records for every chunk, from a
+// per-block table) and the r words go out as one coalesced store.
+constexpr int PG_WARPS = 8;
+__global__ void __launch_bounds__(PG_WARPS * 32) k_pack_global(const uint32_t* __restrict__ col,
+                                                               const uint32_t* __restrict__ w, uint64_t arcs,
+                                                               uint32_t s, uint32_t omega, uint64_t* __restrict__ out,
+                                                               uint64_t data_words) {
   const uint32_t r = s + omega;  // 1..64
   __shared__ uint8_t tj0[64], tj1[64];  // first and last record of word q within a chunk of 64 records
+  __shared__ uint64_t recs[PG_WARPS][64];
   if (threadIdx.x < r) {
     tj0[threadIdx.x] = (uint8_t)(threadIdx.x * 64u / r);
     tj1[threadIdx.x] = (uint8_t)((threadIdx.x * 64u + 63u) / r);
   }
   __syncthreads();
-  for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < data_words;
-       k += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t c = (k >> 32) ? k / r : (uint64_t)((uint32_t)k / r);
-    const uint32_t q = (uint32_t)(k - c * r);
-    const uint64_t b0 = k * 64;
-    const uint64_t j0 = c * 64 + tj0[q];
-    uint64_t j1 = c * 64 + tj1[q];
-    if (j1 >= arcs) j1 = arcs - 1;
-    uint64_t acc = 0;
-    for (uint64_t j = j0; j <= j1; j++) {
-      uint64_t rec = (uint64_t)col[j];
-      if (w) rec |= (uint64_t)w[j] << s;
-      const int64_t off = (int64_t)(j * r) - (int64_t)b0;
-      acc |= off >= 0 ? (rec << off) : (rec >> (-off));
+  const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+  uint64_t* rec = recs[wid];
+  const uint64_t nchunks = (arcs + 63) / 64;
+  for (uint64_t c = (uint64_t)blockIdx.x * PG_WARPS + wid; c < nchunks; c += (uint64_t)gridDim.x * PG_WARPS) {
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      const uint64_t j = c * 64 + 32u * h + lane;
+      uint64_t x = 0;
+      if (j < arcs) {
+        x = (uint64_t)col[j];
+        if (w) x |= (uint64_t)w[j] << s;
+      }
+      rec[32 * h + lane] = x;  // records past the last arc are zero
     }
-    out[k] = acc;
+    __syncwarp();
+    for (uint32_t q = lane; q < r; q += 32) {
+      const uint64_t k = c * r + q;
+      if (k < data_words) {
+        uint64_t acc = 0;
+        for (uint32_t j = tj0[q]; j <= tj1[q]; j++) {
+          const int off = (int)(j * r) - (int)(q * 64u);
+          acc |= off >= 0 ? (rec[j] << off) : (rec[j] >> (-off));
+        }
+        out[k] = acc;
+      }
+    }
+    __syncwarp();
   }
 }
 
 cudaError_t enc_pack_global(const uint32_t* col, const uint32_t* w, uint64_t arcs, uint32_t s, uint32_t omega,
                             uint64_t* out, uint64_t data_words, cudaStream_t st) {
   if (data_words == 0) return cudaSuccess;
-  k_pack_global<<<grid_for(data_words, 256, 152 * 32), 256, 0, st>>>(col, w, arcs, s, omega, out, data_words);
+  k_pack_global<<<grid_for((arcs + 63) / 64, PG_WARPS, 152 * 12), PG_WARPS * 32, 0, st>>>(col, w, arcs, s, omega,
+                                                                                          out, data_words);
   count_launch();
   return cudaGetLastError();
 }
