@@ -25,6 +25,21 @@
  *   - Thread safety: calls on distinct lg_graph objects may run concurrently;
  *     calls on the same graph may run concurrently only if they use the same
  *     stream or are otherwise ordered by the caller.
+ *
+ * Tuning knobs (environment variables, decimal; unset = the default).  None
+ * changes a result, only how the work is scheduled:
+ *   LG_HEAVY_MIN     256   degrees above this go to the heavy-vertex schedule
+ *                          (a warp per item; 0 = default); read at every
+ *                          lg_encode
+ *   LG_HEAVY_SEG     4096  fields per heavy-schedule item (values below 32 =
+ *                          default); read at every lg_encode
+ *   LG_BFS_PULL_DIV  64    a BFS level runs bottom-up when its frontier holds
+ *                          more than n / LG_BFS_PULL_DIV vertices (0 =
+ *                          default); read once
+ *   LG_HOT_BYTES     64 MiB  DM-relabeled graphs: gathers of the first
+ *                          LG_HOT_BYTES of a per-vertex array (the hubs' rows)
+ *                          are marked evict-last in L2, the rest evict-first
+ *                          (0 = none evict-last); read at every traversal
  */
 #ifndef LG_H
 #define LG_H

@@ -87,7 +87,7 @@ cudaError_t alloc_words(uint64_t** p, uint64_t words, cudaStream_t st) {
   return cudaMemsetAsync(*p, 0, words * sizeof(uint64_t), st);
 }
 
-// tunables (environment overrides are read once)
+// tunables (environment overrides; include/lg.h lists them)
 uint32_t env_u32(const char* name, uint32_t dflt) {
   const char* s = getenv(name);
   if (!s || !*s) return dflt;
